@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Benchmark: MG-CCCS unknowns/s to a 1e-10 relative residual on the 1024^2 TP/ECS workload.
+
+One step = one complete solve (V(1,1)-cycle + CCCS iterations from u = 0 until
+||f - (H-E)u|| / ||f|| <= 1e-10) of the Temkin-Poet problem on [0,30]^2 with ECS
+beyond R0 = 20 (theta = pi/6), E = 0.5, n_b = 3, 8 levels, complex128.  Inputs are
+resident on the device before the timed region; L2 is flushed (256 MB write) before
+every timed step.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (plain NumPy, one core) on the same workload.
+Several GPUs run independent replicas of the solve (the path has no exchange step).
+"""
+import os
+
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import hashlib
+import json
+import math
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "MG-CCCS unknowns/s to 1e-10 rel. residual; % of HBM roofline vs FP64 plain"
+UNIT = "unknowns/s"
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12   # 2 DFMA lanes/clk/SM x 152 SMs x 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--levels", type=int, default=8)
+    ap.add_argument("--E", type=float, default=0.5)
+    ap.add_argument("--nb", type=int, default=3)
+    ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--krylov", type=int, default=20, help="GMRES restart (0 = stand-alone MG-CCCS)")
+    ap.add_argument("--max-iter", type=int, default=2000)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_1412_1953_gb300 import inputs
+    prob = inputs.temkin_poet(args.n, L=30.0, R0=20.0, theta=math.pi / 6, E=args.E, seed=0)
+    cfg = {"workload": f"tp_ecs_{args.n}", "grid_cells": [args.n, args.n], "box": [30.0, 30.0],
+           "ecs": {"R0": 20.0, "theta": "pi/6"}, "unknowns": prob.n_unknowns, "E": args.E,
+           "n_b": args.nb, "levels": args.levels, "cycle": "V(1,1), omega=2/3 Jacobi, FW, bilinear",
+           "coarse_contour_deg": 14.6, "rtol": args.rtol,
+           "outer": f"GMRES({args.krylov}) right-preconditioned by one MG-CCCS iteration" if args.krylov
+           else "stand-alone MG-CCCS iteration", "source": "TP impact source + 1e-3 complex noise, seed 0"}
+    return prob, cfg
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+
+def oracle_rate(prob, args, seconds, min_iters=3):
+    """Time the oracle's MG-CCCS iterations on the workload for about `seconds`, then
+    extrapolate to the iteration count the relative residual needs (observed rate)."""
+    from oracle import mgcccs_oracle as O
+    t0 = time.perf_counter()
+    so = O.Solver(O.params_from_problem(prob, levels=args.levels, n_b=args.nb), prob.v1, prob.v2, prob.v12)
+    setup_s = time.perf_counter() - t0
+    u = np.zeros_like(prob.f)
+    hist, times = [], []
+    t_start = time.perf_counter()
+    while len(times) < min_iters or time.perf_counter() - t_start < seconds:
+        t = time.perf_counter()
+        u = so.iterate(u, prob.f)
+        times.append(time.perf_counter() - t)
+        hist.append(so.relres(u, prob.f))
+        if hist[-1] <= args.rtol or len(times) >= 2000:
+            break
+    t_it = statistics.median(times)
+    k = len(hist)
+    if hist[-1] <= args.rtol:
+        n_it = k
+    else:
+        q = min(3, k - 1)
+        rate = (hist[-1] / hist[-1 - q]) ** (1.0 / q) if q > 0 else 0.9
+        rate = min(max(rate, 1e-3), 0.999)
+        n_it = k + math.ceil(math.log(args.rtol / hist[-1]) / math.log(rate))
+    return {"t_iter_s": t_it, "iters_timed": k, "iters_to_rtol": n_it, "setup_s": setup_s,
+            "relres_last": hist[-1], "value": prob.n_unknowns / (t_it * n_it)}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline helpers
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p)), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("kernels_mg.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1412_1953_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, workload_name):
+    """dram bytes per launch from the committed ncu summary, if it matches this source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload_name}.md")
+    try:
+        vals = {}
+        for line in open(path):
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("source_sha") != kernel_source_sha():
+            return None
+        return float(vals["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def jacobi_flops(sv_box, mx, my):
+    """FP64 flops of one omega-Jacobi sweep: 30 per node in the uniform box (4-neighbour
+    sum, one complex coefficient), 48 elsewhere (four complex coefficients)."""
+    nbox = sv_box[0] * sv_box[1]
+    return 30.0 * nbox + 48.0 * (mx * my - nbox)
+
+
+def uniform_box(n, L, R0):
+    cnt = 0
+    for i in range(n - 1):
+        if (i + 2) * L / n <= R0:
+            cnt = i + 1
+        else:
+            break
+    return cnt
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1412_1953_gb300 import build as B
+    from paper_1412_1953_gb300 import mgcccs as M
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    B.build()
+    prob, cfg = workload(args)
+    N = prob.n_unknowns
+    t0 = time.perf_counter()
+    solver = M.Solver(M.params_for(prob, levels=args.levels, n_b=args.nb, krylov_restart=args.krylov),
+                      prob.v1, prob.v2, prob.v12)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    stream = solver.stream
+    f_d = torch.as_tensor(prob.f).to("cuda")
+    u_d = torch.zeros_like(f_d)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def one_solve():
+        u_d.zero_()
+        return solver.solve(u_d, f_d, rtol=args.rtol, max_iter=args.max_iter)
+
+    for _ in range(args.warmup):
+        its, rr = one_solve()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = solver.launch_count()
+    ms = []
+    iters = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its, rr = one_solve()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        iters.append(its)
+        if rr > args.rtol:
+            raise RuntimeError(f"solve did not reach rtol: {rr}")
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = solver.launch_count() - l0
+    clocks = sampler.stop()
+    total_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * N * args.steps / (total_ms / 1e3)
+
+    # end to end through the host-buffer entry point (H2D of f and u, D2H of u inside)
+    f_h = np.ascontiguousarray(prob.f)
+    e2e_s = []
+    for k in range(max(1, min(args.steps, 3))):
+        u_h = np.zeros_like(f_h)
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        solver.solve_host(u_h, f_h, rtol=args.rtol, max_iter=args.max_iter)
+        e2e_s.append(time.perf_counter() - t)
+    e2e_total = sum(e2e_s)
+    if world > 1:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e = {"value": world * N * len(e2e_s) / e2e_total, "unit": UNIT,
+           "h2d_bytes_per_step": 2 * N * 16, "d2h_bytes_per_step": N * 16}
+
+    # dominant kernel: the fine-level omega-Jacobi sweep, same launch as inside the solve
+    reps = 50
+    u_s = torch.zeros_like(f_d)
+    for _ in range(3):
+        solver.smooth(0, u_s, f_d, 1)
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps // 2):
+        solver.smooth(0, u_s, f_d, 2)      # two launches, ping-pong, result back in u_s
+    e1.record(stream)
+    e1.synchronize()
+    k_ms = e0.elapsed_time(e1) / reps
+    box = uniform_box(args.n, 30.0, 20.0)
+    flops = jacobi_flops((box, box), args.n - 1, args.n - 1)
+    bytes_alg = 80.0 * N                                # u, f, D, omega/D read; u written
+    peaks, peak_src = measured_peaks()
+    traffic = profiled_traffic("k_jacobi", cfg["workload"])
+    roofline = {"bound": "alu", "kernel": "k_jacobi (fine level, complex128)",
+                "achieved": flops / (k_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": flops / (k_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "peak_source": "FP64: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (1.007 TFLOP/s measured)",
+                "kernel_ms": k_ms, "flops_per_launch": flops, "algorithmic_bytes_per_launch": bytes_alg,
+                "hbm_achieved_gbs": bytes_alg / (k_ms * 1e-3) / 1e9,
+                "hbm_peak_gbs": peaks.get("hbm_gbs", 6800.0), "hbm_peak_source": peak_src,
+                "hbm_frac": bytes_alg / (k_ms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}
+    cfg.update({"iterations": int(statistics.median(iters)), "setup_s": round(setup_s, 3),
+                "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                "l2": "flushed before every timed step (256 MB write); working set 0.1 GB"})
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c128 (FP64)", "data": "synthetic",
+           "config": cfg, "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches),
+           "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ob = oracle_rate(prob, args, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": ob["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": (f"{ob['iters_timed']} oracle MG-CCCS iterations on the same "
+                                          f"{args.n}^2 workload (setup {ob['setup_s']:.1f} s excluded), "
+                                          f"median {ob['t_iter_s']:.3f} s/iteration, extrapolated to "
+                                          f"{ob['iters_to_rtol']} iterations to {args.rtol:g} from the "
+                                          f"observed convergence rate")}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return
+    prob, cfg = workload(args)
+    from oracle import mgcccs_oracle as O
+    t0 = time.perf_counter()
+    so = O.Solver(O.params_from_problem(prob, levels=args.levels, n_b=args.nb), prob.v1, prob.v2, prob.v12)
+    setup_s = time.perf_counter() - t0
+    u = np.zeros_like(prob.f)
+    hist = []
+    per_step = 2           # oracle iterations per step (a bounded sample of one solve)
+    for _ in range(args.warmup):
+        for _ in range(per_step):
+            u = so.iterate(u, prob.f)
+            hist.append(so.relres(u, prob.f))
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        for _ in range(per_step):
+            u = so.iterate(u, prob.f)
+            hist.append(so.relres(u, prob.f))
+    el = time.perf_counter() - t
+    t_it = el / (args.steps * per_step)
+    k = len(hist)
+    q = min(3, k - 1)
+    rate = min(max((hist[-1] / hist[-1 - q]) ** (1.0 / q), 1e-3), 0.999)
+    n_it = k if hist[-1] <= args.rtol else k + math.ceil(math.log(args.rtol / hist[-1]) / math.log(rate))
+    value = prob.n_unknowns / (t_it * n_it)
+    sample = (f"{args.steps} x {per_step} timed oracle MG-CCCS iterations (after {args.warmup * per_step} warm-up "
+              f"iterations) on the {args.n}^2 workload, {t_it:.3f} s/iteration, extrapolated to {n_it} iterations "
+              f"to {args.rtol:g} from the observed rate; setup {setup_s:.1f} s excluded")
+    cfg["iterations"] = n_it
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_it * per_step * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (FP64)",
+           "data": "synthetic", "config": cfg,
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

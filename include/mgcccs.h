@@ -1,0 +1,186 @@
+/*
+ * mgcccs.h -- C ABI of the GB300 (sm_103a) MG-CCCS library.
+ *
+ * MG-CCCS (Cools & Vanroose, arXiv:1412.1953) solves the 2D driven Schrodinger
+ * equation of Eq. (7),
+ *
+ *     (-1/2 Laplacian + V1(x) + V2(y) + V12(x,y) - E) u = f ,
+ *
+ * discretised by second-order finite differences (Eq. (11)) on a uniform grid
+ * whose nodes are bent into the complex plane beyond R0 (exterior complex
+ * scaling, Sec. 2.5).  One MG-CCCS iteration is one multigrid V(nu1,nu2)-cycle
+ * with omega-Jacobi smoothing, full-weighting restriction and bilinear
+ * interpolation (Sec. 3.2), followed by one Coupled Channel Correction Step
+ * (Sec. 4.3, Eq. (30)).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Complex values are mgcccs_c128 = {re, im} doubles, bit-compatible with
+ *    cuDoubleComplex and torch.complex128.
+ *  - A grid has nx x ny cells on [0,Lx] x [0,Ly]; the unknowns are the
+ *    (nx-1)*(ny-1) interior nodes, stored row-major [j][i] with x (i) fastest,
+ *    no padding.  Dirichlet zero is implied on the boundary ring.
+ *  - "device" pointers are CUDA global-memory pointers of the current device,
+ *    16-byte aligned; "host" pointers are ordinary host memory.  The caller
+ *    owns every pointer it passes; the library never frees them.
+ *  - All device work is issued on the stream given to mgcccs_setup (NULL =
+ *    legacy default stream).  Entry points marked "async" return once the
+ *    work is queued; the others synchronise that stream before returning.
+ *  - Every entry point returns 0 on success or a negative MGCCCS_E* code;
+ *    mgcccs_strerror() turns a code into text.  On error no output is
+ *    guaranteed unless stated.
+ */
+#ifndef MGCCCS_H
+#define MGCCCS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } mgcccs_c128;
+typedef struct mgcccs_handle* mgcccs_t;
+
+enum {
+  MGCCCS_OK = 0,
+  MGCCCS_EINVAL = -1,      /* bad size, level count, null pointer, n_b, ... */
+  MGCCCS_ECUDA = -2,       /* a CUDA runtime call or kernel launch failed */
+  MGCCCS_ENOSPACE = -3,    /* workspace smaller than mgcccs_workspace_size() */
+  MGCCCS_EBREAKDOWN = -4,  /* zero pivot in the coarsest or channel factorisation,
+                              or the bound-state eigen-solve did not converge */
+  MGCCCS_ENONFINITE = -5,  /* residual became NaN/Inf during a solve */
+  MGCCCS_ENOTCONV = -6     /* max_iter reached without meeting rtol (u, relres valid) */
+};
+
+/* Problem and solver parameters (Sec. 2.5, Sec. 3.2, Sec. 4, Sec. 6). */
+typedef struct {
+  int nx, ny;            /* cells per axis; both divisible by 2^(levels-1) */
+  double Lx, Ly;         /* box [0,Lx] x [0,Ly] */
+  double R0x, R0y;       /* ECS start per axis; R0 >= L means no complex scaling */
+  double theta;          /* ECS angle (radians), z = R0 + (x - R0) e^{i theta} */
+  double E;              /* total energy (real) */
+  int levels;            /* multigrid levels including the fine one (>= 1);
+                            the coarsest, with (nx>>(levels-1))-1 by
+                            (ny>>(levels-1))-1 interior nodes, is solved by a
+                            dense direct method and must have at most 1024 of them */
+  int nu1, nu2;          /* pre/post omega-Jacobi sweeps per level */
+  double omega;          /* Jacobi weight (2/3 in Sec. 3.2) */
+  int n_b;               /* bound states per axis used by the CCCS, 0..8;
+                            0 disables the CCCS (plain multigrid) */
+  double coarse_gamma;   /* the coarse levels (>= 1) use the fine ECS contour
+                            rotated as a whole by e^{i coarse_gamma} */
+  int krylov_restart;    /* outer solver of mgcccs_solve: 0 = stand-alone MG-CCCS
+                            iteration; m in 1..60 = GMRES(m) right-preconditioned by
+                            one MG-CCCS iteration per Arnoldi step (Sec. 6) */
+} mgcccs_params;
+
+/* Bytes of device workspace needed for `p` (0 when p is invalid). */
+size_t mgcccs_workspace_size(const mgcccs_params* p);
+
+/*
+ * Build the solver: ECS node coordinates and 5-point coefficients on every
+ * level (Eq. (11)), the diagonal and omega/diagonal arrays, the dense inverse
+ * of the coarsest operator, the n_b bound states of H1 and H2 (Eq. (9)) with
+ * bilinear normalisation int phi^2 dz = 1 (Sec. 3.1, Remark 3) and two
+ * shift-and-invert refinement steps (Sec. 5.1.2), the channel potentials
+ * V^A, V^B (Sec. 4.2) and the factorised coupled-channel systems
+ * (Eqs. (28)-(29)).  All of it runs in device kernels.
+ *
+ *   out        receives the handle (host memory owned by the library until
+ *              mgcccs_destroy)
+ *   v1, v2     device, nx-1 and ny-1 values of V1, V2 at the interior nodes of
+ *              the ECS contour
+ *   v12        device, (ny-1)*(nx-1) values of V12 at the interior nodes, [j][i]
+ *   workspace  device, >= mgcccs_workspace_size(p) bytes, 256-byte aligned,
+ *              caller-owned, must stay allocated and untouched until destroy
+ *   stream     cudaStream_t (as void*) for all work of this handle
+ * The potentials are copied; they may be freed after this call returns.
+ * Synchronous.  Errors: EINVAL, ENOSPACE, ECUDA, EBREAKDOWN.
+ */
+int mgcccs_setup(mgcccs_t* out, const mgcccs_params* p,
+                 const mgcccs_c128* v1, const mgcccs_c128* v2, const mgcccs_c128* v12,
+                 void* workspace, size_t workspace_bytes, void* stream);
+
+/* One V(nu1,nu2)-cycle on the fine level, u updated in place (Sec. 3.2).
+ * u, f: device, (nx-1)*(ny-1).  Async. */
+int mgcccs_vcycle(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f);
+
+/* One Coupled Channel Correction Step, u updated in place (Sec. 4.3, Eq. (30)):
+ * residual r = f - (H-E)u, projections onto the bound states with the
+ * conventions of Eqs. (25)-(27), the coupled-channel solves of Eqs. (28)-(29)
+ * for the error, and u += sum_m e^A_m(y) phi_m(x) + sum_l e^B_l(x) vphi_l(y).
+ * Requires n_b > 0.  Async. */
+int mgcccs_cccs(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f);
+
+/* Solve (H-E)u = f from the given u until ||f - (H-E)u||_2 / ||f||_2 <= rtol
+ * (Table 1 uses a relative-residual stop) or max_iter iterations.  With
+ * krylov_restart = 0 an iteration is one MG-CCCS iteration (V-cycle then CCCS,
+ * Sec. 6); with krylov_restart = m > 0 it is one Arnoldi step of restarted
+ * GMRES(m) whose right preconditioner is one MG-CCCS iteration from zero (the
+ * paper's MG-CCCS-preconditioned Krylov solver, Sec. 6); the true residual is
+ * recomputed at every restart and at exit.  u: device in/out (start from zeros
+ * for a cold solve); f: device.  iters, relres: host, may be NULL (relres is
+ * the true relative residual at exit); history: host array of max_iter
+ * doubles receiving the relative residual (GMRES: its least-squares estimate)
+ * after each iteration, may be NULL.  Synchronous.  Returns ENOTCONV when
+ * max_iter is reached (u, relres valid), ENONFINITE if the residual is not
+ * finite. */
+int mgcccs_solve(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f, double rtol,
+                 int max_iter, int* iters, double* relres, double* history);
+
+/* Same as mgcccs_solve with HOST u and f: copies f (and the initial u) to the
+ * device, solves, copies u back.  Uses device buffers inside the workspace.
+ * Synchronous. */
+int mgcccs_solve_host(mgcccs_t h, mgcccs_c128* u_host, const mgcccs_c128* f_host,
+                      double rtol, int max_iter, int* iters, double* relres);
+
+/* Preconditioner application z = M^{-1} r (Sec. 6: one V-cycle, then the
+ * CCCS when n_b > 0, from a zero initial guess).  z, r: device, distinct.
+ * Async. */
+int mgcccs_precond_apply(mgcccs_t h, mgcccs_c128* z, const mgcccs_c128* r);
+
+/* y = (H-E)x on the fine level (Eq. (11)); x, y: device, distinct.  Async. */
+int mgcccs_matvec(mgcccs_t h, const mgcccs_c128* x, mgcccs_c128* y);
+
+/* r = f - (H-E)u on the fine level (Eq. (11)); if norm2 is not NULL the
+ * host receives ||r||_2^2 (then synchronous, else async).  u, f, r: device;
+ * r may not alias u. */
+int mgcccs_residual(mgcccs_t h, const mgcccs_c128* u, const mgcccs_c128* f,
+                    mgcccs_c128* r, double* norm2);
+
+/* ---- single steps of the V-cycle, for component checks (Sec. 3.2) ---------
+ * `level` counts from 0 (fine).  Arrays are device, interior-sized for the
+ * level they live on.  All async. */
+
+/* `sweeps` omega-Jacobi sweeps u <- u + omega D^{-1}(f - (H-E)u) on `level`. */
+int mgcccs_smooth(mgcccs_t h, int level, mgcccs_c128* u, const mgcccs_c128* f, int sweeps);
+/* r = f - (H-E)u on `level`. */
+int mgcccs_level_residual(mgcccs_t h, int level, const mgcccs_c128* u,
+                          const mgcccs_c128* f, mgcccs_c128* r);
+/* Full weighting of r (on `level`) onto rc (on level+1). */
+int mgcccs_restrict(mgcccs_t h, int level, const mgcccs_c128* r, mgcccs_c128* rc);
+/* u (on `level`) += bilinear interpolation of ec (on level+1). */
+int mgcccs_prolong_add(mgcccs_t h, int level, const mgcccs_c128* ec, mgcccs_c128* u);
+/* Direct solve of the coarsest-level system: u = A_c^{-1} f. */
+int mgcccs_coarse_solve(mgcccs_t h, const mgcccs_c128* f, mgcccs_c128* u);
+
+/* Bound states found by setup (Eq. (9)).  lambda, mu: host arrays of n_b;
+ * phi: device (nx-1)*n_b, vphi: device (ny-1)*n_b, column-major per state
+ * (phi[k*(nx-1) + i]).  Any pointer may be NULL.  Synchronous. */
+int mgcccs_get_bound_states(mgcccs_t h, mgcccs_c128* lambda, mgcccs_c128* phi,
+                            mgcccs_c128* mu, mgcccs_c128* vphi);
+
+/* Number of kernel launches issued since setup (for launch accounting). */
+long long mgcccs_launch_count(mgcccs_t h);
+
+const char* mgcccs_strerror(int code);
+
+/* Release the handle (host memory and CUDA objects; not the workspace). */
+void mgcccs_destroy(mgcccs_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGCCCS_H */

@@ -441,3 +441,58 @@ def direct_solve(lev: Level, f: np.ndarray) -> np.ndarray:
     A = assemble_weighted(lev).tocsc()
     rhs = weights_2d(lev) * f.ravel()
     return scipy.sparse.linalg.splu(A).solve(rhs).reshape(f.shape)
+
+
+# --------------------------------------------------------------------------------------
+# Krylov acceleration: restarted GMRES(m), right-preconditioned by one MG-CCCS iteration
+# (Sec. 6: MG-CCCS as a Krylov preconditioner, one V-cycle per application)
+# --------------------------------------------------------------------------------------
+
+def gmres(solver: Solver, f: np.ndarray, m: int = 20, rtol: float = 1e-10, max_iter: int = 1000,
+          u0: np.ndarray | None = None, precondition: bool = True):
+    """Restarted GMRES(m) for (H - E)u = f with right preconditioning z = M^{-1} v.
+
+    Textbook form (Saad, Iterative Methods for Sparse Linear Systems, 2nd ed., Alg. 9.5):
+    Arnoldi with modified Gram-Schmidt on the Hermitian inner product, the small
+    least-squares problem min || beta e_1 - H y || solved directly, u += Z y at the end of
+    each cycle, true residual recomputed at every restart.  Returns (u, history of the
+    estimated relative residual per Arnoldi step, true relative residual at exit).
+    """
+    lev = solver.levels[0]
+    A = lambda v: apply_operator(lev, v)
+    Minv = (lambda v: solver.precond_apply(v)) if precondition else (lambda v: v.copy())
+    u = np.zeros_like(f) if u0 is None else u0.copy()
+    fn = np.linalg.norm(f)
+    hist = []
+    steps = 0
+    while steps < max_iter:
+        r = f - A(u)
+        beta = np.linalg.norm(r)
+        if beta <= rtol * fn or beta == 0.0:
+            break
+        V = [r / beta]
+        Z = []
+        H = np.zeros((m + 1, m), dtype=np.complex128)
+        y = np.zeros(0, dtype=np.complex128)
+        for j in range(m):
+            Z.append(Minv(V[j]))
+            w = A(Z[j])
+            for i in range(j + 1):
+                H[i, j] = np.vdot(V[i], w)
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            steps += 1
+            e1 = np.zeros(j + 2, dtype=np.complex128)
+            e1[0] = beta
+            y = np.linalg.lstsq(H[: j + 2, : j + 1], e1, rcond=None)[0]
+            est = np.linalg.norm(H[: j + 2, : j + 1] @ y - e1) / fn
+            hist.append(est)
+            if est <= rtol or H[j + 1, j] == 0.0 or steps >= max_iter:
+                break
+            V.append(w / H[j + 1, j])
+        for k in range(len(y)):
+            u = u + y[k] * Z[k]
+        if hist and hist[-1] <= rtol:
+            if np.linalg.norm(f - A(u)) <= rtol * fn:
+                break
+    return u, hist, np.linalg.norm(f - A(u)) / fn

@@ -1,0 +1,173 @@
+// Internal types and device helpers of the MG-CCCS library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mgcccs.h"
+
+typedef double2 cplx;
+
+#define MGC_MAX_LEVELS 16
+#define MGC_MAX_NB 8
+#define MGC_MAX_COARSE 1024
+#define MGC_MAX_RESTART 60
+
+// ---------------------------------------------------------------- complex arithmetic
+__host__ __device__ __forceinline__ cplx cmk(double re, double im) { return make_double2(re, im); }
+__host__ __device__ __forceinline__ cplx cadd(cplx a, cplx b) { return cmk(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ cplx csub(cplx a, cplx b) { return cmk(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ cplx cneg(cplx a) { return cmk(-a.x, -a.y); }
+__host__ __device__ __forceinline__ cplx cscal(double s, cplx a) { return cmk(s * a.x, s * a.y); }
+__host__ __device__ __forceinline__ cplx cmul(cplx a, cplx b) {
+  return cmk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// acc + a*b
+__host__ __device__ __forceinline__ cplx cfma(cplx a, cplx b, cplx acc) {
+  return cmk(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+// acc - a*b
+__host__ __device__ __forceinline__ cplx cfms(cplx a, cplx b, cplx acc) {
+  return cmk(fma(-a.x, b.x, fma(a.y, b.y, acc.x)), fma(-a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+__host__ __device__ __forceinline__ double cabs2(cplx a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ double cabs1(cplx a) { return fabs(a.x) + fabs(a.y); }
+__host__ __device__ __forceinline__ double cmod(cplx a) { return hypot(a.x, a.y); }
+
+// a / b by Smith's algorithm (R. L. Smith, "Algorithm 116: Complex division",
+// CACM 5(8), 1962): scale by the larger component of b to avoid overflow.
+__host__ __device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
+  if (fabs(b.y) <= fabs(b.x)) {
+    double r = b.y / b.x;
+    double den = b.x + b.y * r;
+    return cmk((a.x + a.y * r) / den, (a.y - a.x * r) / den);
+  } else {
+    double r = b.x / b.y;
+    double den = b.x * r + b.y;
+    return cmk((a.x * r + a.y) / den, (a.y * r - a.x) / den);
+  }
+}
+
+// Principal square root: sqrt(z) = sqrt((|z|+Re z)/2) + i sgn(Im z) sqrt((|z|-Re z)/2),
+// evaluated from the larger of the two to avoid cancellation.
+__host__ __device__ __forceinline__ cplx csqrt_p(cplx z) {
+  double m = hypot(z.x, z.y);
+  if (m == 0.0) return cmk(0.0, 0.0);
+  if (z.x >= 0.0) {
+    double t = sqrt(0.5 * (m + z.x));
+    return cmk(t, z.y / (2.0 * t));
+  } else {
+    double t = sqrt(0.5 * (m - z.x));
+    double s = (z.y < 0.0) ? -t : t;
+    return cmk(z.y / (2.0 * s), s);
+  }
+}
+
+// ---------------------------------------------------------------- level descriptors
+
+// 5-point operator of one level, (H - E)u = D u + west_x u_W + east_x u_E + west_y u_S + east_y u_N.
+// In the box i < ux, j < uy all four neighbour coefficients equal `cu` (uniform spacing on
+// an unbent part of the contour), which the kernels use to skip the per-node coefficients.
+struct StencilView {
+  int mx, my;              // interior nodes per axis (row pitch = mx)
+  int ux, uy;              // uniform box
+  cplx cu;                 // uniform neighbour coefficient in the box
+  const cplx* west_x;      // [mx]
+  const cplx* east_x;      // [mx]
+  const cplx* west_y;      // [my]
+  const cplx* east_y;      // [my]
+  const cplx* D;           // [my*mx] full diagonal of H - E
+  const cplx* Dinv;        // [my*mx] omega / D
+};
+
+// Error bits written by kernels into the handle's device status word.
+enum {
+  MGC_ST_PIVOT = 1,        // zero pivot in a dense or block factorisation
+  MGC_ST_EIG = 2,          // eigen-solve failed to converge
+  MGC_ST_NONFINITE = 4
+};
+
+// ---------------------------------------------------------------- launchers (defined in the .cu files)
+// All return cudaGetLastError() of their launch.
+
+// kernels_mg.cu
+cudaError_t launch_jacobi(const StencilView& s, const cplx* u_in, cplx* u_out, const cplx* f, cudaStream_t st);
+cudaError_t launch_jacobi_zero(const StencilView& s, cplx* u_out, const cplx* f, cudaStream_t st);
+cudaError_t launch_residual(const StencilView& s, const cplx* u, const cplx* f, cplx* r,
+                            double* norm_part, cudaStream_t st);
+int residual_norm_blocks(const StencilView& s);
+cudaError_t launch_restrict(int mx, int my, const cplx* r, cplx* rc, cudaStream_t st);
+cudaError_t launch_prolong_add(int mx, int my, const cplx* ec, cplx* u, cudaStream_t st);
+cudaError_t launch_coarse_solve(int nc, const cplx* Ainv, const cplx* f, cplx* u, cudaStream_t st);
+cudaError_t launch_sum_partials(const double* part, int n, double* out, cudaStream_t st);
+cudaError_t launch_norm2(const cplx* v, long long n, double* part, int nblocks, cudaStream_t st);
+int norm2_blocks(long long n);
+cudaError_t launch_apply(const StencilView& s, const cplx* x, cplx* y, cudaStream_t st);
+
+// kernels_krylov.cu
+int krylov_blocks(long long n);
+cudaError_t launch_multidot(long long n, int k, const cplx* V, long long ld, const cplx* w, cplx* partial,
+                            int nblk, cudaStream_t st);
+cudaError_t launch_reduce_dots(int nblk, int k, const cplx* partial, cplx* out, cplx* acc_into, cudaStream_t st);
+cudaError_t launch_multiaxpy(long long n, int k, const cplx* V, long long ld, const cplx* coef, double sgn,
+                             cplx* w, double* norm_part, int nblk, cudaStream_t st);
+cudaError_t launch_scale_by_norm(long long n, const cplx* w, cplx* out, const double* norm2, cplx* store,
+                                 int nblk, cudaStream_t st);
+cudaError_t launch_givens(int j, int m, cplx* H, cplx* cs, cplx* sn, cplx* g, double* est, cudaStream_t st);
+cudaError_t launch_hess_solve(int k, int m, const cplx* H, const cplx* g, cplx* y, cudaStream_t st);
+cudaError_t launch_zero_c(int n, cplx* a, cudaStream_t st);
+
+// kernels_cccs.cu
+struct CCView {
+  int mx, my, nb;
+  const cplx* wphi;        // [nb][mx]  w_x(i) phi_m(i)
+  const cplx* wvphi;       // [nb][my]  w_y(j) vphi_l(j)
+  const cplx* phi;         // [nb][mx]
+  const cplx* vphi;        // [nb][my]
+  cplx* Px_part;           // [ntx][nb][my]
+  cplx* Py_part;           // [nty][nb][mx]
+  cplx* Px;                // [nb][my]
+  cplx* Py;                // [nb][mx]
+  cplx* c;                 // [nb][nb]  c[a][b] = int int phi_a vphi_b r
+  cplx* rA;                // [nb][my]
+  cplx* rB;                // [nb][mx]
+  cplx* eA;                // [nb][my]
+  cplx* eB;                // [nb][mx]
+  const cplx* GA;          // [my][nb][nb]  block-Thomas inverses, channel A (along y)
+  const cplx* GB;          // [mx][nb][nb]  channel B (along x)
+  const cplx* aA;          // [my] sub-diagonal (west_y) of channel A
+  const cplx* cA;          // [my] super-diagonal (east_y)
+  const cplx* aB;          // [mx] west_x
+  const cplx* cB;          // [mx] east_x
+  cplx* gA;                // [my][nb] forward-sweep scratch
+  cplx* gB;                // [mx][nb]
+};
+int cc_tiles_x(int mx);
+int cc_tiles_y(int my);
+cudaError_t launch_residual_project(const StencilView& s, const CCView& c, const cplx* u, const cplx* f,
+                                    cudaStream_t st);
+cudaError_t launch_cc_rhs(const CCView& c, cudaStream_t st);
+cudaError_t launch_channel_solve(const CCView& c, cudaStream_t st);
+cudaError_t launch_cccs_correct(const CCView& c, cplx* u, cudaStream_t st);
+
+// kernels_setup.cu
+struct AxisSetup {
+  int n;                   // cells
+  double L, R0, theta, gamma;
+  cplx* west; cplx* east; cplx* diag; cplx* w;   // [n-1] each
+};
+cudaError_t launch_setup_axis(const AxisSetup& a, cudaStream_t st);
+cudaError_t launch_setup_diag(int mx, int my, int stride, int fine_mx, const cplx* dx, const cplx* dy,
+                              const cplx* v1, const cplx* v2, const cplx* v12, double E, double omega,
+                              cplx* D, cplx* Dinv, int* status, cudaStream_t st);
+cudaError_t launch_coarse_inverse(const StencilView& s, cplx* aug, cplx* Ainv, int* status, cudaStream_t st);
+cudaError_t launch_bound_states(int m, const cplx* west, const cplx* east, const cplx* diag, const cplx* v,
+                                const cplx* w, int nb, cplx* lam, cplx* phi, cplx* scratch, int* status,
+                                cudaStream_t st);
+size_t bound_states_scratch(int m, int nb);
+cudaError_t launch_weight_states(int m, int nb, const cplx* w, const cplx* phi, cplx* wphi, cudaStream_t st);
+cudaError_t launch_channel_potentials(int mx, int my, int nb, const cplx* wphi, const cplx* phi,
+                                      const cplx* wvphi, const cplx* vphi, const cplx* v12,
+                                      cplx* VA, cplx* VB, cudaStream_t st);
+cudaError_t launch_channel_factor(int m, int nb, const cplx* diag, const cplx* v, double E, const cplx* lam,
+                                  const cplx* Vc, const cplx* a, const cplx* c, cplx* G, int* status,
+                                  cudaStream_t st);

@@ -1,0 +1,291 @@
+// Coupled Channel Correction Step kernels (Sec. 4 of Cools & Vanroose).
+//
+//   residual r = f - (H - E) u                                   (Sec. 4.3)
+//   P^x_i(y) = sum_x w phi_i r,  P^y_j(x) = sum_y w vphi_j r      (projections, Sec. 4.1)
+//   c_ij = sum_y w vphi_j P^x_i = a_ji + b_ij                     (Eq. (27))
+//   a_ji = c_ij (j <= i), b_ij = c_ij (j > i)                     (Eqs. (25)-(26))
+//   r^A_i = P^x_i - sum_{l>i} c_il vphi_l,  r^B_j = P^y_j - sum_{m>=j} c_mj phi_m
+//   coupled-channel solves for e^A, e^B                           (Eqs. (28)-(29))
+//   u += sum_m phi_m(x) e^A_m(y) + sum_l e^B_l(x) vphi_l(y)       (Eq. (30))
+//
+// The projections are fused into the residual pass and reduced deterministically:
+// warp shuffles along x and a shared-memory pass along y give per-tile partials,
+// which a second kernel sums in a fixed order.
+#include "common.cuh"
+
+namespace {
+
+constexpr int TX = 32;        // tile width (one warp per row)
+constexpr int WY = 8;         // warps per block
+constexpr int SY = 4;         // rows per warp
+constexpr int TY = WY * SY;   // tile height
+
+__device__ __forceinline__ cplx ldz(const cplx* __restrict__ a, int p, bool ok) {
+  return ok ? __ldg(a + p) : cmk(0.0, 0.0);
+}
+
+__device__ __forceinline__ cplx residual_at(const StencilView& s, const cplx* __restrict__ u,
+                                            const cplx* __restrict__ f, int i, int j) {
+  const int p = j * s.mx + i;
+  cplx uc = __ldg(u + p);
+  cplx uw = ldz(u, p - 1, i > 0);
+  cplx ue = ldz(u, p + 1, i + 1 < s.mx);
+  cplx us = ldz(u, p - s.mx, j > 0);
+  cplx un = ldz(u, p + s.mx, j + 1 < s.my);
+  cplx a = cmul(__ldg(s.D + p), uc);
+  if (i < s.ux && j < s.uy) {
+    a = cfma(s.cu, cadd(cadd(uw, ue), cadd(us, un)), a);
+  } else {
+    a = cfma(__ldg(s.west_x + i), uw, a);
+    a = cfma(__ldg(s.east_x + i), ue, a);
+    a = cfma(__ldg(s.west_y + j), us, a);
+    a = cfma(__ldg(s.east_y + j), un, a);
+  }
+  return csub(__ldg(f + p), a);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(TX * WY) k_residual_project(StencilView s, CCView c, const cplx* __restrict__ u,
+                                                              const cplx* __restrict__ f) {
+  __shared__ cplx shy[WY][NB][TX];
+  const int lane = threadIdx.x;
+  const int wy = threadIdx.y;
+  const int i = blockIdx.x * TX + lane;
+  const bool col_ok = i < s.mx;
+  cplx wphi[NB];
+#pragma unroll
+  for (int m = 0; m < NB; ++m) wphi[m] = col_ok ? __ldg(c.wphi + m * s.mx + i) : cmk(0.0, 0.0);
+  cplx py[NB];
+#pragma unroll
+  for (int l = 0; l < NB; ++l) py[l] = cmk(0.0, 0.0);
+
+  for (int q = 0; q < SY; ++q) {
+    const int j = blockIdx.y * TY + q * WY + wy;
+    const bool ok = col_ok && j < s.my;
+    cplx r = ok ? residual_at(s, u, f, i, j) : cmk(0.0, 0.0);
+    if (j < s.my) {
+#pragma unroll
+      for (int l = 0; l < NB; ++l) py[l] = cfma(__ldg(c.wvphi + l * s.my + j), r, py[l]);
+    }
+    // P^x partial of this row over the tile's 32 columns
+    cplx px[NB];
+#pragma unroll
+    for (int m = 0; m < NB; ++m) px[m] = cmul(wphi[m], r);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int m = 0; m < NB; ++m) {
+        px[m].x += __shfl_down_sync(0xffffffffu, px[m].x, o);
+        px[m].y += __shfl_down_sync(0xffffffffu, px[m].y, o);
+      }
+    }
+    if (lane == 0 && j < s.my) {
+#pragma unroll
+      for (int m = 0; m < NB; ++m) c.Px_part[((size_t)blockIdx.x * NB + m) * s.my + j] = px[m];
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < NB; ++l) shy[wy][l][lane] = py[l];
+  __syncthreads();
+  if (wy == 0 && col_ok) {
+#pragma unroll
+    for (int l = 0; l < NB; ++l) {
+      cplx acc = shy[0][l][lane];
+#pragma unroll
+      for (int w = 1; w < WY; ++w) acc = cadd(acc, shy[w][l][lane]);
+      c.Py_part[((size_t)blockIdx.y * NB + l) * s.mx + i] = acc;
+    }
+  }
+}
+
+// Sum the per-tile partials in tile order.
+__global__ void __launch_bounds__(256) k_reduce_partials(int nb, int mx, int my, int ntx, int nty,
+                                                         const cplx* __restrict__ Px_part,
+                                                         const cplx* __restrict__ Py_part,
+                                                         cplx* __restrict__ Px, cplx* __restrict__ Py) {
+  const int t = blockIdx.x * 256 + threadIdx.x;
+  const int nx_tot = nb * my, ny_tot = nb * mx;
+  if (t < nx_tot) {
+    cplx acc = cmk(0.0, 0.0);
+    for (int k = 0; k < ntx; ++k) acc = cadd(acc, Px_part[(size_t)k * nx_tot + t]);
+    Px[t] = acc;
+  } else if (t < nx_tot + ny_tot) {
+    const int q = t - nx_tot;
+    cplx acc = cmk(0.0, 0.0);
+    for (int k = 0; k < nty; ++k) acc = cadd(acc, Py_part[(size_t)k * ny_tot + q]);
+    Py[q] = acc;
+  }
+}
+
+// c[a][b] = sum_j w_y(j) vphi_b(j) P^x_a(j): one block per (a, b).
+__global__ void __launch_bounds__(256) k_cc_coef(int nb, int my, const cplx* __restrict__ wvphi,
+                                                 const cplx* __restrict__ Px, cplx* __restrict__ cmat) {
+  __shared__ double sh[2][8];
+  const int a = blockIdx.x / nb, b = blockIdx.x % nb;
+  cplx acc = cmk(0.0, 0.0);
+  for (int j = threadIdx.x; j < my; j += 256) acc = cfma(__ldg(wvphi + b * my + j), __ldg(Px + a * my + j), acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+  }
+  if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = acc.x; sh[1][threadIdx.x >> 5] = acc.y; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cplx tot = cmk(0.0, 0.0);
+    for (int w = 0; w < 8; ++w) tot = cadd(tot, cmk(sh[0][w], sh[1][w]));
+    cmat[a * nb + b] = tot;
+  }
+}
+
+// Channel right-hand sides with the uniqueness conventions.
+__global__ void __launch_bounds__(256) k_cc_split(int nb, int mx, int my, const cplx* __restrict__ cmat,
+                                                  const cplx* __restrict__ phi, const cplx* __restrict__ vphi,
+                                                  const cplx* __restrict__ Px, const cplx* __restrict__ Py,
+                                                  cplx* __restrict__ rA, cplx* __restrict__ rB) {
+  const int t = blockIdx.x * 256 + threadIdx.x;
+  if (t < nb * my) {
+    const int a = t / my, j = t % my;
+    cplx v = Px[t];
+    for (int l = a + 1; l < nb; ++l) v = cfms(cmat[a * nb + l], __ldg(vphi + l * my + j), v);   // b_al
+    rA[t] = v;
+  } else if (t < nb * my + nb * mx) {
+    const int q = t - nb * my;
+    const int b = q / mx, i = q % mx;
+    cplx v = Py[q];
+    for (int m = b; m < nb; ++m) v = cfms(cmat[m * nb + b], __ldg(phi + m * mx + i), v);        // a_bm
+    rB[q] = v;
+  }
+}
+
+// Block-Thomas solve of  a_k x_{k-1} + B_k x_k + c_k x_{k+1} = r_k  with precomputed
+// G_k = (B_k - a_k c_{k-1} G_{k-1})^{-1}:  g_k = G_k (r_k - a_k g_{k-1}),
+// x_k = g_k - c_k G_k x_{k+1}.  Block 0 solves channel A (along y), block 1 channel B.
+// One warp, lane q owns component q.
+__global__ void __launch_bounds__(32) k_channel_solve(CCView c) {
+  __shared__ cplx sv[MGC_MAX_NB];
+  const int q = threadIdx.x;
+  const int nb = c.nb;
+  const bool isA = blockIdx.x == 0;
+  const int m = isA ? c.my : c.mx;
+  const cplx* G = isA ? c.GA : c.GB;
+  const cplx* a = isA ? c.aA : c.aB;
+  const cplx* cc = isA ? c.cA : c.cB;
+  const cplx* r = isA ? c.rA : c.rB;     // [nb][m]
+  cplx* g = isA ? c.gA : c.gB;           // [m][nb]
+  cplx* x = isA ? c.eA : c.eB;           // [nb][m]
+  const bool act = q < nb;
+  cplx prev = cmk(0.0, 0.0);
+  for (int k = 0; k < m; ++k) {
+    if (act) {
+      cplx t = r[q * m + k];
+      if (k > 0) t = cfms(a[k], prev, t);
+      sv[q] = t;
+    }
+    __syncwarp();
+    cplx gq = cmk(0.0, 0.0);
+    if (act) {
+      const cplx* Gk = G + (size_t)k * nb * nb + q * nb;
+      for (int p = 0; p < nb; ++p) gq = cfma(Gk[p], sv[p], gq);
+      g[(size_t)k * nb + q] = gq;
+    }
+    __syncwarp();
+    prev = gq;
+  }
+  cplx xn = prev;           // x_{m-1} = g_{m-1}
+  if (act) x[q * m + (m - 1)] = xn;
+  for (int k = m - 2; k >= 0; --k) {
+    if (act) sv[q] = xn;
+    __syncwarp();
+    if (act) {
+      const cplx* Gk = G + (size_t)k * nb * nb + q * nb;
+      cplx s = cmk(0.0, 0.0);
+      for (int p = 0; p < nb; ++p) s = cfma(Gk[p], sv[p], s);
+      xn = cfms(cc[k], s, g[(size_t)k * nb + q]);
+      x[q * m + k] = xn;
+    }
+    __syncwarp();
+  }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(256) k_cccs_correct(int mx, int my, const cplx* __restrict__ phi,
+                                                      const cplx* __restrict__ vphi, const cplx* __restrict__ eA,
+                                                      const cplx* __restrict__ eB, cplx* __restrict__ u) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 8 + threadIdx.y;
+  if (i >= mx || j >= my) return;
+  const int p = j * mx + i;
+  cplx v = u[p];
+#pragma unroll
+  for (int m = 0; m < NB; ++m) v = cfma(__ldg(phi + m * mx + i), __ldg(eA + m * my + j), v);
+#pragma unroll
+  for (int l = 0; l < NB; ++l) v = cfma(__ldg(eB + l * mx + i), __ldg(vphi + l * my + j), v);
+  u[p] = v;
+}
+
+template <int NB>
+cudaError_t rp_launch(const StencilView& s, const CCView& c, const cplx* u, const cplx* f, cudaStream_t st) {
+  dim3 g(cc_tiles_x(s.mx), cc_tiles_y(s.my));
+  k_residual_project<NB><<<g, dim3(TX, WY), 0, st>>>(s, c, u, f);
+  return cudaGetLastError();
+}
+
+template <int NB>
+cudaError_t corr_launch(const CCView& c, cplx* u, cudaStream_t st) {
+  dim3 g((c.mx + 31) / 32, (c.my + 7) / 8);
+  k_cccs_correct<NB><<<g, dim3(32, 8), 0, st>>>(c.mx, c.my, c.phi, c.vphi, c.eA, c.eB, u);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int cc_tiles_x(int mx) { return (mx + TX - 1) / TX; }
+int cc_tiles_y(int my) { return (my + TY - 1) / TY; }
+
+cudaError_t launch_residual_project(const StencilView& s, const CCView& c, const cplx* u, const cplx* f,
+                                    cudaStream_t st) {
+  switch (c.nb) {
+    case 1: return rp_launch<1>(s, c, u, f, st);
+    case 2: return rp_launch<2>(s, c, u, f, st);
+    case 3: return rp_launch<3>(s, c, u, f, st);
+    case 4: return rp_launch<4>(s, c, u, f, st);
+    case 5: return rp_launch<5>(s, c, u, f, st);
+    case 6: return rp_launch<6>(s, c, u, f, st);
+    case 7: return rp_launch<7>(s, c, u, f, st);
+    case 8: return rp_launch<8>(s, c, u, f, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cc_rhs(const CCView& c, cudaStream_t st) {
+  int tot = c.nb * (c.mx + c.my);
+  k_reduce_partials<<<(tot + 255) / 256, 256, 0, st>>>(c.nb, c.mx, c.my, cc_tiles_x(c.mx), cc_tiles_y(c.my),
+                                                        c.Px_part, c.Py_part, c.Px, c.Py);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_cc_coef<<<c.nb * c.nb, 256, 0, st>>>(c.nb, c.my, c.wvphi, c.Px, c.c);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_cc_split<<<(tot + 255) / 256, 256, 0, st>>>(c.nb, c.mx, c.my, c.c, c.phi, c.vphi, c.Px, c.Py, c.rA, c.rB);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_channel_solve(const CCView& c, cudaStream_t st) {
+  k_channel_solve<<<2, 32, 0, st>>>(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cccs_correct(const CCView& c, cplx* u, cudaStream_t st) {
+  switch (c.nb) {
+    case 1: return corr_launch<1>(c, u, st);
+    case 2: return corr_launch<2>(c, u, st);
+    case 3: return corr_launch<3>(c, u, st);
+    case 4: return corr_launch<4>(c, u, st);
+    case 5: return corr_launch<5>(c, u, st);
+    case 6: return corr_launch<6>(c, u, st);
+    case 7: return corr_launch<7>(c, u, st);
+    case 8: return corr_launch<8>(c, u, st);
+  }
+  return cudaErrorInvalidValue;
+}

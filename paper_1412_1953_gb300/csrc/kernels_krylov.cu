@@ -1,0 +1,190 @@
+// Kernels of the restarted GMRES(m) outer solver, right-preconditioned by one MG-CCCS
+// iteration (Sec. 6: MG-CCCS as a Krylov preconditioner).  Arnoldi uses classical
+// Gram-Schmidt applied twice (each pass: one fused multi-dot, one fused multi-axpy);
+// the Hessenberg least-squares problem is reduced by complex Givens rotations on the
+// device, so the host only reads one residual estimate per step.
+//
+// Basis vectors are stored contiguously: V_i = V + i * ld.
+#include "common.cuh"
+
+namespace {
+
+constexpr int NT = 256;
+
+template <int NTH>
+__device__ __forceinline__ cplx block_sum_c(cplx v, double (*sh)[NTH / 32]) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+  }
+  if ((t & 31) == 0) { sh[0][t >> 5] = v.x; sh[1][t >> 5] = v.y; }
+  __syncthreads();
+  cplx tot = cmk(0.0, 0.0);
+  if (t == 0)
+    for (int w = 0; w < NTH / 32; ++w) tot = cadd(tot, cmk(sh[0][w], sh[1][w]));
+  return tot;
+}
+
+// partial[i][b] = sum over block b's points of conj(V_i) w   (grid: nblk x k)
+__global__ void __launch_bounds__(NT) k_multidot(long long n, const cplx* __restrict__ V, long long ld,
+                                                 const cplx* __restrict__ w, cplx* __restrict__ partial) {
+  __shared__ double sh[2][NT / 32];
+  const int i = blockIdx.y;
+  const cplx* v = V + (size_t)i * ld;
+  cplx acc = cmk(0.0, 0.0);
+  for (long long p = blockIdx.x * (long long)NT + threadIdx.x; p < n; p += (long long)gridDim.x * NT) {
+    cplx a = __ldg(v + p), b = __ldg(w + p);
+    acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
+    acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
+  }
+  cplx tot = block_sum_c<NT>(acc, sh);
+  if (threadIdx.x == 0) partial[(size_t)i * gridDim.x + blockIdx.x] = tot;
+}
+
+// out[i] = sum_b partial[i][b] (fixed order); acc_into[i] += out[i] when given.
+__global__ void __launch_bounds__(NT) k_reduce_dots(int nblk, const cplx* __restrict__ partial,
+                                                    cplx* __restrict__ out, cplx* __restrict__ acc_into) {
+  __shared__ double sh[2][NT / 32];
+  const int i = blockIdx.x;
+  cplx acc = cmk(0.0, 0.0);
+  for (int b = threadIdx.x; b < nblk; b += NT) acc = cadd(acc, partial[(size_t)i * nblk + b]);
+  cplx tot = block_sum_c<NT>(acc, sh);
+  if (threadIdx.x == 0) {
+    out[i] = tot;
+    if (acc_into) acc_into[i] = cadd(acc_into[i], tot);
+  }
+}
+
+// w += sgn * sum_{i<k} coef[i] V_i ; optional per-block partials of |w|^2.
+__global__ void __launch_bounds__(NT) k_multiaxpy(long long n, int k, const cplx* __restrict__ V, long long ld,
+                                                  const cplx* __restrict__ coef, double sgn, cplx* __restrict__ w,
+                                                  double* __restrict__ norm_part) {
+  __shared__ cplx sc[64];
+  __shared__ double sh[NT / 32];
+  for (int i = threadIdx.x; i < k; i += NT) sc[i] = cscal(sgn, coef[i]);
+  __syncthreads();
+  double n2 = 0.0;
+  for (long long p = blockIdx.x * (long long)NT + threadIdx.x; p < n; p += (long long)gridDim.x * NT) {
+    cplx acc = w[p];
+    for (int i = 0; i < k; ++i) acc = cfma(sc[i], __ldg(V + (size_t)i * ld + p), acc);
+    w[p] = acc;
+    n2 += cabs2(acc);
+  }
+  if (norm_part) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n2 += __shfl_down_sync(0xffffffffu, n2, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = n2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int q = 0; q < NT / 32; ++q) tot += sh[q];
+      norm_part[blockIdx.x] = tot;
+    }
+  }
+}
+
+// out = w / sqrt(*norm2) (zeros if the norm vanishes); *store = sqrt(*norm2) + 0i.
+__global__ void __launch_bounds__(NT) k_scale_by_norm(long long n, const cplx* __restrict__ w, cplx* __restrict__ out,
+                                                      const double* __restrict__ norm2, cplx* __restrict__ store) {
+  const double beta = sqrt(*norm2);
+  const double s = beta > 0.0 ? 1.0 / beta : 0.0;
+  const long long p0 = blockIdx.x * (long long)NT + threadIdx.x;
+  if (p0 == 0 && store) *store = cmk(beta, 0.0);
+  for (long long p = p0; p < n; p += (long long)gridDim.x * NT) out[p] = cscal(s, w[p]);
+}
+
+// Apply rotations 0..j-1 to column j of H, build rotation j, update g; est = |g[j+1]|.
+// H is column-major with leading dimension m+1.  Rotation j maps rows (j, j+1) by
+// [conj(c) conj(s); -s c] with c = a/rho, s = b/rho, rho = sqrt(|a|^2 + |b|^2).
+__global__ void k_givens(int j, int m, cplx* __restrict__ H, cplx* __restrict__ cs, cplx* __restrict__ sn,
+                         cplx* __restrict__ g, double* __restrict__ est) {
+  if (threadIdx.x != 0) return;
+  cplx* col = H + (size_t)j * (m + 1);
+  for (int i = 0; i < j; ++i) {
+    cplx x = col[i], y = col[i + 1];
+    cplx c = cs[i], s = sn[i];
+    col[i] = cadd(cmul(cmk(c.x, -c.y), x), cmul(cmk(s.x, -s.y), y));
+    col[i + 1] = csub(cmul(c, y), cmul(s, x));
+  }
+  cplx a = col[j], b = col[j + 1];
+  double rho = sqrt(cabs2(a) + cabs2(b));
+  cplx c, s;
+  if (rho == 0.0) {
+    c = cmk(1.0, 0.0);
+    s = cmk(0.0, 0.0);
+  } else {
+    c = cscal(1.0 / rho, a);
+    s = cscal(1.0 / rho, b);
+  }
+  cs[j] = c;
+  sn[j] = s;
+  col[j] = cmk(rho, 0.0);
+  col[j + 1] = cmk(0.0, 0.0);
+  cplx gj = g[j];
+  g[j + 1] = cneg(cmul(s, gj));
+  g[j] = cmul(cmk(c.x, -c.y), gj);
+  *est = cmod(g[j + 1]);
+}
+
+// Back substitution R y = g[0..k-1] with the rotated (upper-triangular) H.
+__global__ void k_hess_solve(int k, int m, const cplx* __restrict__ H, const cplx* __restrict__ g,
+                             cplx* __restrict__ y) {
+  if (threadIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; --i) {
+    cplx t = g[i];
+    for (int q = i + 1; q < k; ++q) t = cfms(H[(size_t)q * (m + 1) + i], y[q], t);
+    y[i] = cdiv(t, H[(size_t)i * (m + 1) + i]);
+  }
+}
+
+__global__ void k_zero_c(int n, cplx* __restrict__ a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) a[t] = cmk(0.0, 0.0);
+}
+
+}  // namespace
+
+int krylov_blocks(long long n) {
+  long long b = (n + NT - 1) / NT;
+  return (int)(b < 608 ? (b < 1 ? 1 : b) : 608);
+}
+
+cudaError_t launch_multidot(long long n, int k, const cplx* V, long long ld, const cplx* w, cplx* partial,
+                            int nblk, cudaStream_t st) {
+  k_multidot<<<dim3(nblk, k), NT, 0, st>>>(n, V, ld, w, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_dots(int nblk, int k, const cplx* partial, cplx* out, cplx* acc_into, cudaStream_t st) {
+  k_reduce_dots<<<k, NT, 0, st>>>(nblk, partial, out, acc_into);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multiaxpy(long long n, int k, const cplx* V, long long ld, const cplx* coef, double sgn,
+                             cplx* w, double* norm_part, int nblk, cudaStream_t st) {
+  k_multiaxpy<<<nblk, NT, 0, st>>>(n, k, V, ld, coef, sgn, w, norm_part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_by_norm(long long n, const cplx* w, cplx* out, const double* norm2, cplx* store,
+                                 int nblk, cudaStream_t st) {
+  k_scale_by_norm<<<nblk, NT, 0, st>>>(n, w, out, norm2, store);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_givens(int j, int m, cplx* H, cplx* cs, cplx* sn, cplx* g, double* est, cudaStream_t st) {
+  k_givens<<<1, 32, 0, st>>>(j, m, H, cs, sn, g, est);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hess_solve(int k, int m, const cplx* H, const cplx* g, cplx* y, cudaStream_t st) {
+  k_hess_solve<<<1, 32, 0, st>>>(k, m, H, g, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_c(int n, cplx* a, cudaStream_t st) {
+  k_zero_c<<<(n + 255) / 256, 256, 0, st>>>(n, a);
+  return cudaGetLastError();
+}

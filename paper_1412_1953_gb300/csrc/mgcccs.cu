@@ -1,0 +1,628 @@
+// Host side of the MG-CCCS library: workspace layout, setup sequence, V-cycle
+// recursion, CCCS sequence, solve loop and the C ABI declared in include/mgcccs.h.
+// Every numerical step runs in the kernels of kernels_*.cu; this file only orders
+// launches on the handle's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace {
+
+struct LevelBufs {
+  int nxc, nyc;            // cells
+  int mx, my;              // interior nodes
+  double gamma;            // contour rotation of this level
+  cplx *west_x, *east_x, *diag_x, *w_x;
+  cplx *west_y, *east_y, *diag_y, *w_y;
+  cplx *D, *Dinv;
+  cplx *u, *f, *t, *r;     // level 0: only t, r (u and f belong to the caller)
+  StencilView sv;
+};
+
+}  // namespace
+
+struct mgcccs_handle {
+  mgcccs_params p;
+  cudaStream_t st;
+  int L;
+  LevelBufs lv[MGC_MAX_LEVELS];
+  int nc;
+  cplx* Ainv;
+  cplx* aug;
+  int nb;
+  cplx *lam, *mu, *phi, *vphi, *wphi, *wvphi, *VA, *VB, *GA, *GB;
+  cplx* eig_scratch;
+  CCView cc;
+  double* norm_part;
+  int norm_nparts;
+  double* norm_out;
+  int* status;
+  cplx *hu, *hf;
+  // GMRES(m) outer solver
+  int km;
+  int kr_nblk;
+  cplx *V, *Z, *Hh, *cs, *sn, *g, *y, *hc, *dotpart;
+  long long launches;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+// Two-pass workspace carving: with base == nullptr only the size is accumulated.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + kAlign - 1) / kAlign * kAlign;
+    T* ptr = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return ptr;
+  }
+};
+
+bool valid_params(const mgcccs_params* p) {
+  if (!p) return false;
+  if (p->levels < 1 || p->levels > MGC_MAX_LEVELS) return false;
+  if (p->nx < 2 || p->ny < 2) return false;
+  const int s = 1 << (p->levels - 1);
+  if (p->nx % s || p->ny % s) return false;
+  const int cx = p->nx / s, cy = p->ny / s;
+  if (cx < 2 || cy < 2) return false;
+  if ((long long)(cx - 1) * (cy - 1) > MGC_MAX_COARSE) return false;
+  if (p->n_b < 0 || p->n_b > MGC_MAX_NB || p->n_b > p->nx - 1 || p->n_b > p->ny - 1) return false;
+  if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 > 64) return false;
+  if (!(p->Lx > 0) || !(p->Ly > 0) || !std::isfinite(p->E) || !std::isfinite(p->omega)) return false;
+  if (!std::isfinite(p->theta) || !std::isfinite(p->coarse_gamma)) return false;
+  if (p->krylov_restart < 0 || p->krylov_restart > MGC_MAX_RESTART) return false;
+  return true;
+}
+
+void layout(mgcccs_handle* h, Carver& cv) {
+  const mgcccs_params& p = h->p;
+  const int L = p.levels;
+  for (int l = 0; l < L; ++l) {
+    LevelBufs& b = h->lv[l];
+    b.nxc = p.nx >> l;
+    b.nyc = p.ny >> l;
+    b.mx = b.nxc - 1;
+    b.my = b.nyc - 1;
+    const size_t n2 = (size_t)b.mx * b.my;
+    b.west_x = cv.take<cplx>(b.mx); b.east_x = cv.take<cplx>(b.mx);
+    b.diag_x = cv.take<cplx>(b.mx); b.w_x = cv.take<cplx>(b.mx);
+    b.west_y = cv.take<cplx>(b.my); b.east_y = cv.take<cplx>(b.my);
+    b.diag_y = cv.take<cplx>(b.my); b.w_y = cv.take<cplx>(b.my);
+    b.D = cv.take<cplx>(n2);
+    b.Dinv = cv.take<cplx>(n2);
+    b.t = cv.take<cplx>(n2);
+    b.r = cv.take<cplx>(n2);
+    if (l > 0) {
+      b.u = cv.take<cplx>(n2);
+      b.f = cv.take<cplx>(n2);
+    } else {
+      b.u = b.f = nullptr;
+    }
+  }
+  const LevelBufs& c = h->lv[L - 1];
+  h->nc = c.mx * c.my;
+  h->Ainv = cv.take<cplx>((size_t)h->nc * h->nc);
+  h->aug = cv.take<cplx>((size_t)h->nc * 2 * h->nc);
+  const int nb = p.n_b, mx = h->lv[0].mx, my = h->lv[0].my;
+  h->nb = nb;
+  if (nb > 0) {
+    h->lam = cv.take<cplx>(nb);
+    h->mu = cv.take<cplx>(nb);
+    h->phi = cv.take<cplx>((size_t)nb * mx);
+    h->vphi = cv.take<cplx>((size_t)nb * my);
+    h->wphi = cv.take<cplx>((size_t)nb * mx);
+    h->wvphi = cv.take<cplx>((size_t)nb * my);
+    h->VA = cv.take<cplx>((size_t)my * nb * nb);
+    h->VB = cv.take<cplx>((size_t)mx * nb * nb);
+    h->GA = cv.take<cplx>((size_t)my * nb * nb);
+    h->GB = cv.take<cplx>((size_t)mx * nb * nb);
+    size_t es = bound_states_scratch(mx > my ? mx : my, nb);
+    h->eig_scratch = cv.take<cplx>((es + sizeof(cplx) - 1) / sizeof(cplx));
+    CCView& cc = h->cc;
+    cc.mx = mx; cc.my = my; cc.nb = nb;
+    cc.wphi = h->wphi; cc.wvphi = h->wvphi; cc.phi = h->phi; cc.vphi = h->vphi;
+    cc.Px_part = cv.take<cplx>((size_t)cc_tiles_x(mx) * nb * my);
+    cc.Py_part = cv.take<cplx>((size_t)cc_tiles_y(my) * nb * mx);
+    cc.Px = cv.take<cplx>((size_t)nb * my);
+    cc.Py = cv.take<cplx>((size_t)nb * mx);
+    cc.c = cv.take<cplx>((size_t)nb * nb);
+    cc.rA = cv.take<cplx>((size_t)nb * my);
+    cc.rB = cv.take<cplx>((size_t)nb * mx);
+    cc.eA = cv.take<cplx>((size_t)nb * my);
+    cc.eB = cv.take<cplx>((size_t)nb * mx);
+    cc.gA = cv.take<cplx>((size_t)nb * my);
+    cc.gB = cv.take<cplx>((size_t)nb * mx);
+    cc.GA = h->GA; cc.GB = h->GB;
+    cc.aA = h->lv[0].west_y; cc.cA = h->lv[0].east_y;
+    cc.aB = h->lv[0].west_x; cc.cB = h->lv[0].east_x;
+  }
+  StencilView s0{};
+  s0.mx = mx; s0.my = my;
+  int nparts = residual_norm_blocks(s0);
+  int n2b = norm2_blocks((long long)mx * my);
+  h->norm_nparts = nparts > n2b ? nparts : n2b;
+  const long long N = (long long)mx * my;
+  h->km = p.krylov_restart;
+  h->kr_nblk = krylov_blocks(N);
+  if (h->km > 0) {
+    const int m = h->km;
+    h->V = cv.take<cplx>((size_t)(m + 1) * N);
+    h->Z = cv.take<cplx>((size_t)m * N);
+    h->Hh = cv.take<cplx>((size_t)(m + 1) * m);
+    h->cs = cv.take<cplx>(m);
+    h->sn = cv.take<cplx>(m);
+    h->g = cv.take<cplx>(m + 1);
+    h->y = cv.take<cplx>(m);
+    h->hc = cv.take<cplx>(m + 1);
+    h->dotpart = cv.take<cplx>((size_t)(m + 1) * h->kr_nblk);
+    if (h->kr_nblk > h->norm_nparts) h->norm_nparts = h->kr_nblk;
+  }
+  h->norm_part = cv.take<double>(h->norm_nparts);
+  h->norm_out = cv.take<double>(4);
+  h->status = cv.take<int>(4);
+  h->hu = cv.take<cplx>((size_t)mx * my);
+  h->hf = cv.take<cplx>((size_t)mx * my);
+}
+
+// Number of leading interior nodes whose 3-point stencil lies on the unbent part of
+// the contour (both adjacent cells real before the level rotation).
+int uniform_count(int n, double L, double R0) {
+  int m = n - 1, cnt = 0;
+  for (int i = 0; i < m; ++i) {
+    double x = (double)(i + 2) * L / (double)n;
+    if (x <= R0) cnt = i + 1; else break;
+  }
+  return cnt;
+}
+
+#define MGC_LAUNCH(expr)                         \
+  do {                                           \
+    cudaError_t e_ = (expr);                     \
+    h->launches++;                               \
+    if (e_ != cudaSuccess) return MGCCCS_ECUDA;  \
+  } while (0)
+
+#define MGC_CUDA(expr)                           \
+  do {                                           \
+    if ((expr) != cudaSuccess) return MGCCCS_ECUDA; \
+  } while (0)
+
+int read_status(mgcccs_handle* h) {
+  int st = 0;
+  MGC_CUDA(cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  MGC_CUDA(cudaStreamSynchronize(h->st));
+  if (st & (MGC_ST_PIVOT | MGC_ST_EIG)) return MGCCCS_EBREAKDOWN;
+  if (st & MGC_ST_NONFINITE) return MGCCCS_ENONFINITE;
+  return MGCCCS_OK;
+}
+
+int do_setup(mgcccs_handle* h, const cplx* v1, const cplx* v2, const cplx* v12) {
+  const mgcccs_params& p = h->p;
+  cudaStream_t st = h->st;
+  MGC_CUDA(cudaMemsetAsync(h->status, 0, 4 * sizeof(int), st));
+  const int fine_mx = h->lv[0].mx;
+  for (int l = 0; l < h->L; ++l) {
+    LevelBufs& b = h->lv[l];
+    b.gamma = (l > 0) ? p.coarse_gamma : 0.0;
+    AxisSetup ax{b.nxc, p.Lx, p.R0x, p.theta, b.gamma, b.west_x, b.east_x, b.diag_x, b.w_x};
+    AxisSetup ay{b.nyc, p.Ly, p.R0y, p.theta, b.gamma, b.west_y, b.east_y, b.diag_y, b.w_y};
+    MGC_LAUNCH(launch_setup_axis(ax, st));
+    MGC_LAUNCH(launch_setup_axis(ay, st));
+    MGC_LAUNCH(launch_setup_diag(b.mx, b.my, 1 << l, fine_mx, b.diag_x, b.diag_y, v1, v2, v12, p.E, p.omega,
+                                 b.D, b.Dinv, h->status, st));
+    StencilView& s = b.sv;
+    s.mx = b.mx; s.my = b.my;
+    s.west_x = b.west_x; s.east_x = b.east_x; s.west_y = b.west_y; s.east_y = b.east_y;
+    s.D = b.D; s.Dinv = b.Dinv;
+    const double hx = p.Lx / b.nxc, hy = p.Ly / b.nyc;
+    if (hx == hy) {
+      s.ux = uniform_count(b.nxc, p.Lx, p.R0x);
+      s.uy = uniform_count(b.nyc, p.Ly, p.R0y);
+      // -1/(2 h^2) e^{-2 i gamma}
+      const double a = -0.5 / (hx * hx);
+      s.cu = cmk(a * std::cos(2.0 * b.gamma), -a * std::sin(2.0 * b.gamma));
+      if (s.ux == 0 || s.uy == 0) s.ux = s.uy = 0;
+    } else {
+      s.ux = s.uy = 0;
+      s.cu = cmk(0.0, 0.0);
+    }
+  }
+  MGC_LAUNCH(launch_coarse_inverse(h->lv[h->L - 1].sv, h->aug, h->Ainv, h->status, st));
+  if (h->nb > 0) {
+    const LevelBufs& b = h->lv[0];
+    const int nb = h->nb;
+    MGC_LAUNCH(launch_bound_states(b.mx, b.west_x, b.east_x, b.diag_x, v1, b.w_x, nb, h->lam, h->phi,
+                                   h->eig_scratch, h->status, st));
+    MGC_LAUNCH(launch_bound_states(b.my, b.west_y, b.east_y, b.diag_y, v2, b.w_y, nb, h->mu, h->vphi,
+                                   h->eig_scratch, h->status, st));
+    MGC_LAUNCH(launch_weight_states(b.mx, nb, b.w_x, h->phi, h->wphi, st));
+    MGC_LAUNCH(launch_weight_states(b.my, nb, b.w_y, h->vphi, h->wvphi, st));
+    MGC_LAUNCH(launch_channel_potentials(b.mx, b.my, nb, h->wphi, h->phi, h->wvphi, h->vphi, v12, h->VA, h->VB,
+                                         st));
+    // channel A runs along y with the x bound states; channel B along x with the y ones
+    MGC_LAUNCH(launch_channel_factor(b.my, nb, b.diag_y, v2, p.E, h->lam, h->VA, b.west_y, b.east_y, h->GA,
+                                     h->status, st));
+    MGC_LAUNCH(launch_channel_factor(b.mx, nb, b.diag_x, v1, p.E, h->mu, h->VB, b.west_x, b.east_x, h->GB,
+                                     h->status, st));
+  }
+  return read_status(h);
+}
+
+// One V-cycle on level l.  `u` holds the initial guess unless zero_init; the result is
+// returned in *out (either u or the level's t buffer).
+int vcycle_rec(mgcccs_handle* h, int l, cplx* u, const cplx* f, bool zero_init, cplx** out) {
+  cudaStream_t st = h->st;
+  LevelBufs& b = h->lv[l];
+  if (l == h->L - 1) {
+    MGC_LAUNCH(launch_coarse_solve(h->nc, h->Ainv, f, u, st));
+    *out = u;
+    return MGCCCS_OK;
+  }
+  cplx* cur = u;
+  cplx* oth = b.t;
+  bool zero = zero_init;
+  for (int s = 0; s < h->p.nu1; ++s) {
+    if (zero) MGC_LAUNCH(launch_jacobi_zero(b.sv, oth, f, st));
+    else MGC_LAUNCH(launch_jacobi(b.sv, cur, oth, f, st));
+    zero = false;
+    cplx* tmp = cur; cur = oth; oth = tmp;
+  }
+  if (zero) {
+    // no pre-smoothing and a zero guess: the residual is f itself
+    MGC_CUDA(cudaMemsetAsync(cur, 0, sizeof(cplx) * (size_t)b.mx * b.my, st));
+  }
+  LevelBufs& c = h->lv[l + 1];
+  MGC_LAUNCH(launch_residual(b.sv, cur, f, b.r, nullptr, st));
+  MGC_LAUNCH(launch_restrict(b.mx, b.my, b.r, c.f, st));
+  cplx* ec = nullptr;
+  int rc = vcycle_rec(h, l + 1, c.u, c.f, true, &ec);
+  if (rc) return rc;
+  MGC_LAUNCH(launch_prolong_add(b.mx, b.my, ec, cur, st));
+  for (int s = 0; s < h->p.nu2; ++s) {
+    MGC_LAUNCH(launch_jacobi(b.sv, cur, oth, f, st));
+    cplx* tmp = cur; cur = oth; oth = tmp;
+  }
+  *out = cur;
+  return MGCCCS_OK;
+}
+
+int vcycle_fine(mgcccs_handle* h, cplx* u, const cplx* f, bool zero_init) {
+  cplx* res = nullptr;
+  int rc = vcycle_rec(h, 0, u, f, zero_init, &res);
+  if (rc) return rc;
+  if (res != u) {
+    const LevelBufs& b = h->lv[0];
+    MGC_CUDA(cudaMemcpyAsync(u, res, sizeof(cplx) * (size_t)b.mx * b.my, cudaMemcpyDeviceToDevice, h->st));
+  }
+  return MGCCCS_OK;
+}
+
+int cccs_fine(mgcccs_handle* h, cplx* u, const cplx* f) {
+  cudaStream_t st = h->st;
+  MGC_LAUNCH(launch_residual_project(h->lv[0].sv, h->cc, u, f, st));
+  MGC_LAUNCH(launch_cc_rhs(h->cc, st));
+  h->launches += 2;   // launch_cc_rhs issues three kernels
+  MGC_LAUNCH(launch_channel_solve(h->cc, st));
+  MGC_LAUNCH(launch_cccs_correct(h->cc, u, st));
+  return MGCCCS_OK;
+}
+
+int residual_norm2(mgcccs_handle* h, const cplx* u, const cplx* f, cplx* r, double* norm2) {
+  cudaStream_t st = h->st;
+  const StencilView& s = h->lv[0].sv;
+  MGC_LAUNCH(launch_residual(s, u, f, r, norm2 ? h->norm_part : nullptr, st));
+  if (norm2) {
+    MGC_LAUNCH(launch_sum_partials(h->norm_part, residual_norm_blocks(s), h->norm_out, st));
+    MGC_CUDA(cudaMemcpyAsync(norm2, h->norm_out, sizeof(double), cudaMemcpyDeviceToHost, st));
+    MGC_CUDA(cudaStreamSynchronize(st));
+  }
+  return MGCCCS_OK;
+}
+
+int vec_norm2(mgcccs_handle* h, const cplx* v, double* out) {
+  cudaStream_t st = h->st;
+  long long n = (long long)h->lv[0].mx * h->lv[0].my;
+  int nbk = norm2_blocks(n);
+  MGC_LAUNCH(launch_norm2(v, n, h->norm_part, nbk, st));
+  MGC_LAUNCH(launch_sum_partials(h->norm_part, nbk, h->norm_out, st));
+  MGC_CUDA(cudaMemcpyAsync(out, h->norm_out, sizeof(double), cudaMemcpyDeviceToHost, st));
+  MGC_CUDA(cudaStreamSynchronize(st));
+  return MGCCCS_OK;
+}
+
+int read_double(mgcccs_handle* h, const double* dev, double* out) {
+  MGC_CUDA(cudaMemcpyAsync(out, dev, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  MGC_CUDA(cudaStreamSynchronize(h->st));
+  return MGCCCS_OK;
+}
+
+// z = M^{-1} r: one V-cycle from zero, then the CCCS.
+int precond(mgcccs_handle* h, cplx* z, const cplx* r) {
+  int rc = vcycle_fine(h, z, r, true);
+  if (rc) return rc;
+  if (h->nb > 0) rc = cccs_fine(h, z, r);
+  return rc;
+}
+
+// Restarted GMRES(m), right-preconditioned by one MG-CCCS iteration; Arnoldi with
+// classical Gram-Schmidt applied twice; Givens rotations and the triangular solve on
+// the device.  Counts Arnoldi steps as iterations.
+int gmres_impl(mgcccs_handle* h, cplx* u, const cplx* f, double fn, double rtol, int max_iter, int* iters,
+               double* relres, double* history) {
+  cudaStream_t st = h->st;
+  const int m = h->km;
+  const StencilView& s0 = h->lv[0].sv;
+  const long long N = (long long)s0.mx * s0.my;
+  const int nb = h->kr_nblk;
+  int steps = 0;
+  double rr = INFINITY;
+  for (;;) {
+    // true residual r = f - A u into V_0
+    MGC_LAUNCH(launch_residual(s0, u, f, h->V, h->norm_part, st));
+    MGC_LAUNCH(launch_sum_partials(h->norm_part, residual_norm_blocks(s0), h->norm_out, st));
+    double rn2 = 0.0;
+    int rc = read_double(h, h->norm_out, &rn2);
+    if (rc) return rc;
+    rr = std::sqrt(rn2) / fn;
+    if (!std::isfinite(rr)) {
+      if (iters) *iters = steps;
+      if (relres) *relres = rr;
+      return MGCCCS_ENONFINITE;
+    }
+    if (rr <= rtol || steps >= max_iter) break;
+    MGC_LAUNCH(launch_zero_c(m + 1, h->g, st));
+    MGC_LAUNCH(launch_scale_by_norm(N, h->V, h->V, h->norm_out, h->g, nb, st));
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      cplx* vj = h->V + (size_t)j * N;
+      cplx* w = h->V + (size_t)(j + 1) * N;
+      cplx* zj = h->Z + (size_t)j * N;
+      cplx* col = h->Hh + (size_t)j * (m + 1);
+      rc = precond(h, zj, vj);
+      if (rc) return rc;
+      MGC_LAUNCH(launch_apply(s0, zj, w, st));
+      // Gram-Schmidt, first pass: H(0:j, j) = V^H w ; w -= V H(0:j, j)
+      MGC_LAUNCH(launch_multidot(N, j + 1, h->V, N, w, h->dotpart, nb, st));
+      MGC_LAUNCH(launch_reduce_dots(nb, j + 1, h->dotpart, col, nullptr, st));
+      MGC_LAUNCH(launch_multiaxpy(N, j + 1, h->V, N, col, -1.0, w, nullptr, nb, st));
+      // second pass: corrections added into H(0:j, j); |w|^2 partials for h_{j+1,j}
+      MGC_LAUNCH(launch_multidot(N, j + 1, h->V, N, w, h->dotpart, nb, st));
+      MGC_LAUNCH(launch_reduce_dots(nb, j + 1, h->dotpart, h->hc, col, st));
+      MGC_LAUNCH(launch_multiaxpy(N, j + 1, h->V, N, h->hc, -1.0, w, h->norm_part, nb, st));
+      MGC_LAUNCH(launch_sum_partials(h->norm_part, nb, h->norm_out + 1, st));
+      MGC_LAUNCH(launch_scale_by_norm(N, w, w, h->norm_out + 1, col + j + 1, nb, st));
+      MGC_LAUNCH(launch_givens(j, m, h->Hh, h->cs, h->sn, h->g, h->norm_out + 2, st));
+      double est = 0.0;
+      rc = read_double(h, h->norm_out + 2, &est);
+      if (rc) return rc;
+      est /= fn;
+      if (history) history[steps] = est;
+      ++steps;
+      k = j + 1;
+      if (!std::isfinite(est)) {
+        if (iters) *iters = steps;
+        if (relres) *relres = est;
+        return MGCCCS_ENONFINITE;
+      }
+      if (est <= rtol || steps >= max_iter) break;
+    }
+    MGC_LAUNCH(launch_hess_solve(k, m, h->Hh, h->g, h->y, st));
+    MGC_LAUNCH(launch_multiaxpy(N, k, h->Z, N, h->y, 1.0, u, nullptr, nb, st));
+  }
+  if (iters) *iters = steps;
+  if (relres) *relres = rr;
+  return rr <= rtol ? MGCCCS_OK : MGCCCS_ENOTCONV;
+}
+
+int solve_impl(mgcccs_handle* h, cplx* u, const cplx* f, double rtol, int max_iter, int* iters, double* relres,
+               double* history) {
+  if (max_iter < 1) return MGCCCS_EINVAL;
+  double fn2 = 0.0;
+  int rc = vec_norm2(h, f, &fn2);
+  if (rc) return rc;
+  if (fn2 == 0.0) {
+    MGC_CUDA(cudaMemsetAsync(u, 0, sizeof(cplx) * (size_t)h->lv[0].mx * h->lv[0].my, h->st));
+    MGC_CUDA(cudaStreamSynchronize(h->st));
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    return MGCCCS_OK;
+  }
+  if (h->km > 0) return gmres_impl(h, u, f, std::sqrt(fn2), rtol, max_iter, iters, relres, history);
+  double rr = INFINITY;
+  int it = 0;
+  for (it = 1; it <= max_iter; ++it) {
+    rc = vcycle_fine(h, u, f, false);
+    if (rc) return rc;
+    if (h->nb > 0) {
+      rc = cccs_fine(h, u, f);
+      if (rc) return rc;
+    }
+    double rn2 = 0.0;
+    rc = residual_norm2(h, u, f, nullptr, &rn2);
+    if (rc) return rc;
+    rr = std::sqrt(rn2 / fn2);
+    if (history) history[it - 1] = rr;
+    if (!std::isfinite(rr)) {
+      if (iters) *iters = it;
+      if (relres) *relres = rr;
+      return MGCCCS_ENONFINITE;
+    }
+    if (rr <= rtol) break;
+  }
+  if (it > max_iter) it = max_iter;
+  if (iters) *iters = it;
+  if (relres) *relres = rr;
+  return rr <= rtol ? MGCCCS_OK : MGCCCS_ENOTCONV;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t mgcccs_workspace_size(const mgcccs_params* p) {
+  if (!valid_params(p)) return 0;
+  mgcccs_handle* h = new (std::nothrow) mgcccs_handle();
+  if (!h) return 0;
+  h->p = *p;
+  h->L = p->levels;
+  Carver cv{nullptr};
+  layout(h, cv);
+  delete h;
+  return cv.off + kAlign;
+}
+
+int mgcccs_setup(mgcccs_t* out, const mgcccs_params* p, const mgcccs_c128* v1, const mgcccs_c128* v2,
+                 const mgcccs_c128* v12, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!out || !valid_params(p) || !v1 || !v2 || !v12 || !workspace) return MGCCCS_EINVAL;
+  *out = nullptr;
+  size_t need = mgcccs_workspace_size(p);
+  if (workspace_bytes < need) return MGCCCS_ENOSPACE;
+  if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return MGCCCS_EINVAL;
+  mgcccs_handle* h = new (std::nothrow) mgcccs_handle();
+  if (!h) return MGCCCS_EINVAL;
+  h->p = *p;
+  h->L = p->levels;
+  h->st = reinterpret_cast<cudaStream_t>(stream);
+  Carver cv{reinterpret_cast<char*>(workspace)};
+  layout(h, cv);
+  int rc = do_setup(h, reinterpret_cast<const cplx*>(v1), reinterpret_cast<const cplx*>(v2),
+                    reinterpret_cast<const cplx*>(v12));
+  if (rc) {
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return MGCCCS_OK;
+}
+
+int mgcccs_vcycle(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f) {
+  if (!h || !u || !f) return MGCCCS_EINVAL;
+  return vcycle_fine(h, reinterpret_cast<cplx*>(u), reinterpret_cast<const cplx*>(f), false);
+}
+
+int mgcccs_cccs(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f) {
+  if (!h || !u || !f || h->nb <= 0) return MGCCCS_EINVAL;
+  return cccs_fine(h, reinterpret_cast<cplx*>(u), reinterpret_cast<const cplx*>(f));
+}
+
+int mgcccs_solve(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f, double rtol, int max_iter, int* iters,
+                 double* relres, double* history) {
+  if (!h || !u || !f) return MGCCCS_EINVAL;
+  return solve_impl(h, reinterpret_cast<cplx*>(u), reinterpret_cast<const cplx*>(f), rtol, max_iter, iters, relres,
+                    history);
+}
+
+int mgcccs_solve_host(mgcccs_t h, mgcccs_c128* u_host, const mgcccs_c128* f_host, double rtol, int max_iter,
+                      int* iters, double* relres) {
+  if (!h || !u_host || !f_host) return MGCCCS_EINVAL;
+  const size_t bytes = sizeof(cplx) * (size_t)h->lv[0].mx * h->lv[0].my;
+  MGC_CUDA(cudaMemcpyAsync(h->hf, f_host, bytes, cudaMemcpyHostToDevice, h->st));
+  MGC_CUDA(cudaMemcpyAsync(h->hu, u_host, bytes, cudaMemcpyHostToDevice, h->st));
+  int rc = solve_impl(h, h->hu, h->hf, rtol, max_iter, iters, relres, nullptr);
+  if (rc && rc != MGCCCS_ENOTCONV) return rc;
+  MGC_CUDA(cudaMemcpyAsync(u_host, h->hu, bytes, cudaMemcpyDeviceToHost, h->st));
+  MGC_CUDA(cudaStreamSynchronize(h->st));
+  return rc;
+}
+
+int mgcccs_precond_apply(mgcccs_t h, mgcccs_c128* z, const mgcccs_c128* r) {
+  if (!h || !z || !r || (const void*)z == (const void*)r) return MGCCCS_EINVAL;
+  return precond(h, reinterpret_cast<cplx*>(z), reinterpret_cast<const cplx*>(r));
+}
+
+int mgcccs_matvec(mgcccs_t h, const mgcccs_c128* x, mgcccs_c128* y) {
+  if (!h || !x || !y || (const void*)x == (const void*)y) return MGCCCS_EINVAL;
+  MGC_LAUNCH(launch_apply(h->lv[0].sv, reinterpret_cast<const cplx*>(x), reinterpret_cast<cplx*>(y), h->st));
+  return MGCCCS_OK;
+}
+
+int mgcccs_residual(mgcccs_t h, const mgcccs_c128* u, const mgcccs_c128* f, mgcccs_c128* r, double* norm2) {
+  if (!h || !u || !f || !r || (const void*)r == (const void*)u) return MGCCCS_EINVAL;
+  return residual_norm2(h, reinterpret_cast<const cplx*>(u), reinterpret_cast<const cplx*>(f),
+                        reinterpret_cast<cplx*>(r), norm2);
+}
+
+int mgcccs_smooth(mgcccs_t h, int level, mgcccs_c128* u, const mgcccs_c128* f, int sweeps) {
+  if (!h || !u || !f || level < 0 || level >= h->L || sweeps < 0) return MGCCCS_EINVAL;
+  LevelBufs& b = h->lv[level];
+  cplx* uu = reinterpret_cast<cplx*>(u);
+  cplx* cur = uu;
+  cplx* oth = b.t;
+  for (int s = 0; s < sweeps; ++s) {
+    MGC_LAUNCH(launch_jacobi(b.sv, cur, oth, reinterpret_cast<const cplx*>(f), h->st));
+    cplx* tmp = cur; cur = oth; oth = tmp;
+  }
+  if (cur != uu)
+    MGC_CUDA(cudaMemcpyAsync(uu, cur, sizeof(cplx) * (size_t)b.mx * b.my, cudaMemcpyDeviceToDevice, h->st));
+  return MGCCCS_OK;
+}
+
+int mgcccs_level_residual(mgcccs_t h, int level, const mgcccs_c128* u, const mgcccs_c128* f, mgcccs_c128* r) {
+  if (!h || !u || !f || !r || level < 0 || level >= h->L) return MGCCCS_EINVAL;
+  MGC_LAUNCH(launch_residual(h->lv[level].sv, reinterpret_cast<const cplx*>(u), reinterpret_cast<const cplx*>(f),
+                             reinterpret_cast<cplx*>(r), nullptr, h->st));
+  return MGCCCS_OK;
+}
+
+int mgcccs_restrict(mgcccs_t h, int level, const mgcccs_c128* r, mgcccs_c128* rc) {
+  if (!h || !r || !rc || level < 0 || level + 1 >= h->L) return MGCCCS_EINVAL;
+  MGC_LAUNCH(launch_restrict(h->lv[level].mx, h->lv[level].my, reinterpret_cast<const cplx*>(r),
+                             reinterpret_cast<cplx*>(rc), h->st));
+  return MGCCCS_OK;
+}
+
+int mgcccs_prolong_add(mgcccs_t h, int level, const mgcccs_c128* ec, mgcccs_c128* u) {
+  if (!h || !ec || !u || level < 0 || level + 1 >= h->L) return MGCCCS_EINVAL;
+  MGC_LAUNCH(launch_prolong_add(h->lv[level].mx, h->lv[level].my, reinterpret_cast<const cplx*>(ec),
+                                reinterpret_cast<cplx*>(u), h->st));
+  return MGCCCS_OK;
+}
+
+int mgcccs_coarse_solve(mgcccs_t h, const mgcccs_c128* f, mgcccs_c128* u) {
+  if (!h || !f || !u) return MGCCCS_EINVAL;
+  MGC_LAUNCH(launch_coarse_solve(h->nc, h->Ainv, reinterpret_cast<const cplx*>(f), reinterpret_cast<cplx*>(u),
+                                 h->st));
+  return MGCCCS_OK;
+}
+
+int mgcccs_get_bound_states(mgcccs_t h, mgcccs_c128* lambda, mgcccs_c128* phi, mgcccs_c128* mu,
+                            mgcccs_c128* vphi) {
+  if (!h || h->nb <= 0) return MGCCCS_EINVAL;
+  const int nb = h->nb;
+  cudaStream_t st = h->st;
+  if (lambda) MGC_CUDA(cudaMemcpyAsync(lambda, h->lam, sizeof(cplx) * nb, cudaMemcpyDeviceToHost, st));
+  if (mu) MGC_CUDA(cudaMemcpyAsync(mu, h->mu, sizeof(cplx) * nb, cudaMemcpyDeviceToHost, st));
+  if (phi)
+    MGC_CUDA(cudaMemcpyAsync(phi, h->phi, sizeof(cplx) * nb * h->lv[0].mx, cudaMemcpyDeviceToDevice, st));
+  if (vphi)
+    MGC_CUDA(cudaMemcpyAsync(vphi, h->vphi, sizeof(cplx) * nb * h->lv[0].my, cudaMemcpyDeviceToDevice, st));
+  MGC_CUDA(cudaStreamSynchronize(st));
+  return MGCCCS_OK;
+}
+
+long long mgcccs_launch_count(mgcccs_t h) { return h ? h->launches : -1; }
+
+const char* mgcccs_strerror(int code) {
+  switch (code) {
+    case MGCCCS_OK: return "ok";
+    case MGCCCS_EINVAL: return "invalid argument (sizes, levels, n_b, null or misaligned pointer)";
+    case MGCCCS_ECUDA: return "CUDA runtime error or kernel launch failure";
+    case MGCCCS_ENOSPACE: return "workspace smaller than mgcccs_workspace_size()";
+    case MGCCCS_EBREAKDOWN: return "zero pivot or eigen-solve breakdown during setup";
+    case MGCCCS_ENONFINITE: return "residual is not finite";
+    case MGCCCS_ENOTCONV: return "max_iter reached before rtol";
+  }
+  return "unknown error code";
+}
+
+void mgcccs_destroy(mgcccs_t h) { delete h; }
+
+}  // extern "C"

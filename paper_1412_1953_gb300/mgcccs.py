@@ -1,0 +1,255 @@
+"""Thin Python binding of the MG-CCCS C ABI (include/mgcccs.h).
+
+Argument marshalling only: every numerical step runs in the CUDA library
+``_lib/libmgcccs.so``.  PyTorch supplies device memory and the stream.  There is
+no CPU path: if the library is missing or no GPU is present, calls raise.
+
+The module-level functions carry the C names (``mgcccs_setup``, ``mgcccs_vcycle``,
+...); ``Solver`` bundles a handle with its workspace tensor.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+HEADER = os.path.join(_build.ROOT, "include", "mgcccs.h")
+
+OK, EINVAL, ECUDA, ENOSPACE, EBREAKDOWN, ENONFINITE, ENOTCONV = 0, -1, -2, -3, -4, -5, -6
+
+
+class MGCCCSError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {mgcccs_strerror(code)} (code {code})")
+
+
+class mgcccs_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("Lx", ctypes.c_double), ("Ly", ctypes.c_double),
+                ("R0x", ctypes.c_double), ("R0y", ctypes.c_double),
+                ("theta", ctypes.c_double), ("E", ctypes.c_double),
+                ("levels", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("omega", ctypes.c_double), ("n_b", ctypes.c_int),
+                ("coarse_gamma", ctypes.c_double), ("krylov_restart", ctypes.c_int)]
+
+
+COARSE_GAMMA_DEFAULT = 14.6 * math.pi / 180.0
+
+_LIB = None
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+_SIGS = {
+    "mgcccs_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(mgcccs_params)]),
+    "mgcccs_setup": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(mgcccs_params), _vp, _vp, _vp, _vp,
+                          ctypes.c_size_t, _vp]),
+    "mgcccs_vcycle": (_i, [_vp, _vp, _vp]),
+    "mgcccs_cccs": (_i, [_vp, _vp, _vp]),
+    "mgcccs_solve": (_i, [_vp, _vp, _vp, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d), _vp]),
+    "mgcccs_solve_host": (_i, [_vp, _vp, _vp, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
+    "mgcccs_precond_apply": (_i, [_vp, _vp, _vp]),
+    "mgcccs_residual": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(_d)]),
+    "mgcccs_matvec": (_i, [_vp, _vp, _vp]),
+    "mgcccs_smooth": (_i, [_vp, _i, _vp, _vp, _i]),
+    "mgcccs_level_residual": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "mgcccs_restrict": (_i, [_vp, _i, _vp, _vp]),
+    "mgcccs_prolong_add": (_i, [_vp, _i, _vp, _vp]),
+    "mgcccs_coarse_solve": (_i, [_vp, _vp, _vp]),
+    "mgcccs_get_bound_states": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "mgcccs_launch_count": (ctypes.c_longlong, [_vp]),
+    "mgcccs_strerror": (ctypes.c_char_p, [_i]),
+    "mgcccs_destroy": (None, [_vp]),
+}
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/mgcccs.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mgcccs_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib():
+    """Load the compiled library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(_build.LIB_PATH):
+            raise RuntimeError(f"MG-CCCS CUDA library missing at {_build.LIB_PATH}; "
+                               "build it with paper_1412_1953_gb300.build.build()")
+        L = ctypes.CDLL(_build.LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def mgcccs_strerror(code: int) -> str:
+    return lib().mgcccs_strerror(int(code)).decode()
+
+
+def _check(code: int, where: str) -> int:
+    if code != OK:
+        raise MGCCCSError(code, where)
+    return code
+
+
+def make_params(nx, ny, Lx, Ly, R0x, R0y, theta, E, levels=5, nu1=1, nu2=1, omega=2.0 / 3.0, n_b=3,
+                coarse_gamma=COARSE_GAMMA_DEFAULT, krylov_restart=0) -> mgcccs_params:
+    return mgcccs_params(int(nx), int(ny), float(Lx), float(Ly), float(R0x), float(R0y), float(theta),
+                         float(E), int(levels), int(nu1), int(nu2), float(omega), int(n_b), float(coarse_gamma),
+                         int(krylov_restart))
+
+
+def params_for(prob, **kw) -> mgcccs_params:
+    return make_params(prob.nx, prob.ny, prob.Lx, prob.Ly, prob.R0x, prob.R0y, prob.theta, prob.E, **kw)
+
+
+def mgcccs_workspace_size(p: mgcccs_params) -> int:
+    return int(lib().mgcccs_workspace_size(ctypes.byref(p)))
+
+
+def _ptr(t) -> int:
+    return t.data_ptr()
+
+
+def _dev_c128(t, n: int, name: str):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.complex128 or not t.is_cuda:
+        raise TypeError(f"{name} must be a complex128 CUDA tensor")
+    if not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name} must be contiguous with {n} elements")
+    return t
+
+
+class Solver:
+    """A setup handle plus its workspace.  u, f, r, z are complex128 CUDA tensors of
+    shape (ny-1, nx-1) (or any contiguous shape with that many elements)."""
+
+    def __init__(self, p: mgcccs_params, v1, v2, v12, stream=None):
+        import torch
+        self.p = p
+        self.mx, self.my = p.nx - 1, p.ny - 1
+        self.n = self.mx * self.my
+        dev = torch.device("cuda", torch.cuda.current_device())
+        as_dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.complex128).to(dev) \
+            if not isinstance(a, torch.Tensor) else a.to(dev, torch.complex128).contiguous()
+        v1d, v2d, v12d = as_dev(v1), as_dev(v2), as_dev(v12)
+        _dev_c128(v1d, self.mx, "v1"), _dev_c128(v2d, self.my, "v2"), _dev_c128(v12d, self.n, "v12")
+        nbytes = mgcccs_workspace_size(p)
+        if nbytes == 0:
+            raise MGCCCSError(EINVAL, "mgcccs_workspace_size")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        h = ctypes.c_void_p()
+        _check(lib().mgcccs_setup(ctypes.byref(h), ctypes.byref(p), _ptr(v1d), _ptr(v2d), _ptr(v12d),
+                                  self._ws_ptr, nbytes, self.stream.cuda_stream), "mgcccs_setup")
+        self.h = h
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mgcccs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _f(self, t, name="array", n=None):
+        return _ptr(_dev_c128(t, self.n if n is None else n, name))
+
+    # -- hot path
+    def vcycle(self, u, f):
+        _check(lib().mgcccs_vcycle(self.h, self._f(u, "u"), self._f(f, "f")), "mgcccs_vcycle")
+
+    def cccs(self, u, f):
+        _check(lib().mgcccs_cccs(self.h, self._f(u, "u"), self._f(f, "f")), "mgcccs_cccs")
+
+    def precond_apply(self, z, r):
+        _check(lib().mgcccs_precond_apply(self.h, self._f(z, "z"), self._f(r, "r")), "mgcccs_precond_apply")
+
+    def solve(self, u, f, rtol=1e-10, max_iter=1000, history=False, raise_on_notconv=True):
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        hist = np.zeros(max_iter) if history else None
+        code = lib().mgcccs_solve(self.h, self._f(u, "u"), self._f(f, "f"), float(rtol), int(max_iter),
+                                  ctypes.byref(it), ctypes.byref(rr),
+                                  hist.ctypes.data if hist is not None else None)
+        if code != OK and not (code == ENOTCONV and not raise_on_notconv):
+            raise MGCCCSError(code, "mgcccs_solve")
+        out = (it.value, rr.value)
+        if history:
+            out = out + (hist[: it.value].copy(),)
+        return out
+
+    def solve_host(self, u: np.ndarray, f: np.ndarray, rtol=1e-10, max_iter=1000):
+        """End-to-end call with host arrays (complex128, C-contiguous); u is updated in place."""
+        if u.dtype != np.complex128 or f.dtype != np.complex128 or not u.flags.c_contiguous \
+                or not f.flags.c_contiguous or u.size != self.n or f.size != self.n:
+            raise ValueError("u and f must be C-contiguous complex128 arrays of the grid size")
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        _check(lib().mgcccs_solve_host(self.h, u.ctypes.data, f.ctypes.data, float(rtol), int(max_iter),
+                                       ctypes.byref(it), ctypes.byref(rr)), "mgcccs_solve_host")
+        return it.value, rr.value
+
+    def residual(self, u, f, r, norm=False):
+        n2 = ctypes.c_double(0.0)
+        _check(lib().mgcccs_residual(self.h, self._f(u, "u"), self._f(f, "f"), self._f(r, "r"),
+                                     ctypes.byref(n2) if norm else None), "mgcccs_residual")
+        return n2.value if norm else None
+
+    def matvec(self, x, y):
+        _check(lib().mgcccs_matvec(self.h, self._f(x, "x"), self._f(y, "y")), "mgcccs_matvec")
+
+    # -- single steps
+    def level_size(self, level: int) -> int:
+        return ((self.p.nx >> level) - 1) * ((self.p.ny >> level) - 1)
+
+    def smooth(self, level, u, f, sweeps=1):
+        n = self.level_size(level)
+        _check(lib().mgcccs_smooth(self.h, level, self._f(u, "u", n), self._f(f, "f", n), sweeps), "mgcccs_smooth")
+
+    def level_residual(self, level, u, f, r):
+        n = self.level_size(level)
+        _check(lib().mgcccs_level_residual(self.h, level, self._f(u, "u", n), self._f(f, "f", n),
+                                           self._f(r, "r", n)), "mgcccs_level_residual")
+
+    def restrict(self, level, r, rc):
+        _check(lib().mgcccs_restrict(self.h, level, self._f(r, "r", self.level_size(level)),
+                                     self._f(rc, "rc", self.level_size(level + 1))), "mgcccs_restrict")
+
+    def prolong_add(self, level, ec, u):
+        _check(lib().mgcccs_prolong_add(self.h, level, self._f(ec, "ec", self.level_size(level + 1)),
+                                        self._f(u, "u", self.level_size(level))), "mgcccs_prolong_add")
+
+    def coarse_solve(self, f, u):
+        n = self.level_size(self.p.levels - 1)
+        _check(lib().mgcccs_coarse_solve(self.h, self._f(f, "f", n), self._f(u, "u", n)), "mgcccs_coarse_solve")
+
+    def bound_states(self):
+        import torch
+        nb = self.p.n_b
+        lam = np.zeros(nb, dtype=np.complex128)
+        mu = np.zeros(nb, dtype=np.complex128)
+        dev = self.workspace.device
+        phi = torch.empty((nb, self.mx), dtype=torch.complex128, device=dev)
+        vphi = torch.empty((nb, self.my), dtype=torch.complex128, device=dev)
+        _check(lib().mgcccs_get_bound_states(self.h, lam.ctypes.data, phi.data_ptr(), mu.ctypes.data,
+                                             vphi.data_ptr()), "mgcccs_get_bound_states")
+        return lam, phi, mu, vphi
+
+    def launch_count(self) -> int:
+        return int(lib().mgcccs_launch_count(self.h))

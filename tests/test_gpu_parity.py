@@ -1,0 +1,299 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle, step by step
+and end to end, on seeded TP/ECS problems.  Tolerances: 1e-13 relative for single
+linear steps, 1e-12 for a V-cycle / CCCS / the first iterates (accumulated rounding of
+two different operation orders), relres <= 1e-10 for solves with the GPU solution
+re-checked by the oracle's operator."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mgcccs_oracle as O
+from paper_1412_1953_gb300 import build, inputs
+from paper_1412_1953_gb300 import mgcccs as M
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+
+
+def tp_small(n, E=0.5, seed=0, ny=None):
+    L = 30.0 * n / 128
+    return inputs.temkin_poet(n, L=L, R0=2 * L / 3, theta=math.pi / 6, E=E, seed=seed, ny=ny)
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a)).to("cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def pair(prob, levels, n_b, **kw):
+    po = O.params_from_problem(prob, levels=levels, n_b=n_b, **kw)
+    so = O.Solver(po, prob.v1, prob.v2, prob.v12)
+    pg = M.params_for(prob, levels=levels, n_b=n_b, **kw)
+    sg = M.Solver(pg, prob.v1, prob.v2, prob.v12)
+    return so, sg
+
+
+def rand_c(shape, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+# ------------------------------------------------------------------ single steps
+
+@pytest.mark.parametrize("level", [0, 1, 2])
+def test_level_steps_match_oracle(level):
+    prob = tp_small(64)
+    so, sg = pair(prob, 4, 3)
+    lev = so.levels[level]
+    shape = lev.shape
+    u, f = rand_c(shape, 1 + level), rand_c(shape, 11 + level)
+    # omega-Jacobi, one and two sweeps
+    for sweeps in (1, 2):
+        ud = dev(u)
+        sg.smooth(level, ud, dev(f), sweeps)
+        assert rel(host(ud), O.jacobi(lev, u, f, 2.0 / 3.0, sweeps)) <= 1e-13
+    # residual
+    rd = torch.empty_like(dev(u))
+    sg.level_residual(level, dev(u), dev(f), rd)
+    assert rel(host(rd), O.residual(lev, u, f)) <= 1e-13
+    # full weighting and bilinear interpolation + add
+    cshape = so.levels[level + 1].shape
+    rc = torch.empty(cshape, dtype=torch.complex128, device="cuda")
+    sg.restrict(level, dev(u), rc)
+    assert rel(host(rc), O.restrict_fw(u)) <= 1e-14
+    ec = rand_c(cshape, 21 + level)
+    ud = dev(u)
+    sg.prolong_add(level, dev(ec), ud)
+    assert rel(host(ud), u + O.prolong_bilinear(ec, shape)) <= 1e-14
+
+
+def test_coarse_solve_matches_dense_solve():
+    prob = tp_small(64)
+    so, sg = pair(prob, 4, 0)
+    lev = so.levels[-1]
+    f = rand_c(lev.shape, 5)
+    ud = torch.empty_like(dev(f))
+    sg.coarse_solve(dev(f), ud)
+    ref = np.linalg.solve(O.assemble_unweighted(lev).toarray(), f.ravel()).reshape(f.shape)
+    assert rel(host(ud), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("n,nb", [(64, 3), (128, 3), (128, 6)])
+def test_bound_states_match_oracle(n, nb):
+    prob = tp_small(n) if n == 64 else inputs.temkin_poet(n)
+    so, sg = pair(prob, 3, nb)
+    lam, phi, mu, vphi = sg.bound_states()
+    np.testing.assert_allclose(lam, so.ch.lam, rtol=0, atol=1e-12 * np.abs(so.ch.lam).max())
+    np.testing.assert_allclose(mu, so.ch.mu, rtol=0, atol=1e-12 * np.abs(so.ch.mu).max())
+    assert rel(host(phi).T, so.ch.phi) <= 1e-10
+    assert rel(host(vphi).T, so.ch.vphi) <= 1e-10
+
+
+# ------------------------------------------------------------------ cycle, correction, iterates
+
+def test_vcycle_matches_oracle():
+    prob = tp_small(64, seed=3)
+    so, sg = pair(prob, 4, 3)
+    u = rand_c(so.levels[0].shape, 7)
+    ud = dev(u)
+    sg.vcycle(ud, dev(prob.f))
+    assert rel(host(ud), so.vcycle(u, prob.f)) <= 1e-12
+
+
+@pytest.mark.parametrize("nb", [1, 3, 6])
+def test_cccs_matches_oracle(nb):
+    prob = tp_small(64, seed=4)
+    so, sg = pair(prob, 4, nb)
+    u = rand_c(so.levels[0].shape, 8)
+    ud = dev(u)
+    sg.cccs(ud, dev(prob.f))
+    assert rel(host(ud), so.cccs(u, prob.f)) <= 1e-11
+
+
+def test_precond_apply_matches_oracle():
+    prob = tp_small(64, seed=5)
+    so, sg = pair(prob, 4, 3)
+    r = rand_c(so.levels[0].shape, 9)
+    zd = torch.zeros_like(dev(r))
+    sg.precond_apply(zd, dev(r))
+    assert rel(host(zd), so.precond_apply(r)) <= 1e-12
+
+
+def test_first_iterates_match_oracle():
+    prob = inputs.temkin_poet(128)
+    so, sg = pair(prob, 5, 3)
+    u = np.zeros_like(prob.f)
+    ud = torch.zeros_like(dev(u))
+    fd = dev(prob.f)
+    for k in range(3):
+        u = so.iterate(u, prob.f)
+        sg.vcycle(ud, fd)
+        sg.cccs(ud, fd)
+        assert rel(host(ud), u) <= 1e-12, k
+
+
+# ------------------------------------------------------------------ solves
+
+def test_solve_128_to_1e10_matches_oracle():
+    """The 128^2 TP/ECS workload (E = 0.5, n_b = 3, V(1,1), omega = 2/3, 5 levels)."""
+    prob = inputs.temkin_poet(128)
+    so, sg = pair(prob, 5, 3)
+    uo, hist = so.solve(prob.f, rtol=1e-10, max_iter=1200)
+    ud = torch.zeros_like(dev(prob.f))
+    its, rr, gh = sg.solve(ud, dev(prob.f), rtol=1e-10, max_iter=1200, history=True)
+    u = host(ud)
+    assert rr <= 1e-10
+    assert abs(its - len(hist)) <= 1
+    assert so.relres(u, prob.f) <= 1.001e-10                # re-checked with the oracle operator
+    k = min(len(hist), its) - 1
+    assert abs(gh[k] - hist[k]) <= 1e-6 * hist[k]
+    assert np.linalg.norm(u - uo) <= 1e-8 * np.linalg.norm(uo)
+
+
+def test_solve_host_matches_device_solve():
+    prob = tp_small(64, seed=6)
+    _, sg = pair(prob, 4, 3)
+    ud = torch.zeros_like(dev(prob.f))
+    its, rr = sg.solve(ud, dev(prob.f), rtol=1e-10, max_iter=500)
+    uh = np.zeros_like(prob.f)
+    its2, rr2 = sg.solve_host(uh, np.ascontiguousarray(prob.f), rtol=1e-10, max_iter=500)
+    assert its2 == its
+    assert rel(uh, host(ud)) <= 1e-15
+
+
+@pytest.mark.parametrize("case", ["plain_mg", "nb1", "nb6", "nonsquare", "nu21", "single_level", "deep"])
+def test_variants_match_oracle(case):
+    kw = dict(levels=4, n_b=3)
+    prob = tp_small(64, seed=2)
+    if case == "plain_mg":
+        kw["n_b"] = 0
+    elif case == "nb1":
+        kw["n_b"] = 1
+    elif case == "nb6":
+        kw["n_b"] = 6
+    elif case == "nonsquare":
+        L = 30.0 * 64 / 128
+        prob = inputs.temkin_poet(64, L=L, R0=2 * L / 3, theta=math.pi / 6, E=0.7, seed=2, ny=32)
+        prob.Ly = L / 2
+        prob.R0y = 2 * prob.Ly / 3
+        # regenerate y-dependent inputs on the shorter y box
+        x, zx = inputs.node_coordinates(64, L, 2 * L / 3, math.pi / 6)
+        y, zy = inputs.node_coordinates(32, L / 2, L / 3, math.pi / 6)
+        prob.v2 = (-1.0 / zy[1:-1]).astype(np.complex128)
+        X, Y = np.meshgrid(x[1:-1], y[1:-1])
+        ZX, ZY = np.meshgrid(zx[1:-1], zy[1:-1])
+        prob.v12 = np.ascontiguousarray(1.0 / np.where(X >= Y, ZX, ZY))
+        prob.f = np.ascontiguousarray(rand_c((31, 63), 12) * 1e-3)
+    elif case == "nu21":
+        kw.update(nu1=2, nu2=1)
+    elif case == "single_level":
+        prob = tp_small(32, seed=2)
+        kw["levels"] = 1
+    elif case == "deep":
+        kw["levels"] = 6          # coarsest 2 cells: one unknown
+    so, sg = pair(prob, **kw)
+    u = rand_c(so.levels[0].shape, 13)
+    ud = dev(u)
+    fd = dev(prob.f)
+    for _ in range(2):
+        u = so.iterate(u, prob.f)
+        sg.vcycle(ud, fd)
+        if kw["n_b"] > 0:
+            sg.cccs(ud, fd)
+    assert rel(host(ud), u) <= 1e-11
+
+
+def test_error_codes_leave_gpu_usable():
+    prob = tp_small(32)
+    _, sg = pair(prob, 3, 2)
+    f = dev(prob.f)
+    f[3, 4] = complex(float("nan"), 0.0)
+    ud = torch.zeros_like(f)
+    with pytest.raises(M.MGCCCSError) as ei:
+        sg.solve(ud, f, rtol=1e-10, max_iter=5)
+    assert ei.value.code == M.ENONFINITE
+    # too small a workspace and a bad pointer are rejected before any launch
+    p = M.params_for(prob, levels=3, n_b=2)
+    h = M.ctypes.c_void_p()
+    z = dev(np.zeros(31, dtype=np.complex128))
+    z2 = dev(np.zeros((31, 31), dtype=np.complex128))
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    assert M.lib().mgcccs_setup(M.ctypes.byref(h), M.ctypes.byref(p), z.data_ptr(), z.data_ptr(),
+                                z2.data_ptr(), ws.data_ptr(), 1024, None) == M.ENOSPACE
+    # the context still works
+    ud = torch.zeros_like(dev(prob.f))
+    its, rr = sg.solve(ud, dev(prob.f), rtol=1e-8, max_iter=300)
+    assert rr <= 1e-8
+
+
+def test_matvec_matches_oracle():
+    prob = tp_small(64, seed=7)
+    so, sg = pair(prob, 4, 3)
+    x = rand_c(so.levels[0].shape, 14)
+    yd = torch.empty_like(dev(x))
+    sg.matvec(dev(x), yd)
+    assert rel(host(yd), O.apply_operator(so.levels[0], x)) <= 1e-13
+
+
+def test_gmres_partial_cycle_matches_oracle():
+    """Ten Arnoldi steps of right-preconditioned GMRES(20) (one partial cycle): the GPU
+    iterate (CGS2 Arnoldi, Givens least squares) equals the oracle's (MGS, dense
+    least squares): both are the residual minimiser over the same Krylov space."""
+    prob = tp_small(64, seed=8)
+    so, sg = pair(prob, 4, 3, krylov_restart=20)
+    uo, hist, rr_o = O.gmres(so, prob.f, m=20, rtol=1e-14, max_iter=10)
+    ud = torch.zeros_like(dev(prob.f))
+    its, rr, gh = sg.solve(ud, dev(prob.f), rtol=1e-14, max_iter=10, history=True, raise_on_notconv=False)
+    assert its == 10
+    assert rel(host(ud), uo) <= 1e-9
+    np.testing.assert_allclose(gh, hist, rtol=1e-7)
+    assert abs(rr - rr_o) <= 1e-6 * rr_o
+
+
+def test_gmres_solve_128_matches_oracle():
+    """GMRES(20) + MG-CCCS on the 128^2 TP/ECS workload to 1e-10."""
+    prob = inputs.temkin_poet(128)
+    so, sg = pair(prob, 5, 3, krylov_restart=20)
+    uo, hist, rr_o = O.gmres(so, prob.f, m=20, rtol=1e-10, max_iter=400)
+    ud = torch.zeros_like(dev(prob.f))
+    its, rr = sg.solve(ud, dev(prob.f), rtol=1e-10, max_iter=400)
+    assert rr <= 1e-10 and abs(its - len(hist)) <= 2
+    u = host(ud)
+    assert so.relres(u, prob.f) <= 1.001e-10
+    assert np.linalg.norm(u - uo) <= 1e-7 * np.linalg.norm(uo)
+
+
+def test_full_size_1024_solve_is_valid():
+    """The 1024^2 workload timed by the benchmark (GMRES(20) + MG-CCCS, 8 levels): the GPU
+    solution meets 1e-10 under the oracle's own operator, and the first MG-CCCS iterate
+    equals the oracle's first iterate."""
+    prob = inputs.temkin_poet(1024)
+    pg = M.params_for(prob, levels=8, n_b=3, krylov_restart=20)
+    sg = M.Solver(pg, prob.v1, prob.v2, prob.v12)
+    fd = dev(prob.f)
+    ud = torch.zeros_like(fd)
+    its, rr = sg.solve(ud, fd, rtol=1e-10, max_iter=400)
+    assert rr <= 1e-10
+    po = O.params_from_problem(prob, levels=8, n_b=3)
+    so = O.Solver(po, prob.v1, prob.v2, prob.v12)
+    assert so.relres(host(ud), prob.f) <= 1.001e-10
+    u1 = so.iterate(np.zeros_like(prob.f), prob.f)
+    ud.zero_()
+    sg.vcycle(ud, fd)
+    sg.cccs(ud, fd)
+    assert rel(host(ud), u1) <= 1e-12

@@ -398,3 +398,47 @@ def test_planted_mistakes_are_caught(monkeypatch):
     with pytest.raises(AssertionError):
         test_bound_states_bilinear_orthonormal_and_refined()
     monkeypatch.setattr(O, "_normalise", orig_norm)
+
+
+# ------------------------------------------------------------------ GMRES acceleration (Sec. 6)
+
+def test_gmres_with_exact_preconditioner_takes_one_step():
+    """levels = 1 and n_b = 0 make one 'V-cycle' the exact solve, so right-preconditioned
+    GMRES converges in exactly one Arnoldi step."""
+    prob = tp_small(16)
+    s = O.Solver(O.params_from_problem(prob, levels=1, n_b=0), prob.v1, prob.v2, prob.v12)
+    u, hist, rr = O.gmres(s, prob.f, m=5, rtol=1e-12)
+    assert len(hist) == 1 and rr <= 1e-12
+
+
+def test_gmres_finite_termination_without_preconditioner():
+    """Unpreconditioned full GMRES on N = 9 unknowns terminates in at most 9 steps."""
+    prob = tp_small(4)
+    s = O.Solver(O.params_from_problem(prob, levels=1, n_b=0), prob.v1, prob.v2, prob.v12)
+    u, hist, rr = O.gmres(s, prob.f, m=9, rtol=1e-12, precondition=False)
+    assert len(hist) <= 9 and rr <= 1e-11
+
+
+def test_gmres_estimate_matches_true_residual_and_direct_solve():
+    """The least-squares residual estimate equals the true residual at exit, the residual
+    estimates never increase within a cycle, and the converged u is the LU solution."""
+    prob = tp_small(32)
+    s = O.Solver(O.params_from_problem(prob, levels=3, n_b=3), prob.v1, prob.v2, prob.v12)
+    u, hist, rr = O.gmres(s, prob.f, m=20, rtol=1e-11)
+    assert rr <= 1e-11
+    assert abs(rr - hist[-1]) <= 1e-3 * rr + 1e-14
+    for c in range(0, len(hist), 20):
+        seg = hist[c:c + 20]
+        assert all(b <= a * (1 + 1e-12) for a, b in zip(seg, seg[1:]))
+    ud = O.direct_solve(s.levels[0], prob.f)
+    assert np.linalg.norm(u - ud) <= 1e-8 * np.linalg.norm(ud)
+
+
+def test_gmres_accelerates_mgcccs_on_tp_workload():
+    """On the 128^2 TP/ECS workload GMRES(20) right-preconditioned by MG-CCCS reaches
+    1e-10 in about a hundred Arnoldi steps, where the stand-alone iteration needs
+    several hundred."""
+    prob = inputs.temkin_poet(128)
+    s = O.Solver(O.params_from_problem(prob, levels=5, n_b=3), prob.v1, prob.v2, prob.v12)
+    u, hist, rr = O.gmres(s, prob.f, m=20, rtol=1e-10, max_iter=300)
+    assert rr <= 1e-10 and len(hist) <= 150
