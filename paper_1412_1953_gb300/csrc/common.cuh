@@ -70,6 +70,7 @@ __host__ __device__ __forceinline__ cplx csqrt_p(cplx z) {
 struct StencilView {
   int mx, my;              // interior nodes per axis (row pitch = mx)
   int ux, uy;              // uniform box
+  int rbox;                // 1: cu and D are real inside the box (unrotated level, real potential)
   cplx cu;                 // uniform neighbour coefficient in the box
   const cplx* west_x;      // [mx]
   const cplx* east_x;      // [mx]
@@ -98,18 +99,21 @@ int residual_norm_blocks(const StencilView& s);
 cudaError_t launch_restrict(int mx, int my, const cplx* r, cplx* rc, cudaStream_t st);
 cudaError_t launch_prolong_add(int mx, int my, const cplx* ec, cplx* u, cudaStream_t st);
 cudaError_t launch_coarse_solve(int nc, const cplx* Ainv, const cplx* f, cplx* u, cudaStream_t st);
-cudaError_t launch_sum_partials(const double* part, int n, double* out, cudaStream_t st);
+cudaError_t launch_sum_partials(const double* part, int n, double* out, cudaStream_t st,
+                                const int* gate = nullptr);
 cudaError_t launch_norm2(const cplx* v, long long n, double* part, int nblocks, cudaStream_t st);
 int norm2_blocks(long long n);
-cudaError_t launch_apply(const StencilView& s, const cplx* x, cplx* y, cudaStream_t st);
+cudaError_t launch_apply(const StencilView& s, const cplx* x, cplx* y, cudaStream_t st,
+                         double* norm_part = nullptr);
 
 // kernels_krylov.cu
 int krylov_blocks(long long n);
 cudaError_t launch_multidot(long long n, int k, const cplx* V, long long ld, const cplx* w, cplx* partial,
-                            int nblk, cudaStream_t st);
+                            int nblk, const int* gate, cudaStream_t st);
 cudaError_t launch_reduce_dots(int nblk, int k, const cplx* partial, cplx* out, cplx* acc_into, cudaStream_t st);
 cudaError_t launch_multiaxpy(long long n, int k, const cplx* V, long long ld, const cplx* coef, double sgn,
-                             cplx* w, double* norm_part, int nblk, cudaStream_t st);
+                             cplx* w, double* norm_part, int nblk, const int* gate, cudaStream_t st);
+cudaError_t launch_dgks(const double* before, const double* after, int* gate, cudaStream_t st);
 cudaError_t launch_scale_by_norm(long long n, const cplx* w, cplx* out, const double* norm2, cplx* store,
                                  int nblk, cudaStream_t st);
 cudaError_t launch_givens(int j, int m, cplx* H, cplx* cs, cplx* sn, cplx* g, double* est, cudaStream_t st);
@@ -132,21 +136,39 @@ struct CCView {
   cplx* rB;                // [nb][mx]
   cplx* eA;                // [nb][my]
   cplx* eB;                // [nb][mx]
-  const cplx* GA;          // [my][nb][nb]  block-Thomas inverses, channel A (along y)
-  const cplx* GB;          // [mx][nb][nb]  channel B (along x)
-  const cplx* aA;          // [my] sub-diagonal (west_y) of channel A
-  const cplx* cA;          // [my] super-diagonal (east_y)
-  const cplx* aB;          // [mx] west_x
-  const cplx* cB;          // [mx] east_x
-  cplx* gA;                // [my][nb] forward-sweep scratch
-  cplx* gB;                // [mx][nb]
 };
+
+// Cyclic-reduction factors of one coupled-channel system (Eqs. (28)-(29)),
+// a_k x_{k-1} + B_k x_k + c_k x_{k+1} = r_k with n_b x n_b blocks.  Rows are numbered
+// 1..M with M = 2^q - 1 >= m; rows past m are identity padding.  Level l (1..q-1)
+// eliminates the odd multiples of s = 2^(l-1); for the kept rows i (multiples of 2s)
+// alpha_i, gamma_i hold A_i B_{i-s}^{-1}, C_i B_{i+s}^{-1}; an eliminated row j keeps
+// P_j = B_j^{-1}, Q_j = B_j^{-1} A_j, R_j = B_j^{-1} C_j of its elimination level; the
+// root 2^(q-1) keeps P only.
+struct CRSystem {
+  int m, q, M, nb;
+  cplx* alpha;             // [M][nb*nb] kept rows of every level, level by level
+  cplx* gamma;
+  cplx* P;                 // [M+1][nb*nb] indexed by row
+  cplx* Q;
+  cplx* R;
+  cplx* X;                 // [(M+2)*nb] reduced right-hand side (solve scratch)
+  cplx* Y;                 // [(M+2)*nb] solution, rows 0 and M+1 zero (solve scratch)
+  const cplx* r;           // [nb][m] right-hand side
+  cplx* e;                 // [nb][m] solution
+};
+int cr_levels(int m);
+__host__ __device__ inline int cr_fwd_offset(int q, int l) {
+  int o = 0;
+  for (int k = 1; k < l; ++k) o += (1 << (q - k)) - 1;
+  return o;
+}
 int cc_tiles_x(int mx);
 int cc_tiles_y(int my);
 cudaError_t launch_residual_project(const StencilView& s, const CCView& c, const cplx* u, const cplx* f,
                                     cudaStream_t st);
 cudaError_t launch_cc_rhs(const CCView& c, cudaStream_t st);
-cudaError_t launch_channel_solve(const CCView& c, cudaStream_t st);
+cudaError_t launch_channel_solve(const CRSystem& A, const CRSystem& B, cudaStream_t st);
 cudaError_t launch_cccs_correct(const CCView& c, cplx* u, cudaStream_t st);
 
 // kernels_setup.cu
@@ -156,6 +178,8 @@ struct AxisSetup {
   cplx* west; cplx* east; cplx* diag; cplx* w;   // [n-1] each
 };
 cudaError_t launch_setup_axis(const AxisSetup& a, cudaStream_t st);
+cudaError_t launch_box_real_check(const StencilView& s, int* flag, cudaStream_t st);
+cudaError_t launch_compare(int n, const cplx* a, const cplx* b, int* flag, cudaStream_t st);
 cudaError_t launch_setup_diag(int mx, int my, int stride, int fine_mx, const cplx* dx, const cplx* dy,
                               const cplx* v1, const cplx* v2, const cplx* v12, double E, double omega,
                               cplx* D, cplx* Dinv, int* status, cudaStream_t st);
@@ -168,6 +192,6 @@ cudaError_t launch_weight_states(int m, int nb, const cplx* w, const cplx* phi, 
 cudaError_t launch_channel_potentials(int mx, int my, int nb, const cplx* wphi, const cplx* phi,
                                       const cplx* wvphi, const cplx* vphi, const cplx* v12,
                                       cplx* VA, cplx* VB, cudaStream_t st);
-cudaError_t launch_channel_factor(int m, int nb, const cplx* diag, const cplx* v, double E, const cplx* lam,
-                                  const cplx* Vc, const cplx* a, const cplx* c, cplx* G, int* status,
+cudaError_t launch_channel_factor(const CRSystem& S, const cplx* diag, const cplx* v, double E, const cplx* lam,
+                                  const cplx* Vc, const cplx* a, const cplx* c, cplx* scratch, int* status,
                                   cudaStream_t st);

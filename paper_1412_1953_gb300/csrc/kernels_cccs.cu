@@ -32,7 +32,14 @@ __device__ __forceinline__ cplx residual_at(const StencilView& s, const cplx* __
   cplx ue = ldz(u, p + 1, i + 1 < s.mx);
   cplx us = ldz(u, p - s.mx, j > 0);
   cplx un = ldz(u, p + s.mx, j + 1 < s.my);
-  cplx a = cmul(__ldg(s.D + p), uc);
+  cplx a;
+  if (s.rbox && i < s.ux && j < s.uy) {
+    cplx sum = cadd(cadd(uw, ue), cadd(us, un));
+    const double d = __ldg(reinterpret_cast<const double*>(s.D) + 2 * p);
+    a = cmk(fma(s.cu.x, sum.x, d * uc.x), fma(s.cu.x, sum.y, d * uc.y));
+    return csub(__ldg(f + p), a);
+  }
+  a = cmul(__ldg(s.D + p), uc);
   if (i < s.ux && j < s.uy) {
     a = cfma(s.cu, cadd(cadd(uw, ue), cadd(us, un)), a);
   } else {
@@ -158,53 +165,67 @@ __global__ void __launch_bounds__(256) k_cc_split(int nb, int mx, int my, const 
   }
 }
 
-// Block-Thomas solve of  a_k x_{k-1} + B_k x_k + c_k x_{k+1} = r_k  with precomputed
-// G_k = (B_k - a_k c_{k-1} G_{k-1})^{-1}:  g_k = G_k (r_k - a_k g_{k-1}),
-// x_k = g_k - c_k G_k x_{k+1}.  Block 0 solves channel A (along y), block 1 channel B.
-// One warp, lane q owns component q.
-__global__ void __launch_bounds__(32) k_channel_solve(CCView c) {
-  __shared__ cplx sv[MGC_MAX_NB];
-  const int q = threadIdx.x;
-  const int nb = c.nb;
-  const bool isA = blockIdx.x == 0;
-  const int m = isA ? c.my : c.mx;
-  const cplx* G = isA ? c.GA : c.GB;
-  const cplx* a = isA ? c.aA : c.aB;
-  const cplx* cc = isA ? c.cA : c.cB;
-  const cplx* r = isA ? c.rA : c.rB;     // [nb][m]
-  cplx* g = isA ? c.gA : c.gB;           // [m][nb]
-  cplx* x = isA ? c.eA : c.eB;           // [nb][m]
-  const bool act = q < nb;
-  cplx prev = cmk(0.0, 0.0);
-  for (int k = 0; k < m; ++k) {
-    if (act) {
-      cplx t = r[q * m + k];
-      if (k > 0) t = cfms(a[k], prev, t);
-      sv[q] = t;
-    }
-    __syncwarp();
-    cplx gq = cmk(0.0, 0.0);
-    if (act) {
-      const cplx* Gk = G + (size_t)k * nb * nb + q * nb;
-      for (int p = 0; p < nb; ++p) gq = cfma(Gk[p], sv[p], gq);
-      g[(size_t)k * nb + q] = gq;
-    }
-    __syncwarp();
-    prev = gq;
+// Cyclic-reduction solve of one coupled-channel system with the setup-time factors:
+// forward, level by level, X_i -= alpha_i X_{i-s} + gamma_i X_{i+s} on the kept rows;
+// root Y = P X; backward, Y_j = P_j X_j - Q_j Y_{j-s} - R_j Y_{j+s} on the rows each
+// level eliminated.  Block 0 solves channel A (along y), block 1 channel B (along x);
+// each level is one parallel pass over (row, component) pairs.
+__global__ void __launch_bounds__(512) k_channel_solve(CRSystem SA, CRSystem SB) {
+  const CRSystem& S = blockIdx.x == 0 ? SA : SB;
+  const int nb = S.nb, nb2 = nb * nb, M = S.M, q = S.q, m = S.m;
+  const int t0 = threadIdx.x, nt = blockDim.x;
+  for (int idx = t0; idx < (M + 2) * nb; idx += nt) {
+    const int row = idx / nb, comp = idx % nb;
+    S.X[idx] = (row >= 1 && row <= m) ? S.r[comp * m + row - 1] : cmk(0.0, 0.0);
+    S.Y[idx] = cmk(0.0, 0.0);
   }
-  cplx xn = prev;           // x_{m-1} = g_{m-1}
-  if (act) x[q * m + (m - 1)] = xn;
-  for (int k = m - 2; k >= 0; --k) {
-    if (act) sv[q] = xn;
-    __syncwarp();
-    if (act) {
-      const cplx* Gk = G + (size_t)k * nb * nb + q * nb;
-      cplx s = cmk(0.0, 0.0);
-      for (int p = 0; p < nb; ++p) s = cfma(Gk[p], sv[p], s);
-      xn = cfms(cc[k], s, g[(size_t)k * nb + q]);
-      x[q * m + k] = xn;
+  __syncthreads();
+  for (int l = 1; l < q; ++l) {
+    const int s = 1 << (l - 1);
+    const int nk = (1 << (q - l)) - 1;
+    const int off = cr_fwd_offset(q, l);
+    for (int w = t0; w < nk * nb; w += nt) {
+      const int t = w / nb + 1, comp = w % nb, i = 2 * s * t;
+      const cplx* al = S.alpha + (size_t)(off + t - 1) * nb2 + comp * nb;
+      const cplx* ga = S.gamma + (size_t)(off + t - 1) * nb2 + comp * nb;
+      cplx acc = S.X[i * nb + comp];
+      for (int p = 0; p < nb; ++p) {
+        acc = cfms(al[p], S.X[(i - s) * nb + p], acc);
+        acc = cfms(ga[p], S.X[(i + s) * nb + p], acc);
+      }
+      S.X[i * nb + comp] = acc;
     }
-    __syncwarp();
+    __syncthreads();
+  }
+  const int root = 1 << (q - 1);
+  if (t0 < nb) {
+    const cplx* Pr = S.P + (size_t)root * nb2 + t0 * nb;
+    cplx acc = cmk(0.0, 0.0);
+    for (int p = 0; p < nb; ++p) acc = cfma(Pr[p], S.X[root * nb + p], acc);
+    S.Y[root * nb + t0] = acc;
+  }
+  __syncthreads();
+  for (int l = q - 1; l >= 1; --l) {
+    const int s = 1 << (l - 1);
+    const int ne = 1 << (q - l);           // odd multiples of s in 1..M
+    for (int w = t0; w < ne * nb; w += nt) {
+      const int j = s * (2 * (w / nb) + 1), comp = w % nb;
+      const cplx* Pj = S.P + (size_t)j * nb2 + comp * nb;
+      const cplx* Qj = S.Q + (size_t)j * nb2 + comp * nb;
+      const cplx* Rj = S.R + (size_t)j * nb2 + comp * nb;
+      cplx acc = cmk(0.0, 0.0);
+      for (int p = 0; p < nb; ++p) {
+        acc = cfma(Pj[p], S.X[j * nb + p], acc);
+        acc = cfms(Qj[p], S.Y[(j - s) * nb + p], acc);
+        acc = cfms(Rj[p], S.Y[(j + s) * nb + p], acc);
+      }
+      S.Y[j * nb + comp] = acc;
+    }
+    __syncthreads();
+  }
+  for (int idx = t0; idx < m * nb; idx += nt) {
+    const int comp = idx / m, k = idx % m;
+    S.e[idx] = S.Y[(k + 1) * nb + comp];
   }
 }
 
@@ -271,8 +292,14 @@ cudaError_t launch_cc_rhs(const CCView& c, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_channel_solve(const CCView& c, cudaStream_t st) {
-  k_channel_solve<<<2, 32, 0, st>>>(c);
+int cr_levels(int m) {
+  int q = 1;
+  while ((1 << q) - 1 < m) ++q;
+  return q;
+}
+
+cudaError_t launch_channel_solve(const CRSystem& A, const CRSystem& B, cudaStream_t st) {
+  k_channel_solve<<<2, 512, 0, st>>>(A, B);
   return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // Kernels of the restarted GMRES(m) outer solver, right-preconditioned by one MG-CCCS
 // iteration (Sec. 6: MG-CCCS as a Krylov preconditioner).  Arnoldi uses classical
-// Gram-Schmidt applied twice (each pass: one fused multi-dot, one fused multi-axpy);
+// Gram-Schmidt (each pass: one fused multi-dot, one fused multi-axpy) with a second pass
+// when the Daniel-Gragg-Kaufman-Stewart test asks for it (decided on the device);
 // the Hessenberg least-squares problem is reduced by complex Givens rotations on the
 // device, so the host only reads one residual estimate per step.
 //
@@ -27,11 +28,17 @@ __device__ __forceinline__ cplx block_sum_c(cplx v, double (*sh)[NTH / 32]) {
   return tot;
 }
 
-// partial[i][b] = sum over block b's points of conj(V_i) w   (grid: nblk x k)
+// partial[i][b] = sum over block b's points of conj(V_i) w   (grid: nblk x k).
+// When `gate` is given and *gate == 0 the pass is skipped (partials set to zero).
 __global__ void __launch_bounds__(NT) k_multidot(long long n, const cplx* __restrict__ V, long long ld,
-                                                 const cplx* __restrict__ w, cplx* __restrict__ partial) {
+                                                 const cplx* __restrict__ w, cplx* __restrict__ partial,
+                                                 const int* __restrict__ gate) {
   __shared__ double sh[2][NT / 32];
   const int i = blockIdx.y;
+  if (gate && *gate == 0) {
+    if (threadIdx.x == 0) partial[(size_t)i * gridDim.x + blockIdx.x] = cmk(0.0, 0.0);
+    return;
+  }
   const cplx* v = V + (size_t)i * ld;
   cplx acc = cmk(0.0, 0.0);
   for (long long p = blockIdx.x * (long long)NT + threadIdx.x; p < n; p += (long long)gridDim.x * NT) {
@@ -60,9 +67,10 @@ __global__ void __launch_bounds__(NT) k_reduce_dots(int nblk, const cplx* __rest
 // w += sgn * sum_{i<k} coef[i] V_i ; optional per-block partials of |w|^2.
 __global__ void __launch_bounds__(NT) k_multiaxpy(long long n, int k, const cplx* __restrict__ V, long long ld,
                                                   const cplx* __restrict__ coef, double sgn, cplx* __restrict__ w,
-                                                  double* __restrict__ norm_part) {
+                                                  double* __restrict__ norm_part, const int* __restrict__ gate) {
   __shared__ cplx sc[64];
   __shared__ double sh[NT / 32];
+  if (gate && *gate == 0) return;
   for (int i = threadIdx.x; i < k; i += NT) sc[i] = cscal(sgn, coef[i]);
   __syncthreads();
   double n2 = 0.0;
@@ -139,6 +147,12 @@ __global__ void k_hess_solve(int k, int m, const cplx* __restrict__ H, const cpl
   }
 }
 
+// Daniel-Gragg-Kaufman-Stewart test: a second Gram-Schmidt pass is needed when the
+// first pass removed more than half of |w|^2 (|w_after| < |w_before| / sqrt(2)).
+__global__ void k_dgks(const double* __restrict__ before, const double* __restrict__ after, int* __restrict__ gate) {
+  if (threadIdx.x == 0) *gate = (*after < 0.5 * *before) ? 1 : 0;
+}
+
 __global__ void k_zero_c(int n, cplx* __restrict__ a) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) a[t] = cmk(0.0, 0.0);
@@ -152,8 +166,8 @@ int krylov_blocks(long long n) {
 }
 
 cudaError_t launch_multidot(long long n, int k, const cplx* V, long long ld, const cplx* w, cplx* partial,
-                            int nblk, cudaStream_t st) {
-  k_multidot<<<dim3(nblk, k), NT, 0, st>>>(n, V, ld, w, partial);
+                            int nblk, const int* gate, cudaStream_t st) {
+  k_multidot<<<dim3(nblk, k), NT, 0, st>>>(n, V, ld, w, partial, gate);
   return cudaGetLastError();
 }
 
@@ -163,8 +177,8 @@ cudaError_t launch_reduce_dots(int nblk, int k, const cplx* partial, cplx* out, 
 }
 
 cudaError_t launch_multiaxpy(long long n, int k, const cplx* V, long long ld, const cplx* coef, double sgn,
-                             cplx* w, double* norm_part, int nblk, cudaStream_t st) {
-  k_multiaxpy<<<nblk, NT, 0, st>>>(n, k, V, ld, coef, sgn, w, norm_part);
+                             cplx* w, double* norm_part, int nblk, const int* gate, cudaStream_t st) {
+  k_multiaxpy<<<nblk, NT, 0, st>>>(n, k, V, ld, coef, sgn, w, norm_part, gate);
   return cudaGetLastError();
 }
 
@@ -181,6 +195,11 @@ cudaError_t launch_givens(int j, int m, cplx* H, cplx* cs, cplx* sn, cplx* g, do
 
 cudaError_t launch_hess_solve(int k, int m, const cplx* H, const cplx* g, cplx* y, cudaStream_t st) {
   k_hess_solve<<<1, 32, 0, st>>>(k, m, H, g, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dgks(const double* before, const double* after, int* gate, cudaStream_t st) {
+  k_dgks<<<1, 32, 0, st>>>(before, after, gate);
   return cudaGetLastError();
 }
 

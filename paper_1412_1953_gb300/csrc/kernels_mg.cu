@@ -37,6 +37,21 @@ __device__ __forceinline__ cplx apply_op(const StencilView& s, const cplx* __res
   return a;
 }
 
+// Real part of a complex array element (only 8 bytes are loaded).
+__device__ __forceinline__ double ldre(const cplx* __restrict__ a, int p) {
+  return __ldg(reinterpret_cast<const double*>(a) + 2 * p);
+}
+
+// (H - E) u in the real box: real coefficient cu.x and real diagonal.
+__device__ __forceinline__ cplx apply_op_rbox(const StencilView& s, const cplx* __restrict__ u, int i, int j,
+                                              cplx uc) {
+  const int p = j * s.mx + i;
+  cplx sum = cadd(cadd(ldz(u, p - 1, i > 0), ldz(u, p + 1, i + 1 < s.mx)),
+                  cadd(ldz(u, p - s.mx, j > 0), ldz(u, p + s.mx, j + 1 < s.my)));
+  const double d = ldre(s.D, p);
+  return cmk(fma(s.cu.x, sum.x, d * uc.x), fma(s.cu.x, sum.y, d * uc.y));
+}
+
 __global__ void __launch_bounds__(BX * BY) k_jacobi(StencilView s, const cplx* __restrict__ u_in,
                                                     cplx* __restrict__ u_out, const cplx* __restrict__ f) {
   const int i = blockIdx.x * BX + threadIdx.x;
@@ -44,8 +59,14 @@ __global__ void __launch_bounds__(BX * BY) k_jacobi(StencilView s, const cplx* _
   if (i >= s.mx || j >= s.my) return;
   const int p = j * s.mx + i;
   cplx uc = __ldg(u_in + p);
-  cplx r = csub(__ldg(f + p), apply_op(s, u_in, i, j, uc));
-  u_out[p] = cfma(__ldg(s.Dinv + p), r, uc);
+  if (s.rbox && i < s.ux && j < s.uy) {
+    cplx r = csub(__ldg(f + p), apply_op_rbox(s, u_in, i, j, uc));
+    const double di = ldre(s.Dinv, p);
+    u_out[p] = cmk(fma(di, r.x, uc.x), fma(di, r.y, uc.y));
+  } else {
+    cplx r = csub(__ldg(f + p), apply_op(s, u_in, i, j, uc));
+    u_out[p] = cfma(__ldg(s.Dinv + p), r, uc);
+  }
 }
 
 // First sweep from a zero initial guess: u = omega D^{-1} f.
@@ -80,7 +101,9 @@ __global__ void __launch_bounds__(BX * BY) k_residual(StencilView s, const cplx*
   double n2 = 0.0;
   if (i < s.mx && j < s.my) {
     const int p = j * s.mx + i;
-    cplx rv = csub(__ldg(f + p), apply_op(s, u, i, j, __ldg(u + p)));
+    const cplx uc = __ldg(u + p);
+    cplx rv = csub(__ldg(f + p), (s.rbox && i < s.ux && j < s.uy) ? apply_op_rbox(s, u, i, j, uc)
+                                                                    : apply_op(s, u, i, j, uc));
     if (r) r[p] = rv;
     n2 = cabs2(rv);
   }
@@ -152,10 +175,12 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int nc, const cplx* __rest
   if (lane == 0) u[row] = acc;
 }
 
-// Sum of n partials in a fixed order (one block), result to out[0].
+// Sum of n partials in a fixed order (one block), result to out[0]; skipped when
+// `gate` is given and *gate == 0.
 __global__ void __launch_bounds__(256) k_sum_partials(const double* __restrict__ part, int n,
-                                                      double* __restrict__ out) {
+                                                      double* __restrict__ out, const int* __restrict__ gate) {
   __shared__ double sh[8];
+  if (gate && *gate == 0) return;
   double v = 0.0;
   for (int k = threadIdx.x; k < n; k += 256) v += part[k];
   double tot = block_sum<256>(v, sh);
@@ -171,12 +196,23 @@ __global__ void __launch_bounds__(256) k_norm2(const cplx* __restrict__ v, long 
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(BX * BY) k_apply(StencilView s, const cplx* __restrict__ x, cplx* __restrict__ y) {
+__global__ void __launch_bounds__(BX * BY) k_apply(StencilView s, const cplx* __restrict__ x, cplx* __restrict__ y,
+                                                   double* __restrict__ norm_part) {
+  __shared__ double sh[BX * BY / 32];
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
-  if (i >= s.mx || j >= s.my) return;
-  const int p = j * s.mx + i;
-  y[p] = apply_op(s, x, i, j, __ldg(x + p));
+  double n2 = 0.0;
+  if (i < s.mx && j < s.my) {
+    const int p = j * s.mx + i;
+    const cplx xc = __ldg(x + p);
+    cplx v = (s.rbox && i < s.ux && j < s.uy) ? apply_op_rbox(s, x, i, j, xc) : apply_op(s, x, i, j, xc);
+    y[p] = v;
+    n2 = cabs2(v);
+  }
+  if (norm_part) {
+    double tot = block_sum<BX * BY>(n2, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) norm_part[blockIdx.y * gridDim.x + blockIdx.x] = tot;
+  }
 }
 
 inline dim3 grid2(int mx, int my) { return dim3((mx + BX - 1) / BX, (my + BY - 1) / BY); }
@@ -222,8 +258,8 @@ cudaError_t launch_coarse_solve(int nc, const cplx* Ainv, const cplx* f, cplx* u
   return cudaGetLastError();
 }
 
-cudaError_t launch_sum_partials(const double* part, int n, double* out, cudaStream_t st) {
-  k_sum_partials<<<1, 256, 0, st>>>(part, n, out);
+cudaError_t launch_sum_partials(const double* part, int n, double* out, cudaStream_t st, const int* gate) {
+  k_sum_partials<<<1, 256, 0, st>>>(part, n, out, gate);
   return cudaGetLastError();
 }
 
@@ -237,7 +273,7 @@ cudaError_t launch_norm2(const cplx* v, long long n, double* part, int nblocks, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_apply(const StencilView& s, const cplx* x, cplx* y, cudaStream_t st) {
-  k_apply<<<grid2(s.mx, s.my), dim3(BX, BY), 0, st>>>(s, x, y);
+cudaError_t launch_apply(const StencilView& s, const cplx* x, cplx* y, cudaStream_t st, double* norm_part) {
+  k_apply<<<grid2(s.mx, s.my), dim3(BX, BY), 0, st>>>(s, x, y, norm_part);
   return cudaGetLastError();
 }

@@ -5,14 +5,15 @@
 //    contour.
 //  * Diagonal D of H - E and omega/D per node, potentials injected at coincident nodes.
 //  * Dense inverse of the coarsest-level operator (Gauss-Jordan, partial pivoting).
-//  * Bound states of H1, H2 (Eq. (9)): eigenvalues by implicit QL with a Wilkinson
-//    shift applied without conjugation to the complex-symmetric tridiagonal
+//  * Bound states of H1, H2 (Eq. (9)): eigenvalue estimates by implicit QL with a
+//    Wilkinson shift applied without conjugation to the complex-symmetric tridiagonal
 //    (Bowdler, Martin, Reinsch & Wilkinson, Numer. Math. 11, 1968; the
-//    complex-symmetric use follows Cullum & Willoughby), the n_b with smallest real
-//    part, eigenvectors by inverse iteration with a pivoted tridiagonal LU, bilinear
-//    normalisation int phi^2 dz = 1 (Sec. 3.1, Remark 3), then two shift-and-invert
-//    steps and a bilinear Rayleigh quotient (Sec. 5.1.2, Sec. 5.2).
-//  * Channel potentials V^A, V^B (Sec. 4.2) and the block-Thomas factors of the
+//    complex-symmetric use follows Cullum & Willoughby), run in single precision; the
+//    n_b with smallest real part are refined in double precision by inverse and
+//    Rayleigh-quotient iteration with a pivoted tridiagonal LU, normalised bilinearly,
+//    int phi^2 dz = 1 (Sec. 3.1, Remark 3), then two shift-and-invert steps and a
+//    bilinear Rayleigh quotient (Sec. 5.1.2, Sec. 5.2).
+//  * Channel potentials V^A, V^B (Sec. 4.2) and the cyclic-reduction factors of the
 //    coupled-channel systems (Eqs. (28)-(29)).
 #include "common.cuh"
 
@@ -64,6 +65,20 @@ __global__ void k_setup_diag(int mx, int my, int stride, int fine_mx, const cplx
   } else {
     Dinv[p] = cdiv(cmk(omega, 0.0), d);
   }
+}
+
+// flag := 1 if a[k] != b[k] for some k (bitwise comparison of the values).
+__global__ void k_compare(int n, const cplx* __restrict__ a, const cplx* __restrict__ b, int* flag) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n && (a[k].x != b[k].x || a[k].y != b[k].y)) atomicOr(flag, 1);
+}
+
+// flag := 1 if some node of the uniform box has a complex diagonal.
+__global__ void k_box_real_check(int mx, int ux, int uy, const cplx* __restrict__ D, int* flag) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 8 + threadIdx.y;
+  if (i >= ux || j >= uy) return;
+  if (D[(size_t)j * mx + i].y != 0.0) atomicOr(flag, 1);
 }
 
 // Dense inverse of the coarsest operator by Gauss-Jordan elimination with partial
@@ -144,53 +159,80 @@ __global__ void __launch_bounds__(1024) k_coarse_inverse(StencilView s, cplx* __
 
 // ---- bound states ---------------------------------------------------------------
 
-// Eigenvalues of the complex-symmetric tridiagonal (d, e) by implicit QL; d is
-// overwritten with the eigenvalues.  Returns false if an eigenvalue needs more than
-// 60 sweeps or a rotation breaks down.
-__device__ bool ql_eigenvalues(int m, cplx* d, cplx* e) {
-  e[m - 1] = cmk(0.0, 0.0);
+// single-precision complex helpers for the eigenvalue estimates
+__device__ __forceinline__ float2 fk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return fk(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) { return fk(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return fk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ float fabs1(float2 a) { return fabsf(a.x) + fabsf(a.y); }
+__device__ __forceinline__ float2 fdiv2(float2 a, float2 b) {      // Smith's algorithm
+  if (fabsf(b.y) <= fabsf(b.x)) {
+    float r = b.y / b.x, den = b.x + b.y * r;
+    return fk((a.x + a.y * r) / den, (a.y - a.x * r) / den);
+  }
+  float r = b.x / b.y, den = b.x * r + b.y;
+  return fk((a.x * r + a.y) / den, (a.y * r - a.x) / den);
+}
+__device__ __forceinline__ float2 fsqrt2(float2 z) {                // principal branch
+  float m = hypotf(z.x, z.y);
+  if (m == 0.0f) return fk(0.0f, 0.0f);
+  if (z.x >= 0.0f) {
+    float t = sqrtf(0.5f * (m + z.x));
+    return fk(t, z.y / (2.0f * t));
+  }
+  float t = sqrtf(0.5f * (m - z.x));
+  float sg = (z.y < 0.0f) ? -t : t;
+  return fk(z.y / (2.0f * sg), sg);
+}
+
+// Eigenvalue estimates of the complex-symmetric tridiagonal (d, e) by single-precision
+// implicit QL with a Wilkinson shift; d is overwritten with the eigenvalues.  The
+// estimates only pick the states and start the FP64 refinement.  Returns false if an
+// eigenvalue needs more than 60 sweeps or a rotation breaks down.
+__device__ bool ql_eigenvalues_f32(int m, float2* d, float2* e) {
+  e[m - 1] = fk(0.0f, 0.0f);
   for (int l = 0; l < m; ++l) {
     int sweeps = 0;
     for (;;) {
       int mm = l;
       for (; mm < m - 1; ++mm) {
-        double dd = cabs1(d[mm]) + cabs1(d[mm + 1]);
-        if (cabs1(e[mm]) + dd == dd) break;
+        float dd = fabs1(d[mm]) + fabs1(d[mm + 1]);
+        if (fabs1(e[mm]) + dd == dd) break;
       }
       if (mm == l) break;
       if (++sweeps > 60) return false;
-      // shift from the leading 2x2 block
-      cplx g = cdiv(csub(d[l + 1], d[l]), cscal(2.0, e[l]));
-      cplx r = csqrt_p(cadd(cmul(g, g), cmk(1.0, 0.0)));
-      cplx gp = cadd(g, r), gm = csub(g, r);
-      cplx den = (cabs2(gp) >= cabs2(gm)) ? gp : gm;
-      g = cadd(csub(d[mm], d[l]), cdiv(e[l], den));
-      cplx s = cmk(1.0, 0.0), c = cmk(1.0, 0.0), p = cmk(0.0, 0.0);
+      float2 g = fdiv2(fsub2(d[l + 1], d[l]), fk(2.0f * e[l].x, 2.0f * e[l].y));
+      float2 r = fsqrt2(fadd2(fmul2(g, g), fk(1.0f, 0.0f)));
+      float2 gp = fadd2(g, r), gm = fsub2(g, r);
+      float2 den = (gp.x * gp.x + gp.y * gp.y >= gm.x * gm.x + gm.y * gm.y) ? gp : gm;
+      g = fadd2(fsub2(d[mm], d[l]), fdiv2(e[l], den));
+      float2 s = fk(1.0f, 0.0f), c = fk(1.0f, 0.0f), p = fk(0.0f, 0.0f);
       bool restart = false;
       for (int i = mm - 1; i >= l; --i) {
-        cplx f = cmul(s, e[i]);
-        cplx b = cmul(c, e[i]);
-        r = csqrt_p(cadd(cmul(f, f), cmul(g, g)));
+        float2 f = fmul2(s, e[i]);
+        float2 b = fmul2(c, e[i]);
+        r = fsqrt2(fadd2(fmul2(f, f), fmul2(g, g)));
         e[i + 1] = r;
-        if (r.x == 0.0 && r.y == 0.0) {
-          if (f.x != 0.0 || f.y != 0.0) return false;       // isotropic breakdown
-          d[i + 1] = csub(d[i + 1], p);
-          e[mm] = cmk(0.0, 0.0);
+        if (r.x == 0.0f && r.y == 0.0f) {
+          if (f.x != 0.0f || f.y != 0.0f) return false;
+          d[i + 1] = fsub2(d[i + 1], p);
+          e[mm] = fk(0.0f, 0.0f);
           restart = true;
           break;
         }
-        s = cdiv(f, r);
-        c = cdiv(g, r);
-        g = csub(d[i + 1], p);
-        r = cadd(cmul(csub(d[i], g), s), cscal(2.0, cmul(c, b)));
-        p = cmul(s, r);
-        d[i + 1] = cadd(g, p);
-        g = csub(cmul(c, r), b);
+        s = fdiv2(f, r);
+        c = fdiv2(g, r);
+        g = fsub2(d[i + 1], p);
+        float2 cb = fmul2(c, b);
+        r = fadd2(fmul2(fsub2(d[i], g), s), fk(2.0f * cb.x, 2.0f * cb.y));
+        p = fmul2(s, r);
+        d[i + 1] = fadd2(g, p);
+        g = fsub2(fmul2(c, r), b);
       }
       if (restart) continue;
-      d[l] = csub(d[l], p);
+      d[l] = fsub2(d[l], p);
       e[l] = g;
-      e[mm] = cmk(0.0, 0.0);
+      e[mm] = fk(0.0f, 0.0f);
     }
   }
   for (int k = 0; k < m; ++k)
@@ -287,72 +329,112 @@ __device__ cplx rayleigh(int m, const cplx* west, const cplx* east, const cplx* 
   return acc;
 }
 
+// bilinear Rayleigh quotient x^T W H x / x^T W x (x not normalised)
+__device__ cplx rayleigh_ratio(int m, const cplx* west, const cplx* east, const cplx* diag, const cplx* v,
+                               const cplx* w, const cplx* x) {
+  cplx num = cmk(0.0, 0.0), den = cmk(0.0, 0.0);
+  for (int k = 0; k < m; ++k) {
+    cplx hx = cmul(cadd(diag[k], v[k]), x[k]);
+    if (k > 0) hx = cfma(west[k], x[k - 1], hx);
+    if (k + 1 < m) hx = cfma(east[k], x[k + 1], hx);
+    cplx xw = cmul(x[k], w[k]);
+    num = cfma(xw, hx, num);
+    den = cfma(xw, x[k], den);
+  }
+  return cdiv(num, den);
+}
+
+// Eigenvalue estimates by single-precision QL (thread 0), the n_b with the smallest
+// real part; then per state (thread q): FP64 inverse iteration at the estimate, Rayleigh-
+// quotient iteration to the FP64 eigenvalue, bilinear normalisation, and the paper's two
+// shift-and-invert steps.  Coinciding refined eigenvalues flag a failure.
 __global__ void __launch_bounds__(32) k_bound_states(int m, const cplx* __restrict__ west,
                                                      const cplx* __restrict__ east, const cplx* __restrict__ diag,
                                                      const cplx* __restrict__ v, const cplx* __restrict__ w, int nb,
                                                      cplx* __restrict__ lam, cplx* __restrict__ phi,
                                                      cplx* __restrict__ scratch, int* status) {
   __shared__ cplx sel[MGC_MAX_NB];
+  __shared__ cplx fin_l[MGC_MAX_NB];
   __shared__ int ok;
   const int q = threadIdx.x;
-  cplx* d = scratch;            // m
-  cplx* e = scratch + m;        // m
+  float2* d = reinterpret_cast<float2*>(scratch);          // m
+  float2* e = d + m;                                        // m
   if (q == 0) {
     // symmetric form: e_k^2 = east_k * west_{k+1}
     for (int k = 0; k < m; ++k) {
-      d[k] = cadd(diag[k], v[k]);
-      e[k] = (k + 1 < m) ? csqrt_p(cmul(east[k], west[k + 1])) : cmk(0.0, 0.0);
+      cplx dk = cadd(diag[k], v[k]);
+      d[k] = fk((float)dk.x, (float)dk.y);
+      cplx ek = (k + 1 < m) ? csqrt_p(cmul(east[k], west[k + 1])) : cmk(0.0, 0.0);
+      e[k] = fk((float)ek.x, (float)ek.y);
     }
-    ok = ql_eigenvalues(m, d, e) ? 1 : 0;
+    ok = ql_eigenvalues_f32(m, d, e) ? 1 : 0;
     if (ok) {
       // the nb eigenvalues with the smallest real part, ascending (ties: lower index)
       for (int s = 0; s < nb; ++s) {
         int kb = -1;
         for (int k = 0; k < m; ++k) {
-          if (e[k].x == 1.0e300) continue;           // already taken
+          if (e[k].x == 1.0e30f) continue;            // already taken
           if (kb < 0 || d[k].x < d[kb].x) kb = k;
         }
-        sel[s] = d[kb];
-        e[kb] = cmk(1.0e300, 0.0);
+        sel[s] = cmk((double)d[kb].x, (double)d[kb].y);
+        e[kb] = fk(1.0e30f, 0.0f);
       }
     } else {
       atomicOr(status, MGC_ST_EIG);
     }
   }
   __syncthreads();
-  if (!ok || q >= nb) return;
-  // per-state scratch
-  cplx* base = scratch + 2 * m + (size_t)q * 5 * m;
-  TriLU lu{base, base + m, base + 2 * m, base + 3 * m,
-           reinterpret_cast<int*>(scratch + 2 * m + (size_t)nb * 5 * m) + (size_t)q * m};
-  cplx* x = base + 4 * m;
-  double scale = 0.0;
-  for (int k = 0; k < m; ++k) scale = fmax(scale, cabs1(cadd(diag[k], v[k])));
-  const double tiny = 1e-300 + 1e-16 * scale;
-  cplx lmb = sel[q];
-  // eigenvector by inverse iteration at the QL eigenvalue
-  tri_lu(m, west, east, diag, v, lmb, lu);
-  for (int k = 0; k < m; ++k) x[k] = cmk(1.0, 0.0);
-  for (int it = 0; it < 3; ++it) {
-    tri_solve(m, lu, x, tiny);
-    max_normalise(m, x);
-  }
-  bilinear_normalise(m, w, x);
-  // two shift-and-invert refinement steps with a Rayleigh-quotient update
-  for (int it = 0; it < 2; ++it) {
+  if (ok && q < nb) {
+    cplx* base = scratch + m + (size_t)q * 5 * m;
+    TriLU lu{base, base + m, base + 2 * m, base + 3 * m,
+             reinterpret_cast<int*>(scratch + m + (size_t)nb * 5 * m) + (size_t)q * m};
+    cplx* x = base + 4 * m;
+    double scale = 0.0;
+    for (int k = 0; k < m; ++k) scale = fmax(scale, cabs1(cadd(diag[k], v[k])));
+    const double tiny = 1e-300 + 1e-16 * scale;
+    cplx lmb = sel[q];
+    for (int k = 0; k < m; ++k) x[k] = cmk(1.0, 0.0);
+    // two inverse-iteration steps at the single-precision estimate
     tri_lu(m, west, east, diag, v, lmb, lu);
-    tri_solve(m, lu, x, tiny);
-    max_normalise(m, x);
+    for (int it = 0; it < 2; ++it) {
+      tri_solve(m, lu, x, tiny);
+      max_normalise(m, x);
+    }
+    // Rayleigh-quotient iteration to the double-precision eigenvalue
+    for (int it = 0; it < 6; ++it) {
+      cplx ln = rayleigh_ratio(m, west, east, diag, v, w, x);
+      const bool conv = cabs1(csub(ln, lmb)) <= 1e-14 * fmax(1.0, cabs1(ln));
+      lmb = ln;
+      tri_lu(m, west, east, diag, v, lmb, lu);
+      tri_solve(m, lu, x, tiny);
+      max_normalise(m, x);
+      if (conv) break;
+    }
     bilinear_normalise(m, w, x);
-    lmb = rayleigh(m, west, east, diag, v, w, x);
+    // two shift-and-invert refinement steps with a Rayleigh-quotient update
+    for (int it = 0; it < 2; ++it) {
+      tri_lu(m, west, east, diag, v, lmb, lu);
+      tri_solve(m, lu, x, tiny);
+      max_normalise(m, x);
+      bilinear_normalise(m, w, x);
+      lmb = rayleigh(m, west, east, diag, v, w, x);
+    }
+    bool fin = isfinite(lmb.x) && isfinite(lmb.y);
+    for (int k = 0; k < m; ++k) {
+      phi[(size_t)q * m + k] = x[k];
+      fin = fin && isfinite(x[k].x) && isfinite(x[k].y);
+    }
+    lam[q] = lmb;
+    fin_l[q] = lmb;
+    if (!fin) atomicOr(status, MGC_ST_EIG);
   }
-  bool fin = isfinite(lmb.x) && isfinite(lmb.y);
-  for (int k = 0; k < m; ++k) {
-    phi[(size_t)q * m + k] = x[k];
-    fin = fin && isfinite(x[k].x) && isfinite(x[k].y);
+  __syncthreads();
+  if (ok && q == 0) {
+    // two states that refined onto the same eigenvalue mean the estimates were too poor
+    for (int a = 0; a < nb; ++a)
+      for (int b = a + 1; b < nb; ++b)
+        if (cabs1(csub(fin_l[a], fin_l[b])) <= 1e-10 * fmax(1.0, cabs1(fin_l[a]))) atomicOr(status, MGC_ST_EIG);
   }
-  lam[q] = lmb;
-  if (!fin) atomicOr(status, MGC_ST_EIG);
 }
 
 __global__ void k_weight_states(int m, int nb, const cplx* __restrict__ w, const cplx* __restrict__ phi,
@@ -417,30 +499,103 @@ __device__ bool small_inverse(int n, cplx* A /* n*n row-major, replaced by inver
   return true;
 }
 
-// Block-Thomas factors of the coupled-channel system along one axis:
-// B_k = (diag_k + v_k - E) I + diag(lam) + Vc_k,  G_0 = B_0^{-1},
-// G_k = (B_k - a_k c_{k-1} G_{k-1})^{-1}.
-__global__ void k_channel_factor(int m, int nb, const cplx* __restrict__ diag, const cplx* __restrict__ v,
-                                 double E, const cplx* __restrict__ lam, const cplx* __restrict__ Vc,
-                                 const cplx* __restrict__ a, const cplx* __restrict__ c, cplx* __restrict__ G,
-                                 int* status) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  cplx M[MGC_MAX_NB * MGC_MAX_NB];
-  for (int k = 0; k < m; ++k) {
-    cplx base = cadd(diag[k], v[k]);
-    base.x -= E;
-    for (int r = 0; r < nb; ++r)
-      for (int q = 0; q < nb; ++q) {
-        cplx val = Vc[((size_t)k * nb + r) * nb + q];
-        if (r == q) val = cadd(val, cadd(base, lam[r]));
-        if (k > 0) val = cfms(cmul(a[k], c[k - 1]), G[((size_t)(k - 1) * nb + r) * nb + q], val);
-        M[r * nb + q] = val;
-      }
-    if (!small_inverse(nb, M)) {
-      atomicOr(status, MGC_ST_PIVOT);
-      return;
+// C = A B for n x n row-major blocks.
+__device__ void small_matmul(int n, const cplx* A, const cplx* B, cplx* C) {
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) {
+      cplx acc = cmk(0.0, 0.0);
+      for (int k = 0; k < n; ++k) acc = cfma(A[r * n + k], B[k * n + c], acc);
+      C[r * n + c] = acc;
     }
-    for (int r = 0; r < nb * nb; ++r) G[(size_t)k * nb * nb + r] = M[r];
+}
+
+// Cyclic-reduction factors of the coupled-channel system along one axis (one block):
+// B_k = (diag_k + v_k - E) I + diag(lam) + Vc_k, A_k = a_k I, C_k = c_k I, rows padded
+// with identity to M = 2^q - 1.  `scratch` holds the current A, B, C of rows 0..M.
+__global__ void __launch_bounds__(256) k_channel_factor(CRSystem S, const cplx* __restrict__ diag,
+                                                        const cplx* __restrict__ v, double E,
+                                                        const cplx* __restrict__ lam, const cplx* __restrict__ Vc,
+                                                        const cplx* __restrict__ sub, const cplx* __restrict__ sup,
+                                                        cplx* __restrict__ scratch, int* status) {
+  const int nb = S.nb, nb2 = nb * nb, M = S.M, q = S.q, m = S.m;
+  cplx* Ac = scratch;
+  cplx* Bc = scratch + (size_t)(M + 1) * nb2;
+  cplx* Cc = scratch + (size_t)2 * (M + 1) * nb2;
+  const int t0 = threadIdx.x, nt = blockDim.x;
+  for (int i = 1 + t0; i <= M; i += nt) {
+    cplx* A = Ac + (size_t)i * nb2;
+    cplx* B = Bc + (size_t)i * nb2;
+    cplx* C = Cc + (size_t)i * nb2;
+    if (i <= m) {
+      const int k = i - 1;
+      cplx base = cadd(diag[k], v[k]);
+      base.x -= E;
+      for (int r = 0; r < nb; ++r)
+        for (int c = 0; c < nb; ++c) {
+          cplx val = Vc[((size_t)k * nb + r) * nb + c];
+          if (r == c) val = cadd(val, cadd(base, lam[r]));
+          B[r * nb + c] = val;
+          A[r * nb + c] = (r == c && k > 0) ? sub[k] : cmk(0.0, 0.0);
+          C[r * nb + c] = (r == c && k < m - 1) ? sup[k] : cmk(0.0, 0.0);
+        }
+    } else {
+      for (int r = 0; r < nb2; ++r) {
+        B[r] = cmk((r % (nb + 1)) == 0 ? 1.0 : 0.0, 0.0);
+        A[r] = cmk(0.0, 0.0);
+        C[r] = cmk(0.0, 0.0);
+      }
+    }
+  }
+  __syncthreads();
+  cplx T1[MGC_MAX_NB * MGC_MAX_NB], T2[MGC_MAX_NB * MGC_MAX_NB];
+  for (int l = 1; l < q; ++l) {
+    const int s = 1 << (l - 1);
+    // rows eliminated at this level: P = B^{-1}, Q = P A, R = P C
+    for (int j = s + 2 * s * t0; j <= M; j += 2 * s * nt) {
+      for (int r = 0; r < nb2; ++r) T1[r] = Bc[(size_t)j * nb2 + r];
+      if (!small_inverse(nb, T1)) {
+        atomicOr(status, MGC_ST_PIVOT);
+        for (int r = 0; r < nb2; ++r) T1[r] = cmk(0.0, 0.0);
+      }
+      for (int r = 0; r < nb2; ++r) S.P[(size_t)j * nb2 + r] = T1[r];
+      small_matmul(nb, T1, Ac + (size_t)j * nb2, S.Q + (size_t)j * nb2);
+      small_matmul(nb, T1, Cc + (size_t)j * nb2, S.R + (size_t)j * nb2);
+    }
+    __syncthreads();
+    // kept rows: alpha = A_i P_{i-s}, gamma = C_i P_{i+s}, then the reduced coefficients
+    const int nk = (1 << (q - l)) - 1;
+    const int off = cr_fwd_offset(q, l);
+    for (int t = 1 + t0; t <= nk; t += nt) {
+      const int i = 2 * s * t;
+      cplx* al = S.alpha + (size_t)(off + t - 1) * nb2;
+      cplx* ga = S.gamma + (size_t)(off + t - 1) * nb2;
+      small_matmul(nb, Ac + (size_t)i * nb2, S.P + (size_t)(i - s) * nb2, al);
+      small_matmul(nb, Cc + (size_t)i * nb2, S.P + (size_t)(i + s) * nb2, ga);
+      cplx* B = Bc + (size_t)i * nb2;
+      small_matmul(nb, al, Cc + (size_t)(i - s) * nb2, T1);
+      small_matmul(nb, ga, Ac + (size_t)(i + s) * nb2, T2);
+      for (int r = 0; r < nb2; ++r) B[r] = csub(csub(B[r], T1[r]), T2[r]);
+      small_matmul(nb, al, Ac + (size_t)(i - s) * nb2, T1);
+      small_matmul(nb, ga, Cc + (size_t)(i + s) * nb2, T2);
+      for (int r = 0; r < nb2; ++r) {
+        Ac[(size_t)i * nb2 + r] = cneg(T1[r]);
+        Cc[(size_t)i * nb2 + r] = cneg(T2[r]);
+      }
+    }
+    __syncthreads();
+  }
+  if (t0 == 0) {
+    const int root = 1 << (q - 1);
+    for (int r = 0; r < nb2; ++r) T1[r] = Bc[(size_t)root * nb2 + r];
+    if (!small_inverse(nb, T1)) {
+      atomicOr(status, MGC_ST_PIVOT);
+      for (int r = 0; r < nb2; ++r) T1[r] = cmk(0.0, 0.0);
+    }
+    for (int r = 0; r < nb2; ++r) {
+      S.P[(size_t)root * nb2 + r] = T1[r];
+      S.Q[(size_t)root * nb2 + r] = cmk(0.0, 0.0);
+      S.R[(size_t)root * nb2 + r] = cmk(0.0, 0.0);
+    }
   }
 }
 
@@ -460,14 +615,26 @@ cudaError_t launch_setup_diag(int mx, int my, int stride, int fine_mx, const cpl
   return cudaGetLastError();
 }
 
+cudaError_t launch_compare(int n, const cplx* a, const cplx* b, int* flag, cudaStream_t st) {
+  k_compare<<<(n + 255) / 256, 256, 0, st>>>(n, a, b, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_box_real_check(const StencilView& s, int* flag, cudaStream_t st) {
+  if (s.ux <= 0 || s.uy <= 0) return cudaSuccess;
+  k_box_real_check<<<dim3((s.ux + 31) / 32, (s.uy + 7) / 8), dim3(32, 8), 0, st>>>(s.mx, s.ux, s.uy, s.D, flag);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_coarse_inverse(const StencilView& s, cplx* aug, cplx* Ainv, int* status, cudaStream_t st) {
   k_coarse_inverse<<<1, 1024, 0, st>>>(s, aug, Ainv, status);
   return cudaGetLastError();
 }
 
 size_t bound_states_scratch(int m, int nb) {
-  // d, e + per state (u0, u1, u2, mu, x) + per state int pivots
-  return sizeof(cplx) * ((size_t)2 * m + (size_t)nb * 5 * m) + sizeof(int) * (size_t)nb * m;
+  // single-precision d, e (one complex128 slot per pair) + per state (u0, u1, u2, mu, x)
+  // + per state int pivots
+  return sizeof(cplx) * ((size_t)m + (size_t)nb * 5 * m) + sizeof(int) * (size_t)nb * m;
 }
 
 cudaError_t launch_bound_states(int m, const cplx* west, const cplx* east, const cplx* diag, const cplx* v,
@@ -495,9 +662,9 @@ cudaError_t launch_channel_potentials(int mx, int my, int nb, const cplx* wphi, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_channel_factor(int m, int nb, const cplx* diag, const cplx* v, double E, const cplx* lam,
-                                  const cplx* Vc, const cplx* a, const cplx* c, cplx* G, int* status,
+cudaError_t launch_channel_factor(const CRSystem& S, const cplx* diag, const cplx* v, double E, const cplx* lam,
+                                  const cplx* Vc, const cplx* a, const cplx* c, cplx* scratch, int* status,
                                   cudaStream_t st) {
-  k_channel_factor<<<1, 1, 0, st>>>(m, nb, diag, v, E, lam, Vc, a, c, G, status);
+  k_channel_factor<<<1, 256, 0, st>>>(S, diag, v, E, lam, Vc, a, c, scratch, status);
   return cudaGetLastError();
 }

@@ -33,7 +33,9 @@ struct mgcccs_handle {
   cplx* Ainv;
   cplx* aug;
   int nb;
-  cplx *lam, *mu, *phi, *vphi, *wphi, *wvphi, *VA, *VB, *GA, *GB;
+  cplx *lam, *mu, *phi, *vphi, *wphi, *wvphi, *VA, *VB;
+  CRSystem crA, crB;       // channel A (along y, x bound states), channel B (along x)
+  cplx* cr_scratch;
   cplx* eig_scratch;
   CCView cc;
   double* norm_part;
@@ -45,6 +47,12 @@ struct mgcccs_handle {
   int km;
   int kr_nblk;
   cplx *V, *Z, *Hh, *cs, *sn, *g, *y, *hc, *dotpart;
+  int* gate;
+  cudaStream_t cap_st;                       // capture stream for the step graphs
+  cudaGraphExec_t step_exec[MGC_MAX_RESTART];
+  long long step_launches[MGC_MAX_RESTART];
+  cudaEvent_t ev[2];
+  double* est_host;                          // pinned, one residual estimate per step
   long long launches;
 };
 
@@ -122,8 +130,25 @@ void layout(mgcccs_handle* h, Carver& cv) {
     h->wvphi = cv.take<cplx>((size_t)nb * my);
     h->VA = cv.take<cplx>((size_t)my * nb * nb);
     h->VB = cv.take<cplx>((size_t)mx * nb * nb);
-    h->GA = cv.take<cplx>((size_t)my * nb * nb);
-    h->GB = cv.take<cplx>((size_t)mx * nb * nb);
+    for (int c = 0; c < 2; ++c) {
+      CRSystem& S = c == 0 ? h->crA : h->crB;
+      S.m = c == 0 ? my : mx;
+      S.nb = nb;
+      S.q = cr_levels(S.m);
+      S.M = (1 << S.q) - 1;
+      const size_t nb2 = (size_t)nb * nb;
+      S.alpha = cv.take<cplx>((size_t)S.M * nb2);
+      S.gamma = cv.take<cplx>((size_t)S.M * nb2);
+      S.P = cv.take<cplx>((size_t)(S.M + 1) * nb2);
+      S.Q = cv.take<cplx>((size_t)(S.M + 1) * nb2);
+      S.R = cv.take<cplx>((size_t)(S.M + 1) * nb2);
+      S.X = cv.take<cplx>((size_t)(S.M + 2) * nb);
+      S.Y = cv.take<cplx>((size_t)(S.M + 2) * nb);
+    }
+    {
+      const int Mmax = h->crA.M > h->crB.M ? h->crA.M : h->crB.M;
+      h->cr_scratch = cv.take<cplx>((size_t)3 * (Mmax + 1) * nb * nb);
+    }
     size_t es = bound_states_scratch(mx > my ? mx : my, nb);
     h->eig_scratch = cv.take<cplx>((es + sizeof(cplx) - 1) / sizeof(cplx));
     CCView& cc = h->cc;
@@ -138,11 +163,8 @@ void layout(mgcccs_handle* h, Carver& cv) {
     cc.rB = cv.take<cplx>((size_t)nb * mx);
     cc.eA = cv.take<cplx>((size_t)nb * my);
     cc.eB = cv.take<cplx>((size_t)nb * mx);
-    cc.gA = cv.take<cplx>((size_t)nb * my);
-    cc.gB = cv.take<cplx>((size_t)nb * mx);
-    cc.GA = h->GA; cc.GB = h->GB;
-    cc.aA = h->lv[0].west_y; cc.cA = h->lv[0].east_y;
-    cc.aB = h->lv[0].west_x; cc.cB = h->lv[0].east_x;
+    h->crA.r = cc.rA; h->crA.e = cc.eA;
+    h->crB.r = cc.rB; h->crB.e = cc.eB;
   }
   StencilView s0{};
   s0.mx = mx; s0.my = my;
@@ -163,6 +185,7 @@ void layout(mgcccs_handle* h, Carver& cv) {
     h->y = cv.take<cplx>(m);
     h->hc = cv.take<cplx>(m + 1);
     h->dotpart = cv.take<cplx>((size_t)(m + 1) * h->kr_nblk);
+    h->gate = cv.take<int>(4);
     if (h->kr_nblk > h->norm_nparts) h->norm_nparts = h->kr_nblk;
   }
   h->norm_part = cv.take<double>(h->norm_nparts);
@@ -234,6 +257,20 @@ int do_setup(mgcccs_handle* h, const cplx* v1, const cplx* v2, const cplx* v12) 
       s.ux = s.uy = 0;
       s.cu = cmk(0.0, 0.0);
     }
+    s.rbox = 0;
+  }
+  // a level whose uniform box has a real coefficient and a real diagonal everywhere
+  // uses the real-coefficient path there (scan on the device, flag read back)
+  for (int l = 0; l < h->L; ++l) {
+    StencilView& s = h->lv[l].sv;
+    if (s.ux > 0 && s.cu.y == 0.0) {
+      int complex_seen = 0;
+      MGC_CUDA(cudaMemsetAsync(h->status + 3, 0, sizeof(int), st));
+      MGC_LAUNCH(launch_box_real_check(s, h->status + 3, st));
+      MGC_CUDA(cudaMemcpyAsync(&complex_seen, h->status + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+      MGC_CUDA(cudaStreamSynchronize(st));
+      s.rbox = complex_seen ? 0 : 1;
+    }
   }
   MGC_LAUNCH(launch_coarse_inverse(h->lv[h->L - 1].sv, h->aug, h->Ainv, h->status, st));
   if (h->nb > 0) {
@@ -241,16 +278,31 @@ int do_setup(mgcccs_handle* h, const cplx* v1, const cplx* v2, const cplx* v12) 
     const int nb = h->nb;
     MGC_LAUNCH(launch_bound_states(b.mx, b.west_x, b.east_x, b.diag_x, v1, b.w_x, nb, h->lam, h->phi,
                                    h->eig_scratch, h->status, st));
-    MGC_LAUNCH(launch_bound_states(b.my, b.west_y, b.east_y, b.diag_y, v2, b.w_y, nb, h->mu, h->vphi,
-                                   h->eig_scratch, h->status, st));
+    // the y eigenproblem is the x one when both axes and potentials coincide (square TP grids)
+    bool same = p.nx == p.ny && p.Lx == p.Ly && p.R0x == p.R0y;
+    if (same) {
+      int differs = 0;
+      MGC_CUDA(cudaMemsetAsync(h->status + 3, 0, sizeof(int), st));
+      MGC_LAUNCH(launch_compare(b.mx, v1, v2, h->status + 3, st));
+      MGC_CUDA(cudaMemcpyAsync(&differs, h->status + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+      MGC_CUDA(cudaStreamSynchronize(st));
+      same = differs == 0;
+    }
+    if (same) {
+      MGC_CUDA(cudaMemcpyAsync(h->mu, h->lam, sizeof(cplx) * nb, cudaMemcpyDeviceToDevice, st));
+      MGC_CUDA(cudaMemcpyAsync(h->vphi, h->phi, sizeof(cplx) * nb * b.mx, cudaMemcpyDeviceToDevice, st));
+    } else {
+      MGC_LAUNCH(launch_bound_states(b.my, b.west_y, b.east_y, b.diag_y, v2, b.w_y, nb, h->mu, h->vphi,
+                                     h->eig_scratch, h->status, st));
+    }
     MGC_LAUNCH(launch_weight_states(b.mx, nb, b.w_x, h->phi, h->wphi, st));
     MGC_LAUNCH(launch_weight_states(b.my, nb, b.w_y, h->vphi, h->wvphi, st));
     MGC_LAUNCH(launch_channel_potentials(b.mx, b.my, nb, h->wphi, h->phi, h->wvphi, h->vphi, v12, h->VA, h->VB,
                                          st));
     // channel A runs along y with the x bound states; channel B along x with the y ones
-    MGC_LAUNCH(launch_channel_factor(b.my, nb, b.diag_y, v2, p.E, h->lam, h->VA, b.west_y, b.east_y, h->GA,
+    MGC_LAUNCH(launch_channel_factor(h->crA, b.diag_y, v2, p.E, h->lam, h->VA, b.west_y, b.east_y, h->cr_scratch,
                                      h->status, st));
-    MGC_LAUNCH(launch_channel_factor(b.mx, nb, b.diag_x, v1, p.E, h->mu, h->VB, b.west_x, b.east_x, h->GB,
+    MGC_LAUNCH(launch_channel_factor(h->crB, b.diag_x, v1, p.E, h->mu, h->VB, b.west_x, b.east_x, h->cr_scratch,
                                      h->status, st));
   }
   return read_status(h);
@@ -310,7 +362,7 @@ int cccs_fine(mgcccs_handle* h, cplx* u, const cplx* f) {
   MGC_LAUNCH(launch_residual_project(h->lv[0].sv, h->cc, u, f, st));
   MGC_LAUNCH(launch_cc_rhs(h->cc, st));
   h->launches += 2;   // launch_cc_rhs issues three kernels
-  MGC_LAUNCH(launch_channel_solve(h->cc, st));
+  MGC_LAUNCH(launch_channel_solve(h->crA, h->crB, st));
   MGC_LAUNCH(launch_cccs_correct(h->cc, u, st));
   return MGCCCS_OK;
 }
@@ -352,9 +404,78 @@ int precond(mgcccs_handle* h, cplx* z, const cplx* r) {
   return rc;
 }
 
-// Restarted GMRES(m), right-preconditioned by one MG-CCCS iteration; Arnoldi with
-// classical Gram-Schmidt applied twice; Givens rotations and the triangular solve on
-// the device.  Counts Arnoldi steps as iterations.
+// Arnoldi step j of GMRES(m): z_j = M^{-1} v_j, w = A z_j, classical Gram-Schmidt with
+// a DGKS-gated second pass, h_{j+1,j} = |w|, v_{j+1} = w / h_{j+1,j}, Givens rotation j,
+// and the residual estimate |g_{j+1}| copied to est_host[j].  Touches only buffers of
+// the handle, so the launch sequence of each j is fixed and can be replayed as a graph.
+int issue_arnoldi_step(mgcccs_handle* h, int j) {
+  cudaStream_t st = h->st;
+  const int m = h->km;
+  const StencilView& s0 = h->lv[0].sv;
+  const long long N = (long long)s0.mx * s0.my;
+  const int nb = h->kr_nblk;
+  cplx* vj = h->V + (size_t)j * N;
+  cplx* w = h->V + (size_t)(j + 1) * N;
+  cplx* zj = h->Z + (size_t)j * N;
+  cplx* col = h->Hh + (size_t)j * (m + 1);
+  int rc = precond(h, zj, vj);
+  if (rc) return rc;
+  // w = A z_j, with |w|^2 for the reorthogonalisation test
+  MGC_LAUNCH(launch_apply(s0, zj, w, st, h->norm_part));
+  MGC_LAUNCH(launch_sum_partials(h->norm_part, residual_norm_blocks(s0), h->norm_out + 3, st));
+  // Gram-Schmidt, first pass: H(0:j, j) = V^H w ; w -= V H(0:j, j)
+  MGC_LAUNCH(launch_multidot(N, j + 1, h->V, N, w, h->dotpart, nb, nullptr, st));
+  MGC_LAUNCH(launch_reduce_dots(nb, j + 1, h->dotpart, col, nullptr, st));
+  MGC_LAUNCH(launch_multiaxpy(N, j + 1, h->V, N, col, -1.0, w, h->norm_part, nb, nullptr, st));
+  MGC_LAUNCH(launch_sum_partials(h->norm_part, nb, h->norm_out + 1, st));
+  // second pass only when the first one cancelled more than half of |w|^2 (DGKS);
+  // the corrections are added into H(0:j, j)
+  MGC_LAUNCH(launch_dgks(h->norm_out + 3, h->norm_out + 1, h->gate, st));
+  MGC_LAUNCH(launch_multidot(N, j + 1, h->V, N, w, h->dotpart, nb, h->gate, st));
+  MGC_LAUNCH(launch_reduce_dots(nb, j + 1, h->dotpart, h->hc, col, st));
+  MGC_LAUNCH(launch_multiaxpy(N, j + 1, h->V, N, h->hc, -1.0, w, h->norm_part, nb, h->gate, st));
+  MGC_LAUNCH(launch_sum_partials(h->norm_part, nb, h->norm_out + 1, st, h->gate));
+  MGC_LAUNCH(launch_scale_by_norm(N, w, w, h->norm_out + 1, col + j + 1, nb, st));
+  MGC_LAUNCH(launch_givens(j, m, h->Hh, h->cs, h->sn, h->g, h->norm_out + 2, st));
+  MGC_CUDA(cudaMemcpyAsync(h->est_host + j, h->norm_out + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+  return MGCCCS_OK;
+}
+
+// Launch Arnoldi step j: replay its graph, capturing it on first use.
+int launch_arnoldi_step(mgcccs_handle* h, int j) {
+  if (!h->step_exec[j]) {
+    cudaStream_t orig = h->st;
+    const long long before = h->launches;
+    h->st = h->cap_st;
+    MGC_CUDA(cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal));
+    int rc = issue_arnoldi_step(h, j);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap_st, &g);
+    h->st = orig;
+    h->step_launches[j] = h->launches - before;
+    h->launches = before;
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return MGCCCS_ECUDA;
+    e = cudaGraphInstantiate(&h->step_exec[j], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      h->step_exec[j] = nullptr;
+      return MGCCCS_ECUDA;
+    }
+  }
+  MGC_CUDA(cudaGraphLaunch(h->step_exec[j], h->st));
+  h->launches += h->step_launches[j];
+  return MGCCCS_OK;
+}
+
+// Restarted GMRES(m), right-preconditioned by one MG-CCCS iteration (graph-replayed
+// Arnoldi steps).  The host checks the residual estimate of step j-1 while step j
+// runs, so the device never waits for the host inside a cycle; a step launched after
+// convergence is simply not used (the solution only needs columns and g entries
+// below it).  Counts Arnoldi steps as iterations.
 int gmres_impl(mgcccs_handle* h, cplx* u, const cplx* f, double fn, double rtol, int max_iter, int* iters,
                double* relres, double* history) {
   cudaStream_t st = h->st;
@@ -381,45 +502,42 @@ int gmres_impl(mgcccs_handle* h, cplx* u, const cplx* f, double fn, double rtol,
     MGC_LAUNCH(launch_zero_c(m + 1, h->g, st));
     MGC_LAUNCH(launch_scale_by_norm(N, h->V, h->V, h->norm_out, h->g, nb, st));
     int k = 0;
-    for (int j = 0; j < m; ++j) {
-      cplx* vj = h->V + (size_t)j * N;
-      cplx* w = h->V + (size_t)(j + 1) * N;
-      cplx* zj = h->Z + (size_t)j * N;
-      cplx* col = h->Hh + (size_t)j * (m + 1);
-      rc = precond(h, zj, vj);
-      if (rc) return rc;
-      MGC_LAUNCH(launch_apply(s0, zj, w, st));
-      // Gram-Schmidt, first pass: H(0:j, j) = V^H w ; w -= V H(0:j, j)
-      MGC_LAUNCH(launch_multidot(N, j + 1, h->V, N, w, h->dotpart, nb, st));
-      MGC_LAUNCH(launch_reduce_dots(nb, j + 1, h->dotpart, col, nullptr, st));
-      MGC_LAUNCH(launch_multiaxpy(N, j + 1, h->V, N, col, -1.0, w, nullptr, nb, st));
-      // second pass: corrections added into H(0:j, j); |w|^2 partials for h_{j+1,j}
-      MGC_LAUNCH(launch_multidot(N, j + 1, h->V, N, w, h->dotpart, nb, st));
-      MGC_LAUNCH(launch_reduce_dots(nb, j + 1, h->dotpart, h->hc, col, st));
-      MGC_LAUNCH(launch_multiaxpy(N, j + 1, h->V, N, h->hc, -1.0, w, h->norm_part, nb, st));
-      MGC_LAUNCH(launch_sum_partials(h->norm_part, nb, h->norm_out + 1, st));
-      MGC_LAUNCH(launch_scale_by_norm(N, w, w, h->norm_out + 1, col + j + 1, nb, st));
-      MGC_LAUNCH(launch_givens(j, m, h->Hh, h->cs, h->sn, h->g, h->norm_out + 2, st));
-      double est = 0.0;
-      rc = read_double(h, h->norm_out + 2, &est);
-      if (rc) return rc;
-      est /= fn;
+    bool nonfinite = false;
+    for (int j = 0; j <= m; ++j) {
+      if (j < m) {
+        rc = launch_arnoldi_step(h, j);
+        if (rc) return rc;
+        MGC_CUDA(cudaEventRecord(h->ev[j & 1], st));
+      }
+      if (j == 0) continue;
+      // residual estimate of step j-1 (step j, if launched, runs meanwhile)
+      MGC_CUDA(cudaEventSynchronize(h->ev[(j - 1) & 1]));
+      const double est = h->est_host[j - 1] / fn;
       if (history) history[steps] = est;
       ++steps;
-      k = j + 1;
-      if (!std::isfinite(est)) {
-        if (iters) *iters = steps;
-        if (relres) *relres = est;
-        return MGCCCS_ENONFINITE;
-      }
+      k = j;
+      if (!std::isfinite(est)) { nonfinite = true; break; }
       if (est <= rtol || steps >= max_iter) break;
     }
+    if (nonfinite) {
+      MGC_CUDA(cudaStreamSynchronize(st));
+      if (iters) *iters = steps;
+      if (relres) *relres = NAN;
+      return MGCCCS_ENONFINITE;
+    }
     MGC_LAUNCH(launch_hess_solve(k, m, h->Hh, h->g, h->y, st));
-    MGC_LAUNCH(launch_multiaxpy(N, k, h->Z, N, h->y, 1.0, u, nullptr, nb, st));
+    MGC_LAUNCH(launch_multiaxpy(N, k, h->Z, N, h->y, 1.0, u, nullptr, nb, nullptr, st));
   }
   if (iters) *iters = steps;
   if (relres) *relres = rr;
   return rr <= rtol ? MGCCCS_OK : MGCCCS_ENOTCONV;
+}
+
+int create_krylov_objects(mgcccs_handle* h) {
+  MGC_CUDA(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+  for (int q = 0; q < 2; ++q) MGC_CUDA(cudaEventCreateWithFlags(&h->ev[q], cudaEventDisableTiming));
+  MGC_CUDA(cudaMallocHost(reinterpret_cast<void**>(&h->est_host), sizeof(double) * MGC_MAX_RESTART));
+  return MGCCCS_OK;
 }
 
 int solve_impl(mgcccs_handle* h, cplx* u, const cplx* f, double rtol, int max_iter, int* iters, double* relres,
@@ -495,8 +613,9 @@ int mgcccs_setup(mgcccs_t* out, const mgcccs_params* p, const mgcccs_c128* v1, c
   layout(h, cv);
   int rc = do_setup(h, reinterpret_cast<const cplx*>(v1), reinterpret_cast<const cplx*>(v2),
                     reinterpret_cast<const cplx*>(v12));
+  if (!rc && h->km > 0) rc = create_krylov_objects(h);
   if (rc) {
-    delete h;
+    mgcccs_destroy(h);
     return rc;
   }
   *out = h;
@@ -623,6 +742,15 @@ const char* mgcccs_strerror(int code) {
   return "unknown error code";
 }
 
-void mgcccs_destroy(mgcccs_t h) { delete h; }
+void mgcccs_destroy(mgcccs_t h) {
+  if (!h) return;
+  for (int j = 0; j < MGC_MAX_RESTART; ++j)
+    if (h->step_exec[j]) cudaGraphExecDestroy(h->step_exec[j]);
+  for (int q = 0; q < 2; ++q)
+    if (h->ev[q]) cudaEventDestroy(h->ev[q]);
+  if (h->cap_st) cudaStreamDestroy(h->cap_st);
+  if (h->est_host) cudaFreeHost(h->est_host);
+  delete h;
+}
 
 }  // extern "C"
