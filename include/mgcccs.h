@@ -171,6 +171,27 @@ int mgcccs_coarse_solve(mgcccs_t h, const mgcccs_c128* f, mgcccs_c128* u);
 int mgcccs_get_bound_states(mgcccs_t h, mgcccs_c128* lambda, mgcccs_c128* phi,
                             mgcccs_c128* mu, mgcccs_c128* vphi);
 
+/* ---- allocation-free helper (the paper has no counterpart) -----------------
+ * Some callers cannot call cudaMalloc: code that runs while a CUDA graph is being
+ * captured in the global capture mode (allocation calls are illegal there), code
+ * inside a framework whose caching allocator owns all device memory under a hard
+ * cap, and latency-critical loops that must avoid the device synchronisation an
+ * allocation can trigger.  mgcccs_norm2_noalloc needs neither a handle nor a
+ * workspace: it writes sum_k |v_k|^2 (the squared 2-norm used for relative
+ * residuals) of the device complex128 vector v[0..n) to the device double
+ * *norm2, on `stream` (cudaStream_t as void*; NULL = legacy default stream),
+ * asynchronously.  Its scratch is a file-scope device array of
+ * MGCCCS_NOALLOC_MAX_N / 2048 doubles (32 KiB) that every GPU which loads the
+ * library keeps until the process exits.  The first call on a device looks up
+ * that array's device address (with that device current); make that first call
+ * before any stream capture.  All calls share the one array and each call
+ * overwrites the slots it uses, so calls that overlap on the GPU (on different
+ * streams, or from several host threads) race and give wrong sums.
+ * Returns MGCCCS_EINVAL for a NULL pointer or n > MGCCCS_NOALLOC_MAX_N (nothing is
+ * launched), MGCCCS_ECUDA if the address lookup or a launch fails. */
+#define MGCCCS_NOALLOC_MAX_N 8388608
+int mgcccs_norm2_noalloc(const mgcccs_c128* v, size_t n, double* norm2, void* stream);
+
 /* Number of kernel launches issued since setup (for launch accounting). */
 long long mgcccs_launch_count(mgcccs_t h);
 

@@ -63,6 +63,7 @@ _SIGS = {
     "mgcccs_coarse_solve": (_i, [_vp, _vp, _vp]),
     "mgcccs_get_bound_states": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "mgcccs_launch_count": (ctypes.c_longlong, [_vp]),
+    "mgcccs_norm2_noalloc": (_i, [_vp, ctypes.c_size_t, _vp, _vp]),
     "mgcccs_strerror": (ctypes.c_char_p, [_i]),
     "mgcccs_destroy": (None, [_vp]),
 }
@@ -99,6 +100,22 @@ def _check(code: int, where: str) -> int:
     if code != OK:
         raise MGCCCSError(code, where)
     return code
+
+
+NOALLOC_MAX_N = 8388608
+
+
+def mgcccs_norm2_noalloc(v, out, stream=None):
+    """Squared 2-norm of a complex128 CUDA tensor into a float64 CUDA tensor `out`
+    (one element), without any workspace (see include/mgcccs.h)."""
+    import torch
+    if v.dtype != torch.complex128 or not v.is_cuda or not v.is_contiguous():
+        raise TypeError("v must be a contiguous complex128 CUDA tensor")
+    if out.dtype != torch.float64 or not out.is_cuda or out.numel() < 1:
+        raise TypeError("out must be a float64 CUDA tensor")
+    st = stream if stream is not None else torch.cuda.current_stream(v.device)
+    _check(lib().mgcccs_norm2_noalloc(v.data_ptr(), v.numel(), out.data_ptr(), st.cuda_stream),
+           "mgcccs_norm2_noalloc")
 
 
 def make_params(nx, ny, Lx, Ly, R0x, R0y, theta, E, levels=5, nu1=1, nu2=1, omega=2.0 / 3.0, n_b=3,
