@@ -52,7 +52,11 @@ def parse():
     ap.add_argument("--max-iter", type=int, default=2000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["bench", "solve-only", "kernel"], default="bench",
+    ap.add_argument("--box", type=float, default=30.0, help="box length L of [0,L]^2")
+    ap.add_argument("--R0", type=float, default=20.0, help="ECS start")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--mode", choices=["bench", "solve-only", "kernel", "adjoint", "sweep", "precision"],
+                    default="bench",
                     help="solve-only: setup + warm-up + timed solves, nothing else (for launch lists); "
                          "kernel: setup + 6 launches of one kernel (for ncu captures)")
     ap.add_argument("--kernel", choices=["jacobi", "residual_project", "multidot"], default="jacobi")
@@ -61,9 +65,11 @@ def parse():
 
 def workload(args):
     from paper_1412_1953_gb300 import inputs
-    prob = inputs.temkin_poet(args.n, L=30.0, R0=20.0, theta=math.pi / 6, E=args.E, seed=0)
-    cfg = {"workload": f"tp_ecs_{args.n}", "grid_cells": [args.n, args.n], "box": [30.0, 30.0],
-           "ecs": {"R0": 20.0, "theta": "pi/6"}, "unknowns": prob.n_unknowns, "E": args.E,
+    prob = inputs.temkin_poet(args.n, L=args.box, R0=args.R0, theta=math.pi / 6, E=args.E, seed=0)
+    name = f"tp_ecs_{args.n}" if (args.box, args.R0) == (30.0, 20.0) else f"tp_ecs_{args.n}_L{args.box:g}"
+    cfg = {"workload": name, "grid_cells": [args.n, args.n], "box": [args.box, args.box],
+           "ecs": {"R0": args.R0, "theta": "pi/6"}, "unknowns": prob.n_unknowns, "E": args.E,
+           "precision": "complex64 inner cycles in FP64 refinement" if args.precision == "mixed" else "complex128",
            "n_b": args.nb, "levels": args.levels, "cycle": "V(1,1), omega=2/3 Jacobi, FW, bilinear",
            "coarse_contour_deg": 14.6, "rtol": args.rtol,
            "outer": f"GMRES({args.krylov}) right-preconditioned by one MG-CCCS iteration" if args.krylov
@@ -260,6 +266,132 @@ def run_kernel(args):
     print(json.dumps({"mode": "kernel", "kernel": args.kernel, "workload": cfg["workload"]}))
 
 
+def run_adjoint(args):
+    """Differentiation workload: J = <g|u> on the 1024^2 TP problem (Z = 1, E = 0.5),
+    g a Gaussian window at (15, 15) with sigma = 2; forward + adjoint solve timed, and
+    dJ/dE, dJ/dZ, dJ/d(dV) at two nodes checked against central differences (step 1e-6)."""
+    import torch
+    from paper_1412_1953_gb300 import adjoint as A
+    from paper_1412_1953_gb300 import build as B
+    B.build()
+    n = args.n
+    geom = dict(n=n, L=30.0, R0=20.0, theta=math.pi / 6)
+    kw = dict(levels=args.levels, n_b=args.nb, krylov_restart=args.krylov)
+    prob, cfg = workload(args)
+    f = torch.as_tensor(prob.f).to("cuda")
+    g = torch.as_tensor(inputs_gaussian(n)).to("cuda")
+    dV0 = torch.zeros(prob.f.shape, dtype=torch.float64, device="cuda")
+    rtol = 1e-11
+    A.amplitude_and_gradients(args.E, 1.0, dV0, f, g, geom, kw, rtol=rtol)        # warm-up
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    res = A.amplitude_and_gradients(args.E, 1.0, dV0, f, g, geom, kw, rtol=rtol)
+    torch.cuda.synchronize()
+    t_fb = time.perf_counter() - t
+    h = 1e-6
+    J = lambda E_, Z_, dV_: A.amplitude_and_gradients(E_, Z_, dV_, f, g, geom, kw, rtol=rtol)["J"]
+    fdE = (J(args.E + h, 1.0, dV0) - J(args.E - h, 1.0, dV0)) / (2 * h)
+    fdZ = (J(args.E, 1.0 + h, dV0) - J(args.E, 1.0 - h, dV0)) / (2 * h)
+    nodes = [(n // 2 - 1, n // 2 - 1), (n // 2 + 40, n // 2 - 60)]
+    dv_err = []
+    for (j, i) in nodes:
+        e = torch.zeros_like(dV0)
+        e[j, i] = h
+        fd = (J(args.E, 1.0, dV0 + e) - J(args.E, 1.0, dV0 - e)) / (2 * h)
+        dv_err.append(abs(res["ddV"][j, i].item() - fd) / abs(fd))
+    out = {"mode": "adjoint", "workload": f"tp_ecs_{n}_adjoint", "J": [res["J"].real, res["J"].imag],
+           "dJ_dE": [res["dE"].real, res["dE"].imag], "dJ_dZ": [res["dZ"].real, res["dZ"].imag],
+           "fd_rel_err_E": abs(res["dE"] - fdE) / abs(fdE), "fd_rel_err_Z": abs(res["dZ"] - fdZ) / abs(fdZ),
+           "fd_rel_err_dV": dv_err, "fd_step": h, "rtol": rtol, "forward_adjoint_steps": list(res["its"]),
+           "seconds_setup_forward_adjoint": t_fb,
+           "unknowns_per_s_forward_plus_adjoint": prob.n_unknowns / t_fb}
+    print(json.dumps(out), flush=True)
+
+
+def inputs_gaussian(n):
+    from paper_1412_1953_gb300 import inputs
+    return inputs.gaussian_window(n, 30.0, 15.0, 15.0, 2.0)
+
+
+def run_sweep(args):
+    """Iteration counts and times of plain MG and MG-CCCS, stand-alone and as the
+    GMRES(20) preconditioner, over E in {0.3, 0.5, 1.5} and n_b in {3, 6}."""
+    import torch
+    from paper_1412_1953_gb300 import build as B
+    from paper_1412_1953_gb300 import inputs
+    from paper_1412_1953_gb300 import mgcccs as M
+    B.build()
+    for n, lv in [(512, 7), (1024, 8)]:
+        for E in (0.3, 0.5, 1.5):
+            prob = inputs.temkin_poet(n, E=E, seed=0)
+            f = torch.as_tensor(prob.f).to("cuda")
+            for nb in (0, 3, 6):
+                for kr in (0, 20):
+                    try:
+                        sv = M.Solver(M.params_for(prob, levels=lv, n_b=nb, krylov_restart=kr), prob.v1, prob.v2,
+                                      prob.v12)
+                    except M.MGCCCSError as exc:
+                        print(json.dumps({"mode": "sweep", "n": n, "E": E, "n_b": nb, "krylov": kr,
+                                          "error": str(exc)}), flush=True)
+                        continue
+                    u = torch.zeros_like(f)
+                    sv.solve(u, f, rtol=1e-10, max_iter=5, raise_on_notconv=False)   # warm-up / graphs
+                    u.zero_()
+                    torch.cuda.synchronize()
+                    t = time.perf_counter()
+                    its, rr = sv.solve(u, f, rtol=1e-10, max_iter=400 if kr else 300, raise_on_notconv=False)
+                    torch.cuda.synchronize()
+                    el = time.perf_counter() - t
+                    print(json.dumps({"mode": "sweep", "n": n, "levels": lv, "E": E, "n_b": nb,
+                                      "outer": f"GMRES({kr})" if kr else "stand-alone", "iterations": its,
+                                      "relres": rr, "seconds": el,
+                                      "unknowns_per_s": prob.n_unknowns / el if rr <= 1e-10 else None}),
+                          flush=True)
+                    sv.close()
+
+
+def run_precision(args):
+    """Precision form: the same workload solved to rtol by plain FP64 GMRES(m)+MG-CCCS and
+    by the mixed form; time, iterations, relres under the oracle's FP64 operator, and the
+    mixed solution's relative difference from the FP64 one."""
+    import torch
+    from oracle import mgcccs_oracle as O
+    from paper_1412_1953_gb300 import build as B
+    from paper_1412_1953_gb300 import mgcccs as M
+    B.build()
+    prob, cfg = workload(args)
+    f = torch.as_tensor(prob.f).to("cuda")
+    lev = O.build_levels(O.params_from_problem(prob, levels=1, n_b=0), prob.v1, prob.v2, prob.v12)[0]
+    res, sols = {}, {}
+    for prec in ("fp64", "mixed"):
+        sv = M.Solver(M.params_for(prob, levels=args.levels, n_b=args.nb, krylov_restart=args.krylov,
+                                   precision=1 if prec == "mixed" else 0), prob.v1, prob.v2, prob.v12)
+        u = torch.zeros_like(f)
+        for _ in range(2):
+            u.zero_()
+            sv.solve(u, f, rtol=args.rtol, max_iter=args.max_iter)
+        times = []
+        for _ in range(max(1, args.steps)):
+            u.zero_()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            its, rr = sv.solve(u, f, rtol=args.rtol, max_iter=args.max_iter)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t)
+        uh = u.cpu().numpy()
+        sols[prec] = uh
+        t_med = statistics.median(times)
+        res[prec] = {"seconds": t_med, "iterations": its, "relres": rr,
+                     "relres_oracle_operator": float(O.relres(lev, uh, prob.f)) if hasattr(O, "relres") else
+                     float(np.linalg.norm(O.residual(lev, uh, prob.f)) / np.linalg.norm(prob.f)),
+                     "unknowns_per_s": prob.n_unknowns / t_med}
+        sv.close()
+    diff = float(np.linalg.norm(sols["mixed"] - sols["fp64"]) / np.linalg.norm(sols["fp64"]))
+    print(json.dumps({"mode": "precision", "config": cfg, "fp64": res["fp64"], "mixed": res["mixed"],
+                      "mixed_vs_fp64_rel_diff": diff,
+                      "speedup": res["fp64"]["seconds"] / res["mixed"]["seconds"]}), flush=True)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -274,7 +406,8 @@ def run_ours(args):
     prob, cfg = workload(args)
     N = prob.n_unknowns
     t0 = time.perf_counter()
-    solver = M.Solver(M.params_for(prob, levels=args.levels, n_b=args.nb, krylov_restart=args.krylov),
+    solver = M.Solver(M.params_for(prob, levels=args.levels, n_b=args.nb, krylov_restart=args.krylov,
+                                   precision=1 if args.precision == "mixed" else 0),
                       prob.v1, prob.v2, prob.v12)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
@@ -369,8 +502,9 @@ def run_ours(args):
                 "l2": "flushed before every timed step (256 MB write); working set 0.1 GB"})
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "c128 (FP64)", "data": "synthetic",
-           "config": cfg, "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches),
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "c64 inner / c128 refinement" if args.precision == "mixed" else "c128 (FP64)",
+           "data": "synthetic", "config": cfg, "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches),
            "clocks": clocks}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_step, k, osetup = oracle_step_time(prob, args, args.cpu_seconds)
@@ -437,6 +571,12 @@ def main():
         run_reference(args)
     elif args.mode == "kernel":
         run_kernel(args)
+    elif args.mode == "adjoint":
+        run_adjoint(args)
+    elif args.mode == "sweep":
+        run_sweep(args)
+    elif args.mode == "precision":
+        run_precision(args)
     else:
         run_ours(args)
 

@@ -73,6 +73,14 @@ typedef struct {
   int krylov_restart;    /* outer solver of mgcccs_solve: 0 = stand-alone MG-CCCS
                             iteration; m in 1..60 = GMRES(m) right-preconditioned by
                             one MG-CCCS iteration per Arnoldi step (Sec. 6) */
+  int precision;         /* 0: complex128 throughout.  1 (needs krylov_restart >= 1):
+                            iterative refinement with the residual and solution in
+                            FP64 around complex64 GMRES(m) cycles whose MG-CCCS
+                            preconditioner smooths, restricts, interpolates and
+                            projects in complex64; the bound states, channel solves,
+                            coarsest solve and Hessenberg stay FP64 */
+  double inner_rtol;     /* precision 1: relative residual reduction asked of each
+                            complex64 cycle (0 selects 1e-5) */
 } mgcccs_params;
 
 /* Bytes of device workspace needed for `p` (0 when p is invalid). */
@@ -137,7 +145,8 @@ int mgcccs_solve_host(mgcccs_t h, mgcccs_c128* u_host, const mgcccs_c128* f_host
 
 /* Preconditioner application z = M^{-1} r (Sec. 6: one V-cycle, then the
  * CCCS when n_b > 0, from a zero initial guess).  z, r: device, distinct.
- * Async. */
+ * With precision 1 the complex64 preconditioner is applied to r rounded to
+ * complex64 and z is its exact widening.  Async. */
 int mgcccs_precond_apply(mgcccs_t h, mgcccs_c128* z, const mgcccs_c128* r);
 
 /* y = (H-E)x on the fine level (Eq. (11)); x, y: device, distinct.  Async. */
@@ -148,6 +157,23 @@ int mgcccs_matvec(mgcccs_t h, const mgcccs_c128* x, mgcccs_c128* y);
  * r may not alias u. */
 int mgcccs_residual(mgcccs_t h, const mgcccs_c128* u, const mgcccs_c128* f,
                     mgcccs_c128* r, double* norm2);
+
+/* ---- amplitude functional and adjoint gradients ----------------------------
+ * With w_k = w_x(i) w_y(j) the fine-level quadrature weights (h_{i-1}+h_i)/2 of the
+ * ECS contour (the weights of the bilinear normalisation, Sec. 3.1), the amplitude
+ * J = <g|u> = sum_k w_k g_k u_k is bilinear (no conjugation).  W(H-E) is complex
+ * symmetric (Sec. 2.5), so the adjoint of (H-E)u = f for J is the forward problem
+ * (H-E) mu = g (solve it with mgcccs_solve), and for any parameter p of H - E,
+ * dJ/dp = -sum_k w_k mu_k ((d(H-E)/dp) u)_k.  The two entry points below form these
+ * sums and products; a, b, d, out are device arrays of (nx-1)*(ny-1) values (out of
+ * mgcccs_weighted_dot is one device value).  Async. */
+
+/* *out = scale * sum_k w_k a_k b_k d_k  (d may be NULL: d_k = 1).  Deterministic order. */
+int mgcccs_weighted_dot(mgcccs_t h, const mgcccs_c128* a, const mgcccs_c128* b, const mgcccs_c128* d,
+                        mgcccs_c128 scale, mgcccs_c128* out);
+/* out_k = scale * w_k a_k b_k  (e.g. dJ/d(dV_k) = -w_k mu_k u_k with scale = -1). */
+int mgcccs_weighted_product(mgcccs_t h, const mgcccs_c128* a, const mgcccs_c128* b, mgcccs_c128 scale,
+                            mgcccs_c128* out);
 
 /* ---- single steps of the V-cycle, for component checks (Sec. 3.2) ---------
  * `level` counts from 0 (fine).  Arrays are device, interior-sized for the

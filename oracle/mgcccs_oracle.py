@@ -496,3 +496,28 @@ def gmres(solver: Solver, f: np.ndarray, m: int = 20, rtol: float = 1e-10, max_i
             if np.linalg.norm(f - A(u)) <= rtol * fn:
                 break
     return u, hist, np.linalg.norm(f - A(u)) / fn
+
+
+# --------------------------------------------------------------------------------------
+# Amplitude functional and its adjoint gradients (differentiation form)
+# --------------------------------------------------------------------------------------
+# J = <g|u> = sum_k w_k g_k u_k (bilinear, quadrature weights of Sec. 3.1's
+# normalisation, no conjugation), u solving (H - E)u = f with f held fixed.
+# Because W (H - E) is complex symmetric (Sec. 2.5), the adjoint equation
+# (H - E)^T lambda = W g is (H - E) mu = g with lambda = W mu, and for a parameter p
+#     dJ/dp = - sum_k w_k mu_k ((d(H - E)/dp) u)_k .
+# For E: d(H-E)/dE = -I.  For the charge Z in V1 + V2 = -Z/x - Z/y:
+# d(H-E)/dZ = diag(-1/x - 1/y).  For a per-node perturbation dV_k of V: e_k e_k^T.
+
+def amplitude(lev: Level, g: np.ndarray, u: np.ndarray) -> complex:
+    return complex(np.sum(weights_2d(lev) * g.ravel() * u.ravel()))
+
+
+def adjoint_gradients(lev: Level, u: np.ndarray, mu: np.ndarray, dAdZ: np.ndarray):
+    """(dJ/dE, dJ/dZ, dJ/ddV) from the forward solution u and the adjoint solution mu
+    of (H - E) mu = g; dAdZ is the diagonal of d(H - E)/dZ on the interior nodes."""
+    wmu_u = weights_2d(lev).reshape(u.shape) * mu * u
+    dE = complex(np.sum(wmu_u))
+    dZ = complex(-np.sum(wmu_u * dAdZ))
+    ddV = -wmu_u
+    return dE, dZ, ddV

@@ -62,23 +62,58 @@ __host__ __device__ __forceinline__ cplx csqrt_p(cplx z) {
   }
 }
 
+// single-precision complex (complex64) counterparts, used by the mixed-precision
+// smoother, transfers and inner Krylov solve
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cscal(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) {
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
+}
+__host__ __device__ __forceinline__ float2 cfms(float2 a, float2 b, float2 acc) {
+  return make_float2(fmaf(-a.x, b.x, fmaf(a.y, b.y, acc.x)), fmaf(-a.x, b.y, fmaf(-a.y, b.x, acc.y)));
+}
+__host__ __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
+
+// Complex element type traits: C = double2 (complex128) or float2 (complex64).
+template <class C> struct CT;
+template <> struct CT<double2> {
+  typedef double R;
+  static __host__ __device__ __forceinline__ double2 make(double a, double b) { return make_double2(a, b); }
+};
+template <> struct CT<float2> {
+  typedef float R;
+  static __host__ __device__ __forceinline__ float2 make(double a, double b) {
+    return make_float2((float)a, (float)b);
+  }
+};
+__host__ __device__ __forceinline__ double2 to_c128(double2 a) { return a; }
+__host__ __device__ __forceinline__ double2 to_c128(float2 a) { return make_double2(a.x, a.y); }
+
 // ---------------------------------------------------------------- level descriptors
 
 // 5-point operator of one level, (H - E)u = D u + west_x u_W + east_x u_E + west_y u_S + east_y u_N.
 // In the box i < ux, j < uy all four neighbour coefficients equal `cu` (uniform spacing on
 // an unbent part of the contour), which the kernels use to skip the per-node coefficients.
-struct StencilView {
+template <class C>
+struct StencilViewT {
   int mx, my;              // interior nodes per axis (row pitch = mx)
   int ux, uy;              // uniform box
   int rbox;                // 1: cu and D are real inside the box (unrotated level, real potential)
-  cplx cu;                 // uniform neighbour coefficient in the box
-  const cplx* west_x;      // [mx]
-  const cplx* east_x;      // [mx]
-  const cplx* west_y;      // [my]
-  const cplx* east_y;      // [my]
-  const cplx* D;           // [my*mx] full diagonal of H - E
-  const cplx* Dinv;        // [my*mx] omega / D
+  C cu;                    // uniform neighbour coefficient in the box
+  const C* west_x;         // [mx]
+  const C* east_x;         // [mx]
+  const C* west_y;         // [my]
+  const C* east_y;         // [my]
+  const C* D;              // [my*mx] full diagonal of H - E
+  const C* Dinv;           // [my*mx] omega / D
 };
+typedef StencilViewT<cplx> StencilView;
+typedef StencilViewT<float2> StencilView32;
 
 // Error bits written by kernels into the handle's device status word.
 enum {
@@ -90,45 +125,64 @@ enum {
 // ---------------------------------------------------------------- launchers (defined in the .cu files)
 // All return cudaGetLastError() of their launch.
 
-// kernels_mg.cu
-cudaError_t launch_jacobi(const StencilView& s, const cplx* u_in, cplx* u_out, const cplx* f, cudaStream_t st);
-cudaError_t launch_jacobi_zero(const StencilView& s, cplx* u_out, const cplx* f, cudaStream_t st);
-cudaError_t launch_residual(const StencilView& s, const cplx* u, const cplx* f, cplx* r,
-                            double* norm_part, cudaStream_t st);
-int residual_norm_blocks(const StencilView& s);
-cudaError_t launch_restrict(int mx, int my, const cplx* r, cplx* rc, cudaStream_t st);
-cudaError_t launch_prolong_add(int mx, int my, const cplx* ec, cplx* u, cudaStream_t st);
-cudaError_t launch_coarse_solve(int nc, const cplx* Ainv, const cplx* f, cplx* u, cudaStream_t st);
+// kernels_mg.cu (templates instantiated for C = double2 and C = float2)
+template <class C>
+cudaError_t launch_jacobi(const StencilViewT<C>& s, const C* u_in, C* u_out, const C* f, cudaStream_t st);
+template <class C>
+cudaError_t launch_jacobi_zero(const StencilViewT<C>& s, C* u_out, const C* f, cudaStream_t st);
+template <class C>
+cudaError_t launch_residual(const StencilViewT<C>& s, const C* u, const C* f, C* r, double* norm_part,
+                            cudaStream_t st);
+template <class C>
+int residual_norm_blocks(const StencilViewT<C>& s);
+template <class C>
+cudaError_t launch_restrict(int mx, int my, const C* r, C* rc, cudaStream_t st);
+template <class C>
+cudaError_t launch_prolong_add(int mx, int my, const C* ec, C* u, cudaStream_t st);
+template <class C>
+cudaError_t launch_coarse_solve(int nc, const cplx* Ainv, const C* f, C* u, cudaStream_t st);
+template <class C>
+cudaError_t launch_apply(const StencilViewT<C>& s, const C* x, C* y, cudaStream_t st, double* norm_part = nullptr);
+template <class C>
+cudaError_t launch_norm2(const C* v, long long n, double* part, int nblocks, cudaStream_t st);
 cudaError_t launch_sum_partials(const double* part, int n, double* out, cudaStream_t st,
                                 const int* gate = nullptr);
-cudaError_t launch_norm2(const cplx* v, long long n, double* part, int nblocks, cudaStream_t st);
 int norm2_blocks(long long n);
-cudaError_t launch_apply(const StencilView& s, const cplx* x, cplx* y, cudaStream_t st,
-                         double* norm_part = nullptr);
+cudaError_t launch_demote(long long n, const cplx* x, const double* norm2, float2* y, cudaStream_t st);
+cudaError_t launch_promote_add(long long n, const float2* e, const double* norm2, cplx* u, cudaStream_t st);
+cudaError_t launch_round_copy(long long n, const cplx* a, float2* b, cudaStream_t st);
+cudaError_t launch_promote(long long n, const float2* x, cplx* y, cudaStream_t st);
 
 // kernels_krylov.cu
 int krylov_blocks(long long n);
-cudaError_t launch_multidot(long long n, int k, const cplx* V, long long ld, const cplx* w, cplx* partial,
+template <class C>
+cudaError_t launch_multidot(long long n, int k, const C* V, long long ld, const C* w, cplx* partial,
                             int nblk, const int* gate, cudaStream_t st);
 cudaError_t launch_reduce_dots(int nblk, int k, const cplx* partial, cplx* out, cplx* acc_into, cudaStream_t st);
-cudaError_t launch_multiaxpy(long long n, int k, const cplx* V, long long ld, const cplx* coef, double sgn,
-                             cplx* w, double* norm_part, int nblk, const int* gate, cudaStream_t st);
+template <class C>
+cudaError_t launch_multiaxpy(long long n, int k, const C* V, long long ld, const cplx* coef, double sgn,
+                             C* w, double* norm_part, int nblk, const int* gate, cudaStream_t st);
 cudaError_t launch_dgks(const double* before, const double* after, int* gate, cudaStream_t st);
-cudaError_t launch_scale_by_norm(long long n, const cplx* w, cplx* out, const double* norm2, cplx* store,
+template <class C>
+cudaError_t launch_scale_by_norm(long long n, const C* w, C* out, const double* norm2, cplx* store,
                                  int nblk, cudaStream_t st);
 cudaError_t launch_givens(int j, int m, cplx* H, cplx* cs, cplx* sn, cplx* g, double* est, cudaStream_t st);
 cudaError_t launch_hess_solve(int k, int m, const cplx* H, const cplx* g, cplx* y, cudaStream_t st);
 cudaError_t launch_zero_c(int n, cplx* a, cudaStream_t st);
 
 // kernels_cccs.cu
-struct CCView {
+// Bound-state data of the CCCS for grid element type C: the states and weighted states
+// and the per-tile projection partials are of type C; reduced projections, channel
+// right-hand sides and channel solutions are always FP64 (the channel solves stay FP64).
+template <class C>
+struct CCViewT {
   int mx, my, nb;
-  const cplx* wphi;        // [nb][mx]  w_x(i) phi_m(i)
-  const cplx* wvphi;       // [nb][my]  w_y(j) vphi_l(j)
-  const cplx* phi;         // [nb][mx]
-  const cplx* vphi;        // [nb][my]
-  cplx* Px_part;           // [ntx][nb][my]
-  cplx* Py_part;           // [nty][nb][mx]
+  const C* wphi;           // [nb][mx]  w_x(i) phi_m(i)
+  const C* wvphi;          // [nb][my]  w_y(j) vphi_l(j)
+  const C* phi;            // [nb][mx]
+  const C* vphi;           // [nb][my]
+  C* Px_part;              // [ntx][nb][my]
+  C* Py_part;              // [nty][nb][mx]
   cplx* Px;                // [nb][my]
   cplx* Py;                // [nb][mx]
   cplx* c;                 // [nb][nb]  c[a][b] = int int phi_a vphi_b r
@@ -136,7 +190,12 @@ struct CCView {
   cplx* rB;                // [nb][mx]
   cplx* eA;                // [nb][my]
   cplx* eB;                // [nb][mx]
+  const cplx* phi64;       // [nb][mx] FP64 states for the channel right-hand sides
+  const cplx* vphi64;      // [nb][my]
+  const cplx* wvphi64;     // [nb][my]
 };
+typedef CCViewT<cplx> CCView;
+typedef CCViewT<float2> CCView32;
 
 // Cyclic-reduction factors of one coupled-channel system (Eqs. (28)-(29)),
 // a_k x_{k-1} + B_k x_k + c_k x_{k+1} = r_k with n_b x n_b blocks.  Rows are numbered
@@ -165,11 +224,14 @@ __host__ __device__ inline int cr_fwd_offset(int q, int l) {
 }
 int cc_tiles_x(int mx);
 int cc_tiles_y(int my);
-cudaError_t launch_residual_project(const StencilView& s, const CCView& c, const cplx* u, const cplx* f,
+template <class C>
+cudaError_t launch_residual_project(const StencilViewT<C>& s, const CCViewT<C>& c, const C* u, const C* f,
                                     cudaStream_t st);
-cudaError_t launch_cc_rhs(const CCView& c, cudaStream_t st);
+template <class C>
+cudaError_t launch_cc_rhs(const CCViewT<C>& c, cudaStream_t st);
 cudaError_t launch_channel_solve(const CRSystem& A, const CRSystem& B, cudaStream_t st);
-cudaError_t launch_cccs_correct(const CCView& c, cplx* u, cudaStream_t st);
+template <class C>
+cudaError_t launch_cccs_correct(const CCViewT<C>& c, C* u, cudaStream_t st);
 
 // kernels_setup.cu
 struct AxisSetup {
@@ -195,3 +257,10 @@ cudaError_t launch_channel_potentials(int mx, int my, int nb, const cplx* wphi, 
 cudaError_t launch_channel_factor(const CRSystem& S, const cplx* diag, const cplx* v, double E, const cplx* lam,
                                   const cplx* Vc, const cplx* a, const cplx* c, cplx* scratch, int* status,
                                   cudaStream_t st);
+
+// kernels_adjoint.cu
+int wdot_blocks(long long n);
+cudaError_t launch_weighted_dot(int mx, int my, const cplx* wx, const cplx* wy, const cplx* a, const cplx* b,
+                                const cplx* d, cplx scale, cplx* part, cplx* out, cudaStream_t st);
+cudaError_t launch_weighted_product(int mx, int my, const cplx* wx, const cplx* wy, const cplx* a, const cplx* b,
+                                    cplx scale, cplx* out, cudaStream_t st);

@@ -9,8 +9,8 @@
 //   u += sum_m phi_m(x) e^A_m(y) + sum_l e^B_l(x) vphi_l(y)       (Eq. (30))
 //
 // The projections are fused into the residual pass and reduced deterministically:
-// warp shuffles along x and a shared-memory pass along y give per-tile partials,
-// which a second kernel sums in a fixed order.
+// per 32 x 32 tile, sums along x and along y through a shared-memory tile give
+// per-tile partials, which a second kernel sums in a fixed order.
 #include "common.cuh"
 
 namespace {
@@ -20,23 +20,27 @@ constexpr int WY = 8;         // warps per block
 constexpr int SY = 4;         // rows per warp
 constexpr int TY = WY * SY;   // tile height
 
-__device__ __forceinline__ cplx ldz(const cplx* __restrict__ a, int p, bool ok) {
-  return ok ? __ldg(a + p) : cmk(0.0, 0.0);
+template <class C>
+__device__ __forceinline__ C ldz(const C* __restrict__ a, int p, bool ok) {
+  return ok ? __ldg(a + p) : CT<C>::make(0.0, 0.0);
 }
 
-__device__ __forceinline__ cplx residual_at(const StencilView& s, const cplx* __restrict__ u,
-                                            const cplx* __restrict__ f, int i, int j) {
+template <class C>
+__device__ __forceinline__ C residual_at(const StencilViewT<C>& s, const C* __restrict__ u, const C* __restrict__ f,
+                                         int i, int j) {
+  typedef typename CT<C>::R R;
   const int p = j * s.mx + i;
-  cplx uc = __ldg(u + p);
-  cplx uw = ldz(u, p - 1, i > 0);
-  cplx ue = ldz(u, p + 1, i + 1 < s.mx);
-  cplx us = ldz(u, p - s.mx, j > 0);
-  cplx un = ldz(u, p + s.mx, j + 1 < s.my);
-  cplx a;
+  C uc = __ldg(u + p);
+  C uw = ldz(u, p - 1, i > 0);
+  C ue = ldz(u, p + 1, i + 1 < s.mx);
+  C us = ldz(u, p - s.mx, j > 0);
+  C un = ldz(u, p + s.mx, j + 1 < s.my);
+  C a;
   if (s.rbox && i < s.ux && j < s.uy) {
-    cplx sum = cadd(cadd(uw, ue), cadd(us, un));
-    const double d = __ldg(reinterpret_cast<const double*>(s.D) + 2 * p);
-    a = cmk(fma(s.cu.x, sum.x, d * uc.x), fma(s.cu.x, sum.y, d * uc.y));
+    C sum = cadd(cadd(uw, ue), cadd(us, un));
+    const R d = __ldg(reinterpret_cast<const R*>(s.D) + 2 * p);
+    a.x = fma(s.cu.x, sum.x, d * uc.x);
+    a.y = fma(s.cu.x, sum.y, d * uc.y);
     return csub(__ldg(f + p), a);
   }
   a = cmul(__ldg(s.D + p), uc);
@@ -51,75 +55,64 @@ __device__ __forceinline__ cplx residual_at(const StencilView& s, const cplx* __
   return csub(__ldg(f + p), a);
 }
 
-template <int NB>
-__global__ void __launch_bounds__(TX * WY) k_residual_project(StencilView s, CCView c, const cplx* __restrict__ u,
-                                                              const cplx* __restrict__ f) {
-  __shared__ cplx shy[WY][NB][TX];
+// One 32 x 32 tile per block: each thread computes the residual at four nodes into a
+// padded shared tile; then, with the tile transposed through shared memory, one thread
+// per (row, state) sums P^x over the tile's 32 columns and one thread per (column,
+// state) sums P^y over its 32 rows.  Each residual costs 4 n_b FP64 FMAs of projection
+// work and no shuffle reductions.
+template <int NB, class C>
+__global__ void __launch_bounds__(TX * WY) k_residual_project(StencilViewT<C> s, CCViewT<C> c, const C* __restrict__ u,
+                                                              const C* __restrict__ f) {
+  __shared__ C R[TY][TX + 1];
   const int lane = threadIdx.x;
   const int wy = threadIdx.y;
-  const int i = blockIdx.x * TX + lane;
-  const bool col_ok = i < s.mx;
-  cplx wphi[NB];
-#pragma unroll
-  for (int m = 0; m < NB; ++m) wphi[m] = col_ok ? __ldg(c.wphi + m * s.mx + i) : cmk(0.0, 0.0);
-  cplx py[NB];
-#pragma unroll
-  for (int l = 0; l < NB; ++l) py[l] = cmk(0.0, 0.0);
-
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int i = i0 + lane;
   for (int q = 0; q < SY; ++q) {
-    const int j = blockIdx.y * TY + q * WY + wy;
-    const bool ok = col_ok && j < s.my;
-    cplx r = ok ? residual_at(s, u, f, i, j) : cmk(0.0, 0.0);
-    if (j < s.my) {
-#pragma unroll
-      for (int l = 0; l < NB; ++l) py[l] = cfma(__ldg(c.wvphi + l * s.my + j), r, py[l]);
-    }
-    // P^x partial of this row over the tile's 32 columns
-    cplx px[NB];
-#pragma unroll
-    for (int m = 0; m < NB; ++m) px[m] = cmul(wphi[m], r);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-      for (int m = 0; m < NB; ++m) {
-        px[m].x += __shfl_down_sync(0xffffffffu, px[m].x, o);
-        px[m].y += __shfl_down_sync(0xffffffffu, px[m].y, o);
-      }
-    }
-    if (lane == 0 && j < s.my) {
-#pragma unroll
-      for (int m = 0; m < NB; ++m) c.Px_part[((size_t)blockIdx.x * NB + m) * s.my + j] = px[m];
-    }
+    const int row = q * WY + wy;
+    const int j = j0 + row;
+    R[row][lane] = (i < s.mx && j < s.my) ? residual_at(s, u, f, i, j) : CT<C>::make(0.0, 0.0);
   }
-#pragma unroll
-  for (int l = 0; l < NB; ++l) shy[wy][l][lane] = py[l];
   __syncthreads();
-  if (wy == 0 && col_ok) {
-#pragma unroll
-    for (int l = 0; l < NB; ++l) {
-      cplx acc = shy[0][l][lane];
-#pragma unroll
-      for (int w = 1; w < WY; ++w) acc = cadd(acc, shy[w][l][lane]);
-      c.Py_part[((size_t)blockIdx.y * NB + l) * s.mx + i] = acc;
+  const int t = wy * TX + lane;
+  for (int w = t; w < 2 * TX * NB; w += TX * WY) {
+    if (w < TX * NB) {
+      // P^x partial: row `row`, state m, over the tile's columns
+      const int m = w / TX, row = w % TX;
+      const int ncol = min(TX, s.mx - i0);
+      const C* wp = c.wphi + (size_t)m * s.mx + i0;
+      C acc = CT<C>::make(0.0, 0.0);
+      for (int cc = 0; cc < ncol; ++cc) acc = cfma(__ldg(wp + cc), R[row][cc], acc);
+      if (j0 + row < s.my) c.Px_part[((size_t)blockIdx.x * NB + m) * s.my + j0 + row] = acc;
+    } else {
+      // P^y partial: column `col`, state l, over the tile's rows
+      const int w2 = w - TX * NB;
+      const int l = w2 / TX, col = w2 % TX;
+      const int nrow = min(TY, s.my - j0);
+      const C* wv = c.wvphi + (size_t)l * s.my + j0;
+      C acc = CT<C>::make(0.0, 0.0);
+      for (int rr = 0; rr < nrow; ++rr) acc = cfma(__ldg(wv + rr), R[rr][col], acc);
+      if (i0 + col < s.mx) c.Py_part[((size_t)blockIdx.y * NB + l) * s.mx + i0 + col] = acc;
     }
   }
 }
 
-// Sum the per-tile partials in tile order.
+// Sum the per-tile partials in tile order (in FP64 for either partial type).
+template <class C>
 __global__ void __launch_bounds__(256) k_reduce_partials(int nb, int mx, int my, int ntx, int nty,
-                                                         const cplx* __restrict__ Px_part,
-                                                         const cplx* __restrict__ Py_part,
+                                                         const C* __restrict__ Px_part,
+                                                         const C* __restrict__ Py_part,
                                                          cplx* __restrict__ Px, cplx* __restrict__ Py) {
   const int t = blockIdx.x * 256 + threadIdx.x;
   const int nx_tot = nb * my, ny_tot = nb * mx;
   if (t < nx_tot) {
     cplx acc = cmk(0.0, 0.0);
-    for (int k = 0; k < ntx; ++k) acc = cadd(acc, Px_part[(size_t)k * nx_tot + t]);
+    for (int k = 0; k < ntx; ++k) acc = cadd(acc, to_c128(Px_part[(size_t)k * nx_tot + t]));
     Px[t] = acc;
   } else if (t < nx_tot + ny_tot) {
     const int q = t - nx_tot;
     cplx acc = cmk(0.0, 0.0);
-    for (int k = 0; k < nty; ++k) acc = cadd(acc, Py_part[(size_t)k * ny_tot + q]);
+    for (int k = 0; k < nty; ++k) acc = cadd(acc, to_c128(Py_part[(size_t)k * ny_tot + q]));
     Py[q] = acc;
   }
 }
@@ -229,33 +222,39 @@ __global__ void __launch_bounds__(512) k_channel_solve(CRSystem SA, CRSystem SB)
   }
 }
 
-template <int NB>
-__global__ void __launch_bounds__(256) k_cccs_correct(int mx, int my, const cplx* __restrict__ phi,
-                                                      const cplx* __restrict__ vphi, const cplx* __restrict__ eA,
-                                                      const cplx* __restrict__ eB, cplx* __restrict__ u) {
+template <int NB, class C>
+__global__ void __launch_bounds__(256) k_cccs_correct(int mx, int my, const C* __restrict__ phi,
+                                                      const C* __restrict__ vphi, const cplx* __restrict__ eA,
+                                                      const cplx* __restrict__ eB, C* __restrict__ u) {
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y * 8 + threadIdx.y;
   if (i >= mx || j >= my) return;
   const int p = j * mx + i;
-  cplx v = u[p];
+  C v = u[p];
 #pragma unroll
-  for (int m = 0; m < NB; ++m) v = cfma(__ldg(phi + m * mx + i), __ldg(eA + m * my + j), v);
+  for (int m = 0; m < NB; ++m) {
+    const cplx e = __ldg(eA + m * my + j);
+    v = cfma(__ldg(phi + m * mx + i), CT<C>::make(e.x, e.y), v);
+  }
 #pragma unroll
-  for (int l = 0; l < NB; ++l) v = cfma(__ldg(eB + l * mx + i), __ldg(vphi + l * my + j), v);
+  for (int l = 0; l < NB; ++l) {
+    const cplx e = __ldg(eB + l * mx + i);
+    v = cfma(CT<C>::make(e.x, e.y), __ldg(vphi + l * my + j), v);
+  }
   u[p] = v;
 }
 
-template <int NB>
-cudaError_t rp_launch(const StencilView& s, const CCView& c, const cplx* u, const cplx* f, cudaStream_t st) {
+template <int NB, class C>
+cudaError_t rp_launch(const StencilViewT<C>& s, const CCViewT<C>& c, const C* u, const C* f, cudaStream_t st) {
   dim3 g(cc_tiles_x(s.mx), cc_tiles_y(s.my));
-  k_residual_project<NB><<<g, dim3(TX, WY), 0, st>>>(s, c, u, f);
+  k_residual_project<NB, C><<<g, dim3(TX, WY), 0, st>>>(s, c, u, f);
   return cudaGetLastError();
 }
 
-template <int NB>
-cudaError_t corr_launch(const CCView& c, cplx* u, cudaStream_t st) {
+template <int NB, class C>
+cudaError_t corr_launch(const CCViewT<C>& c, C* u, cudaStream_t st) {
   dim3 g((c.mx + 31) / 32, (c.my + 7) / 8);
-  k_cccs_correct<NB><<<g, dim3(32, 8), 0, st>>>(c.mx, c.my, c.phi, c.vphi, c.eA, c.eB, u);
+  k_cccs_correct<NB, C><<<g, dim3(32, 8), 0, st>>>(c.mx, c.my, c.phi, c.vphi, c.eA, c.eB, u);
   return cudaGetLastError();
 }
 
@@ -264,31 +263,33 @@ cudaError_t corr_launch(const CCView& c, cplx* u, cudaStream_t st) {
 int cc_tiles_x(int mx) { return (mx + TX - 1) / TX; }
 int cc_tiles_y(int my) { return (my + TY - 1) / TY; }
 
-cudaError_t launch_residual_project(const StencilView& s, const CCView& c, const cplx* u, const cplx* f,
+template <class C>
+cudaError_t launch_residual_project(const StencilViewT<C>& s, const CCViewT<C>& c, const C* u, const C* f,
                                     cudaStream_t st) {
   switch (c.nb) {
-    case 1: return rp_launch<1>(s, c, u, f, st);
-    case 2: return rp_launch<2>(s, c, u, f, st);
-    case 3: return rp_launch<3>(s, c, u, f, st);
-    case 4: return rp_launch<4>(s, c, u, f, st);
-    case 5: return rp_launch<5>(s, c, u, f, st);
-    case 6: return rp_launch<6>(s, c, u, f, st);
-    case 7: return rp_launch<7>(s, c, u, f, st);
-    case 8: return rp_launch<8>(s, c, u, f, st);
+    case 1: return rp_launch<1, C>(s, c, u, f, st);
+    case 2: return rp_launch<2, C>(s, c, u, f, st);
+    case 3: return rp_launch<3, C>(s, c, u, f, st);
+    case 4: return rp_launch<4, C>(s, c, u, f, st);
+    case 5: return rp_launch<5, C>(s, c, u, f, st);
+    case 6: return rp_launch<6, C>(s, c, u, f, st);
+    case 7: return rp_launch<7, C>(s, c, u, f, st);
+    case 8: return rp_launch<8, C>(s, c, u, f, st);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_cc_rhs(const CCView& c, cudaStream_t st) {
+template <class C>
+cudaError_t launch_cc_rhs(const CCViewT<C>& c, cudaStream_t st) {
   int tot = c.nb * (c.mx + c.my);
-  k_reduce_partials<<<(tot + 255) / 256, 256, 0, st>>>(c.nb, c.mx, c.my, cc_tiles_x(c.mx), cc_tiles_y(c.my),
-                                                        c.Px_part, c.Py_part, c.Px, c.Py);
+  k_reduce_partials<C><<<(tot + 255) / 256, 256, 0, st>>>(c.nb, c.mx, c.my, cc_tiles_x(c.mx), cc_tiles_y(c.my),
+                                                           c.Px_part, c.Py_part, c.Px, c.Py);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_cc_coef<<<c.nb * c.nb, 256, 0, st>>>(c.nb, c.my, c.wvphi, c.Px, c.c);
+  k_cc_coef<<<c.nb * c.nb, 256, 0, st>>>(c.nb, c.my, c.wvphi64, c.Px, c.c);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_cc_split<<<(tot + 255) / 256, 256, 0, st>>>(c.nb, c.mx, c.my, c.c, c.phi, c.vphi, c.Px, c.Py, c.rA, c.rB);
+  k_cc_split<<<(tot + 255) / 256, 256, 0, st>>>(c.nb, c.mx, c.my, c.c, c.phi64, c.vphi64, c.Px, c.Py, c.rA, c.rB);
   return cudaGetLastError();
 }
 
@@ -303,16 +304,26 @@ cudaError_t launch_channel_solve(const CRSystem& A, const CRSystem& B, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_cccs_correct(const CCView& c, cplx* u, cudaStream_t st) {
+template <class C>
+cudaError_t launch_cccs_correct(const CCViewT<C>& c, C* u, cudaStream_t st) {
   switch (c.nb) {
-    case 1: return corr_launch<1>(c, u, st);
-    case 2: return corr_launch<2>(c, u, st);
-    case 3: return corr_launch<3>(c, u, st);
-    case 4: return corr_launch<4>(c, u, st);
-    case 5: return corr_launch<5>(c, u, st);
-    case 6: return corr_launch<6>(c, u, st);
-    case 7: return corr_launch<7>(c, u, st);
-    case 8: return corr_launch<8>(c, u, st);
+    case 1: return corr_launch<1, C>(c, u, st);
+    case 2: return corr_launch<2, C>(c, u, st);
+    case 3: return corr_launch<3, C>(c, u, st);
+    case 4: return corr_launch<4, C>(c, u, st);
+    case 5: return corr_launch<5, C>(c, u, st);
+    case 6: return corr_launch<6, C>(c, u, st);
+    case 7: return corr_launch<7, C>(c, u, st);
+    case 8: return corr_launch<8, C>(c, u, st);
   }
   return cudaErrorInvalidValue;
 }
+
+#define MGC_INSTANTIATE(C)                                                                                  \
+  template cudaError_t launch_residual_project<C>(const StencilViewT<C>&, const CCViewT<C>&, const C*,     \
+                                                  const C*, cudaStream_t);                                \
+  template cudaError_t launch_cc_rhs<C>(const CCViewT<C>&, cudaStream_t);                                 \
+  template cudaError_t launch_cccs_correct<C>(const CCViewT<C>&, C*, cudaStream_t);
+MGC_INSTANTIATE(double2)
+MGC_INSTANTIATE(float2)
+#undef MGC_INSTANTIATE

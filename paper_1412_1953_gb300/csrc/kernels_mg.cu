@@ -3,30 +3,33 @@
 // (Sec. 3.2 of Cools & Vanroose; the operator is Eq. (11) on the ECS grid of Sec. 2.5).
 //
 // All arrays are interior-only, row-major [j][i] with pitch mx; values outside the
-// interior are the homogeneous Dirichlet boundary (zero).  The complex128 path is
-// bound by the FP64 pipe on this GPU, so every kernel computes each output exactly
-// once (no overlapped halo recomputation) and the uniform-spacing box uses a single
-// neighbour coefficient.
+// interior are the homogeneous Dirichlet boundary (zero).  Every kernel is a template
+// over the element type C: double2 (complex128, the plain path, bound by the FP64
+// pipe on this GPU) or float2 (complex64, the mixed-precision smoother and transfers,
+// bound by HBM).  Each output is computed exactly once (no overlapped halo
+// recomputation) and the uniform-spacing box uses a single neighbour coefficient.
 #include "common.cuh"
 
 namespace {
 
 constexpr int BX = 32, BY = 8;
 
-__device__ __forceinline__ cplx ldz(const cplx* __restrict__ a, int p, bool ok) {
-  return ok ? __ldg(a + p) : cmk(0.0, 0.0);
+template <class C>
+__device__ __forceinline__ C ldz(const C* __restrict__ a, int p, bool ok) {
+  return ok ? __ldg(a + p) : CT<C>::make(0.0, 0.0);
 }
 
 // (H - E) u at interior node (i, j), given the centre value uc.
-__device__ __forceinline__ cplx apply_op(const StencilView& s, const cplx* __restrict__ u, int i, int j, cplx uc) {
+template <class C>
+__device__ __forceinline__ C apply_op(const StencilViewT<C>& s, const C* __restrict__ u, int i, int j, C uc) {
   const int p = j * s.mx + i;
-  cplx uw = ldz(u, p - 1, i > 0);
-  cplx ue = ldz(u, p + 1, i + 1 < s.mx);
-  cplx us = ldz(u, p - s.mx, j > 0);
-  cplx un = ldz(u, p + s.mx, j + 1 < s.my);
-  cplx a = cmul(__ldg(s.D + p), uc);
+  C uw = ldz(u, p - 1, i > 0);
+  C ue = ldz(u, p + 1, i + 1 < s.mx);
+  C us = ldz(u, p - s.mx, j > 0);
+  C un = ldz(u, p + s.mx, j + 1 < s.my);
+  C a = cmul(__ldg(s.D + p), uc);
   if (i < s.ux && j < s.uy) {
-    cplx sum = cadd(cadd(uw, ue), cadd(us, un));
+    C sum = cadd(cadd(uw, ue), cadd(us, un));
     a = cfma(s.cu, sum, a);
   } else {
     a = cfma(__ldg(s.west_x + i), uw, a);
@@ -37,41 +40,55 @@ __device__ __forceinline__ cplx apply_op(const StencilView& s, const cplx* __res
   return a;
 }
 
-// Real part of a complex array element (only 8 bytes are loaded).
-__device__ __forceinline__ double ldre(const cplx* __restrict__ a, int p) {
-  return __ldg(reinterpret_cast<const double*>(a) + 2 * p);
+// Real part of a complex array element (only the real word is loaded).
+template <class C>
+__device__ __forceinline__ typename CT<C>::R ldre(const C* __restrict__ a, int p) {
+  return __ldg(reinterpret_cast<const typename CT<C>::R*>(a) + 2 * p);
 }
 
 // (H - E) u in the real box: real coefficient cu.x and real diagonal.
-__device__ __forceinline__ cplx apply_op_rbox(const StencilView& s, const cplx* __restrict__ u, int i, int j,
-                                              cplx uc) {
+template <class C>
+__device__ __forceinline__ C apply_op_rbox(const StencilViewT<C>& s, const C* __restrict__ u, int i, int j, C uc) {
   const int p = j * s.mx + i;
-  cplx sum = cadd(cadd(ldz(u, p - 1, i > 0), ldz(u, p + 1, i + 1 < s.mx)),
-                  cadd(ldz(u, p - s.mx, j > 0), ldz(u, p + s.mx, j + 1 < s.my)));
-  const double d = ldre(s.D, p);
-  return cmk(fma(s.cu.x, sum.x, d * uc.x), fma(s.cu.x, sum.y, d * uc.y));
+  C sum = cadd(cadd(ldz(u, p - 1, i > 0), ldz(u, p + 1, i + 1 < s.mx)),
+               cadd(ldz(u, p - s.mx, j > 0), ldz(u, p + s.mx, j + 1 < s.my)));
+  const typename CT<C>::R d = ldre(s.D, p);
+  C a;
+  a.x = fma(s.cu.x, sum.x, d * uc.x);
+  a.y = fma(s.cu.x, sum.y, d * uc.y);
+  return a;
 }
 
-__global__ void __launch_bounds__(BX * BY) k_jacobi(StencilView s, const cplx* __restrict__ u_in,
-                                                    cplx* __restrict__ u_out, const cplx* __restrict__ f) {
+template <class C>
+__device__ __forceinline__ C apply_any(const StencilViewT<C>& s, const C* __restrict__ u, int i, int j, C uc) {
+  return (s.rbox && i < s.ux && j < s.uy) ? apply_op_rbox(s, u, i, j, uc) : apply_op(s, u, i, j, uc);
+}
+
+template <class C>
+__global__ void __launch_bounds__(BX * BY) k_jacobi(StencilViewT<C> s, const C* __restrict__ u_in,
+                                                    C* __restrict__ u_out, const C* __restrict__ f) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   if (i >= s.mx || j >= s.my) return;
   const int p = j * s.mx + i;
-  cplx uc = __ldg(u_in + p);
+  C uc = __ldg(u_in + p);
   if (s.rbox && i < s.ux && j < s.uy) {
-    cplx r = csub(__ldg(f + p), apply_op_rbox(s, u_in, i, j, uc));
-    const double di = ldre(s.Dinv, p);
-    u_out[p] = cmk(fma(di, r.x, uc.x), fma(di, r.y, uc.y));
+    C r = csub(__ldg(f + p), apply_op_rbox(s, u_in, i, j, uc));
+    const typename CT<C>::R di = ldre(s.Dinv, p);
+    C o;
+    o.x = fma(di, r.x, uc.x);
+    o.y = fma(di, r.y, uc.y);
+    u_out[p] = o;
   } else {
-    cplx r = csub(__ldg(f + p), apply_op(s, u_in, i, j, uc));
+    C r = csub(__ldg(f + p), apply_op(s, u_in, i, j, uc));
     u_out[p] = cfma(__ldg(s.Dinv + p), r, uc);
   }
 }
 
 // First sweep from a zero initial guess: u = omega D^{-1} f.
-__global__ void __launch_bounds__(256) k_jacobi_zero(long long n, const cplx* __restrict__ Dinv,
-                                                    cplx* __restrict__ u_out, const cplx* __restrict__ f) {
+template <class C>
+__global__ void __launch_bounds__(256) k_jacobi_zero(long long n, const C* __restrict__ Dinv, C* __restrict__ u_out,
+                                                    const C* __restrict__ f) {
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p < n) u_out[p] = cmul(__ldg(Dinv + p), __ldg(f + p));
 }
@@ -92,8 +109,9 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return tot;
 }
 
-__global__ void __launch_bounds__(BX * BY) k_residual(StencilView s, const cplx* __restrict__ u,
-                                                      const cplx* __restrict__ f, cplx* __restrict__ r,
+template <class C>
+__global__ void __launch_bounds__(BX * BY) k_residual(StencilViewT<C> s, const C* __restrict__ u,
+                                                      const C* __restrict__ f, C* __restrict__ r,
                                                       double* __restrict__ norm_part) {
   __shared__ double sh[BX * BY / 32];
   const int i = blockIdx.x * BX + threadIdx.x;
@@ -101,11 +119,9 @@ __global__ void __launch_bounds__(BX * BY) k_residual(StencilView s, const cplx*
   double n2 = 0.0;
   if (i < s.mx && j < s.my) {
     const int p = j * s.mx + i;
-    const cplx uc = __ldg(u + p);
-    cplx rv = csub(__ldg(f + p), (s.rbox && i < s.ux && j < s.uy) ? apply_op_rbox(s, u, i, j, uc)
-                                                                    : apply_op(s, u, i, j, uc));
+    C rv = csub(__ldg(f + p), apply_any(s, u, i, j, __ldg(u + p)));
     if (r) r[p] = rv;
-    n2 = cabs2(rv);
+    n2 = (double)cabs2(rv);
   }
   if (norm_part) {
     double tot = block_sum<BX * BY>(n2, sh);
@@ -115,64 +131,73 @@ __global__ void __launch_bounds__(BX * BY) k_residual(StencilView s, const cplx*
 
 // Full weighting 1/16 [1 2 1; 2 4 2; 1 2 1] onto the coincident nodes: coarse interior
 // (I, J) sits on fine interior (2I+1, 2J+1); all nine taps are interior nodes.
-__global__ void __launch_bounds__(256) k_restrict(int mx, int mcx, int mcy, const cplx* __restrict__ r,
-                                                  cplx* __restrict__ rc) {
+template <class C>
+__global__ void __launch_bounds__(256) k_restrict(int mx, int mcx, int mcy, const C* __restrict__ r,
+                                                  C* __restrict__ rc) {
+  typedef typename CT<C>::R R;
   const int I = blockIdx.x * 32 + threadIdx.x;
   const int J = blockIdx.y * 8 + threadIdx.y;
   if (I >= mcx || J >= mcy) return;
   const int c = (2 * J + 1) * mx + (2 * I + 1);
-  cplx corners = cadd(cadd(__ldg(r + c - mx - 1), __ldg(r + c - mx + 1)),
-                      cadd(__ldg(r + c + mx - 1), __ldg(r + c + mx + 1)));
-  cplx edges = cadd(cadd(__ldg(r + c - 1), __ldg(r + c + 1)), cadd(__ldg(r + c - mx), __ldg(r + c + mx)));
-  cplx centre = __ldg(r + c);
-  cplx acc = cmk(fma(2.0, edges.x, fma(4.0, centre.x, corners.x)),
-                 fma(2.0, edges.y, fma(4.0, centre.y, corners.y)));
-  rc[J * mcx + I] = cscal(0.0625, acc);
+  C corners = cadd(cadd(__ldg(r + c - mx - 1), __ldg(r + c - mx + 1)),
+                   cadd(__ldg(r + c + mx - 1), __ldg(r + c + mx + 1)));
+  C edges = cadd(cadd(__ldg(r + c - 1), __ldg(r + c + 1)), cadd(__ldg(r + c - mx), __ldg(r + c + mx)));
+  C centre = __ldg(r + c);
+  C acc;
+  acc.x = fma(R(2), edges.x, fma(R(4), centre.x, corners.x));
+  acc.y = fma(R(2), edges.y, fma(R(4), centre.y, corners.y));
+  rc[J * mcx + I] = cscal(R(0.0625), acc);
 }
 
-__device__ __forceinline__ cplx coarse_at(const cplx* __restrict__ ec, int mcx, int mcy, int K, int Kp) {
+template <class C>
+__device__ __forceinline__ C coarse_at(const C* __restrict__ ec, int mcx, int mcy, int K, int Kp) {
   // coarse node (K, Kp), 0..mc+1; boundary nodes carry zero
-  return (K >= 1 && K <= mcx && Kp >= 1 && Kp <= mcy) ? __ldg(ec + (Kp - 1) * mcx + (K - 1)) : cmk(0.0, 0.0);
+  return (K >= 1 && K <= mcx && Kp >= 1 && Kp <= mcy) ? __ldg(ec + (Kp - 1) * mcx + (K - 1))
+                                                       : CT<C>::make(0.0, 0.0);
 }
 
 // u += bilinear interpolation of the coarse correction (fine node k = i+1).
-__global__ void __launch_bounds__(BX * BY) k_prolong_add(int mx, int my, int mcx, int mcy,
-                                                         const cplx* __restrict__ ec, cplx* __restrict__ u) {
+template <class C>
+__global__ void __launch_bounds__(BX * BY) k_prolong_add(int mx, int my, int mcx, int mcy, const C* __restrict__ ec,
+                                                         C* __restrict__ u) {
+  typedef typename CT<C>::R R;
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   if (i >= mx || j >= my) return;
   const int kx = i + 1, ky = j + 1;
   const int Kx = kx >> 1, Ky = ky >> 1;
-  cplx v;
+  C v;
   if (!(kx & 1) && !(ky & 1)) {
     v = coarse_at(ec, mcx, mcy, Kx, Ky);
   } else if (!(ky & 1)) {
-    v = cscal(0.5, cadd(coarse_at(ec, mcx, mcy, Kx, Ky), coarse_at(ec, mcx, mcy, Kx + 1, Ky)));
+    v = cscal(R(0.5), cadd(coarse_at(ec, mcx, mcy, Kx, Ky), coarse_at(ec, mcx, mcy, Kx + 1, Ky)));
   } else if (!(kx & 1)) {
-    v = cscal(0.5, cadd(coarse_at(ec, mcx, mcy, Kx, Ky), coarse_at(ec, mcx, mcy, Kx, Ky + 1)));
+    v = cscal(R(0.5), cadd(coarse_at(ec, mcx, mcy, Kx, Ky), coarse_at(ec, mcx, mcy, Kx, Ky + 1)));
   } else {
-    v = cscal(0.25, cadd(cadd(coarse_at(ec, mcx, mcy, Kx, Ky), coarse_at(ec, mcx, mcy, Kx + 1, Ky)),
-                         cadd(coarse_at(ec, mcx, mcy, Kx, Ky + 1), coarse_at(ec, mcx, mcy, Kx + 1, Ky + 1))));
+    v = cscal(R(0.25), cadd(cadd(coarse_at(ec, mcx, mcy, Kx, Ky), coarse_at(ec, mcx, mcy, Kx + 1, Ky)),
+                            cadd(coarse_at(ec, mcx, mcy, Kx, Ky + 1), coarse_at(ec, mcx, mcy, Kx + 1, Ky + 1))));
   }
   const int p = j * mx + i;
   u[p] = cadd(u[p], v);
 }
 
-// Coarsest level: u = A_c^{-1} f with the dense inverse built at setup; one warp per row.
-__global__ void __launch_bounds__(256) k_coarse_solve(int nc, const cplx* __restrict__ Ainv,
-                                                      const cplx* __restrict__ f, cplx* __restrict__ u) {
+// Coarsest level: u = A_c^{-1} f with the FP64 dense inverse built at setup; one warp
+// per row, accumulated in FP64 for either element type.
+template <class C>
+__global__ void __launch_bounds__(256) k_coarse_solve(int nc, const cplx* __restrict__ Ainv, const C* __restrict__ f,
+                                                      C* __restrict__ u) {
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= nc) return;
   cplx acc = cmk(0.0, 0.0);
   const cplx* a = Ainv + (size_t)row * nc;
-  for (int c = lane; c < nc; c += 32) acc = cfma(__ldg(a + c), __ldg(f + c), acc);
+  for (int c = lane; c < nc; c += 32) acc = cfma(__ldg(a + c), to_c128(__ldg(f + c)), acc);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
     acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
   }
-  if (lane == 0) u[row] = acc;
+  if (lane == 0) u[row] = CT<C>::make(acc.x, acc.y);
 }
 
 // Sum of n partials in a fixed order (one block), result to out[0]; skipped when
@@ -187,16 +212,18 @@ __global__ void __launch_bounds__(256) k_sum_partials(const double* __restrict__
   if (threadIdx.x == 0) out[0] = tot;
 }
 
-__global__ void __launch_bounds__(256) k_norm2(const cplx* __restrict__ v, long long n, double* __restrict__ part) {
+template <class C>
+__global__ void __launch_bounds__(256) k_norm2(const C* __restrict__ v, long long n, double* __restrict__ part) {
   __shared__ double sh[8];
   double acc = 0.0;
   for (long long p = blockIdx.x * 256LL + threadIdx.x; p < n; p += (long long)gridDim.x * 256)
-    acc += cabs2(__ldg(v + p));
+    acc += (double)cabs2(__ldg(v + p));
   double tot = block_sum<256>(acc, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(BX * BY) k_apply(StencilView s, const cplx* __restrict__ x, cplx* __restrict__ y,
+template <class C>
+__global__ void __launch_bounds__(BX * BY) k_apply(StencilViewT<C> s, const C* __restrict__ x, C* __restrict__ y,
                                                    double* __restrict__ norm_part) {
   __shared__ double sh[BX * BY / 32];
   const int i = blockIdx.x * BX + threadIdx.x;
@@ -204,10 +231,9 @@ __global__ void __launch_bounds__(BX * BY) k_apply(StencilView s, const cplx* __
   double n2 = 0.0;
   if (i < s.mx && j < s.my) {
     const int p = j * s.mx + i;
-    const cplx xc = __ldg(x + p);
-    cplx v = (s.rbox && i < s.ux && j < s.uy) ? apply_op_rbox(s, x, i, j, xc) : apply_op(s, x, i, j, xc);
+    C v = apply_any(s, x, i, j, __ldg(x + p));
     y[p] = v;
-    n2 = cabs2(v);
+    n2 = (double)cabs2(v);
   }
   if (norm_part) {
     double tot = block_sum<BX * BY>(n2, sh);
@@ -215,48 +241,120 @@ __global__ void __launch_bounds__(BX * BY) k_apply(StencilView s, const cplx* __
   }
 }
 
+// y32 = (x64 * scale) rounded to complex64, scale = 1/sqrt(*norm2) (1 when norm2 is null).
+__global__ void __launch_bounds__(256) k_demote(long long n, const cplx* __restrict__ x, const double* __restrict__ norm2,
+                                                float2* __restrict__ y) {
+  const double s = norm2 ? (*norm2 > 0.0 ? 1.0 / sqrt(*norm2) : 0.0) : 1.0;
+  for (long long p = blockIdx.x * 256LL + threadIdx.x; p < n; p += (long long)gridDim.x * 256) {
+    cplx v = __ldg(x + p);
+    y[p] = make_float2((float)(s * v.x), (float)(s * v.y));
+  }
+}
+
+// u64 += sqrt(*norm2) * e32 (the iterative-refinement update in FP64).
+__global__ void __launch_bounds__(256) k_promote_add(long long n, const float2* __restrict__ e,
+                                                     const double* __restrict__ norm2, cplx* __restrict__ u) {
+  const double s = sqrt(*norm2);
+  for (long long p = blockIdx.x * 256LL + threadIdx.x; p < n; p += (long long)gridDim.x * 256) {
+    float2 v = __ldg(e + p);
+    cplx a = u[p];
+    u[p] = cmk(fma(s, (double)v.x, a.x), fma(s, (double)v.y, a.y));
+  }
+}
+
+// y64 = x32 (exact widening).
+__global__ void __launch_bounds__(256) k_promote(long long n, const float2* __restrict__ x, cplx* __restrict__ y) {
+  for (long long p = blockIdx.x * 256LL + threadIdx.x; p < n; p += (long long)gridDim.x * 256)
+    y[p] = to_c128(__ldg(x + p));
+}
+
+// b32 = a64 rounded (setup: single-precision copies of coefficients and states).
+__global__ void __launch_bounds__(256) k_round_copy(long long n, const cplx* __restrict__ a, float2* __restrict__ b) {
+  for (long long p = blockIdx.x * 256LL + threadIdx.x; p < n; p += (long long)gridDim.x * 256)
+    b[p] = make_float2((float)a[p].x, (float)a[p].y);
+}
+
 inline dim3 grid2(int mx, int my) { return dim3((mx + BX - 1) / BX, (my + BY - 1) / BY); }
+
+inline unsigned stride_blocks(long long n) {
+  long long b = (n + 255) / 256;
+  return (unsigned)(b < 1216 ? (b < 1 ? 1 : b) : 1216);
+}
 
 }  // namespace
 
-cudaError_t launch_jacobi(const StencilView& s, const cplx* u_in, cplx* u_out, const cplx* f, cudaStream_t st) {
-  k_jacobi<<<grid2(s.mx, s.my), dim3(BX, BY), 0, st>>>(s, u_in, u_out, f);
+template <class C>
+cudaError_t launch_jacobi(const StencilViewT<C>& s, const C* u_in, C* u_out, const C* f, cudaStream_t st) {
+  k_jacobi<C><<<grid2(s.mx, s.my), dim3(BX, BY), 0, st>>>(s, u_in, u_out, f);
   return cudaGetLastError();
 }
 
-cudaError_t launch_jacobi_zero(const StencilView& s, cplx* u_out, const cplx* f, cudaStream_t st) {
+template <class C>
+cudaError_t launch_jacobi_zero(const StencilViewT<C>& s, C* u_out, const C* f, cudaStream_t st) {
   long long n = (long long)s.mx * s.my;
-  k_jacobi_zero<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, s.Dinv, u_out, f);
+  k_jacobi_zero<C><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, s.Dinv, u_out, f);
   return cudaGetLastError();
 }
 
-int residual_norm_blocks(const StencilView& s) {
+template <class C>
+int residual_norm_blocks(const StencilViewT<C>& s) {
   dim3 g = grid2(s.mx, s.my);
   return (int)(g.x * g.y);
 }
 
-cudaError_t launch_residual(const StencilView& s, const cplx* u, const cplx* f, cplx* r, double* norm_part,
+template <class C>
+cudaError_t launch_residual(const StencilViewT<C>& s, const C* u, const C* f, C* r, double* norm_part,
                             cudaStream_t st) {
-  k_residual<<<grid2(s.mx, s.my), dim3(BX, BY), 0, st>>>(s, u, f, r, norm_part);
+  k_residual<C><<<grid2(s.mx, s.my), dim3(BX, BY), 0, st>>>(s, u, f, r, norm_part);
   return cudaGetLastError();
 }
 
-cudaError_t launch_restrict(int mx, int my, const cplx* r, cplx* rc, cudaStream_t st) {
+template <class C>
+cudaError_t launch_restrict(int mx, int my, const C* r, C* rc, cudaStream_t st) {
   int mcx = (mx - 1) / 2, mcy = (my - 1) / 2;
-  k_restrict<<<dim3((mcx + 31) / 32, (mcy + 7) / 8), dim3(32, 8), 0, st>>>(mx, mcx, mcy, r, rc);
+  k_restrict<C><<<dim3((mcx + 31) / 32, (mcy + 7) / 8), dim3(32, 8), 0, st>>>(mx, mcx, mcy, r, rc);
   return cudaGetLastError();
 }
 
-cudaError_t launch_prolong_add(int mx, int my, const cplx* ec, cplx* u, cudaStream_t st) {
+template <class C>
+cudaError_t launch_prolong_add(int mx, int my, const C* ec, C* u, cudaStream_t st) {
   int mcx = (mx - 1) / 2, mcy = (my - 1) / 2;
-  k_prolong_add<<<grid2(mx, my), dim3(BX, BY), 0, st>>>(mx, my, mcx, mcy, ec, u);
+  k_prolong_add<C><<<grid2(mx, my), dim3(BX, BY), 0, st>>>(mx, my, mcx, mcy, ec, u);
   return cudaGetLastError();
 }
 
-cudaError_t launch_coarse_solve(int nc, const cplx* Ainv, const cplx* f, cplx* u, cudaStream_t st) {
-  k_coarse_solve<<<(nc + 7) / 8, 256, 0, st>>>(nc, Ainv, f, u);
+template <class C>
+cudaError_t launch_coarse_solve(int nc, const cplx* Ainv, const C* f, C* u, cudaStream_t st) {
+  k_coarse_solve<C><<<(nc + 7) / 8, 256, 0, st>>>(nc, Ainv, f, u);
   return cudaGetLastError();
 }
+
+template <class C>
+cudaError_t launch_apply(const StencilViewT<C>& s, const C* x, C* y, cudaStream_t st, double* norm_part) {
+  k_apply<C><<<grid2(s.mx, s.my), dim3(BX, BY), 0, st>>>(s, x, y, norm_part);
+  return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_norm2(const C* v, long long n, double* part, int nblocks, cudaStream_t st) {
+  k_norm2<C><<<nblocks, 256, 0, st>>>(v, n, part);
+  return cudaGetLastError();
+}
+
+#define MGC_INSTANTIATE(C)                                                                                  \
+  template cudaError_t launch_jacobi<C>(const StencilViewT<C>&, const C*, C*, const C*, cudaStream_t);     \
+  template cudaError_t launch_jacobi_zero<C>(const StencilViewT<C>&, C*, const C*, cudaStream_t);          \
+  template int residual_norm_blocks<C>(const StencilViewT<C>&);                                           \
+  template cudaError_t launch_residual<C>(const StencilViewT<C>&, const C*, const C*, C*, double*,        \
+                                          cudaStream_t);                                                  \
+  template cudaError_t launch_restrict<C>(int, int, const C*, C*, cudaStream_t);                          \
+  template cudaError_t launch_prolong_add<C>(int, int, const C*, C*, cudaStream_t);                       \
+  template cudaError_t launch_coarse_solve<C>(int, const cplx*, const C*, C*, cudaStream_t);              \
+  template cudaError_t launch_apply<C>(const StencilViewT<C>&, const C*, C*, cudaStream_t, double*);      \
+  template cudaError_t launch_norm2<C>(const C*, long long, double*, int, cudaStream_t);
+MGC_INSTANTIATE(double2)
+MGC_INSTANTIATE(float2)
+#undef MGC_INSTANTIATE
 
 cudaError_t launch_sum_partials(const double* part, int n, double* out, cudaStream_t st, const int* gate) {
   k_sum_partials<<<1, 256, 0, st>>>(part, n, out, gate);
@@ -268,12 +366,22 @@ int norm2_blocks(long long n) {
   return (int)(b < 1216 ? (b < 1 ? 1 : b) : 1216);
 }
 
-cudaError_t launch_norm2(const cplx* v, long long n, double* part, int nblocks, cudaStream_t st) {
-  k_norm2<<<nblocks, 256, 0, st>>>(v, n, part);
+cudaError_t launch_demote(long long n, const cplx* x, const double* norm2, float2* y, cudaStream_t st) {
+  k_demote<<<stride_blocks(n), 256, 0, st>>>(n, x, norm2, y);
   return cudaGetLastError();
 }
 
-cudaError_t launch_apply(const StencilView& s, const cplx* x, cplx* y, cudaStream_t st, double* norm_part) {
-  k_apply<<<grid2(s.mx, s.my), dim3(BX, BY), 0, st>>>(s, x, y, norm_part);
+cudaError_t launch_promote_add(long long n, const float2* e, const double* norm2, cplx* u, cudaStream_t st) {
+  k_promote_add<<<stride_blocks(n), 256, 0, st>>>(n, e, norm2, u);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_promote(long long n, const float2* x, cplx* y, cudaStream_t st) {
+  k_promote<<<stride_blocks(n), 256, 0, st>>>(n, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_round_copy(long long n, const cplx* a, float2* b, cudaStream_t st) {
+  k_round_copy<<<stride_blocks(n), 256, 0, st>>>(n, a, b);
   return cudaGetLastError();
 }

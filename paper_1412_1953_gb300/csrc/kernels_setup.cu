@@ -5,14 +5,12 @@
 //    contour.
 //  * Diagonal D of H - E and omega/D per node, potentials injected at coincident nodes.
 //  * Dense inverse of the coarsest-level operator (Gauss-Jordan, partial pivoting).
-//  * Bound states of H1, H2 (Eq. (9)): eigenvalue estimates by implicit QL with a
-//    Wilkinson shift applied without conjugation to the complex-symmetric tridiagonal
-//    (Bowdler, Martin, Reinsch & Wilkinson, Numer. Math. 11, 1968; the
-//    complex-symmetric use follows Cullum & Willoughby), run in single precision; the
-//    n_b with smallest real part are refined in double precision by inverse and
-//    Rayleigh-quotient iteration with a pivoted tridiagonal LU, normalised bilinearly,
-//    int phi^2 dz = 1 (Sec. 3.1, Remark 3), then two shift-and-invert steps and a
-//    bilinear Rayleigh quotient (Sec. 5.1.2, Sec. 5.2).
+//  * Bound states of H1, H2 (Eq. (9)): all eigenvalues by root-free implicit QR on the
+//    squared off-diagonals (Pal-Walker-Kahan form) applied without conjugation to the
+//    complex-symmetric tridiagonal; the n_b with smallest real part are refined by
+//    inverse and Rayleigh-quotient iteration with a pivoted tridiagonal LU, normalised
+//    bilinearly, int phi^2 dz = 1 (Sec. 3.1, Remark 3), then two shift-and-invert steps
+//    and a bilinear Rayleigh quotient (Sec. 5.1.2, Sec. 5.2).
 //  * Channel potentials V^A, V^B (Sec. 4.2) and the cyclic-reduction factors of the
 //    coupled-channel systems (Eqs. (28)-(29)).
 #include "common.cuh"
@@ -159,84 +157,60 @@ __global__ void __launch_bounds__(1024) k_coarse_inverse(StencilView s, cplx* __
 
 // ---- bound states ---------------------------------------------------------------
 
-// single-precision complex helpers for the eigenvalue estimates
-__device__ __forceinline__ float2 fk(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return fk(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 fsub2(float2 a, float2 b) { return fk(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return fk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-__device__ __forceinline__ float fabs1(float2 a) { return fabsf(a.x) + fabsf(a.y); }
-__device__ __forceinline__ float2 fdiv2(float2 a, float2 b) {      // Smith's algorithm
-  if (fabsf(b.y) <= fabsf(b.x)) {
-    float r = b.y / b.x, den = b.x + b.y * r;
-    return fk((a.x + a.y * r) / den, (a.y - a.x * r) / den);
-  }
-  float r = b.x / b.y, den = b.x * r + b.y;
-  return fk((a.x * r + a.y) / den, (a.y * r - a.x) / den);
-}
-__device__ __forceinline__ float2 fsqrt2(float2 z) {                // principal branch
-  float m = hypotf(z.x, z.y);
-  if (m == 0.0f) return fk(0.0f, 0.0f);
-  if (z.x >= 0.0f) {
-    float t = sqrtf(0.5f * (m + z.x));
-    return fk(t, z.y / (2.0f * t));
-  }
-  float t = sqrtf(0.5f * (m - z.x));
-  float sg = (z.y < 0.0f) ? -t : t;
-  return fk(z.y / (2.0f * sg), sg);
+// 1/z = conj(z)/|z|^2 (magnitudes here stay far from under/overflow).
+__device__ __forceinline__ cplx crecip(cplx z) {
+  const double q = 1.0 / (z.x * z.x + z.y * z.y);
+  return cmk(z.x * q, -z.y * q);
 }
 
-// Eigenvalue estimates of the complex-symmetric tridiagonal (d, e) by single-precision
-// implicit QL with a Wilkinson shift; d is overwritten with the eigenvalues.  The
-// estimates only pick the states and start the FP64 refinement.  Returns false if an
-// eigenvalue needs more than 60 sweeps or a rotation breaks down.
-__device__ bool ql_eigenvalues_f32(int m, float2* d, float2* e) {
-  e[m - 1] = fk(0.0f, 0.0f);
-  for (int l = 0; l < m; ++l) {
-    int sweeps = 0;
-    for (;;) {
-      int mm = l;
-      for (; mm < m - 1; ++mm) {
-        float dd = fabs1(d[mm]) + fabs1(d[mm + 1]);
-        if (fabs1(e[mm]) + dd == dd) break;
-      }
-      if (mm == l) break;
-      if (++sweeps > 60) return false;
-      float2 g = fdiv2(fsub2(d[l + 1], d[l]), fk(2.0f * e[l].x, 2.0f * e[l].y));
-      float2 r = fsqrt2(fadd2(fmul2(g, g), fk(1.0f, 0.0f)));
-      float2 gp = fadd2(g, r), gm = fsub2(g, r);
-      float2 den = (gp.x * gp.x + gp.y * gp.y >= gm.x * gm.x + gm.y * gm.y) ? gp : gm;
-      g = fadd2(fsub2(d[mm], d[l]), fdiv2(e[l], den));
-      float2 s = fk(1.0f, 0.0f), c = fk(1.0f, 0.0f), p = fk(0.0f, 0.0f);
-      bool restart = false;
-      for (int i = mm - 1; i >= l; --i) {
-        float2 f = fmul2(s, e[i]);
-        float2 b = fmul2(c, e[i]);
-        r = fsqrt2(fadd2(fmul2(f, f), fmul2(g, g)));
-        e[i + 1] = r;
-        if (r.x == 0.0f && r.y == 0.0f) {
-          if (f.x != 0.0f || f.y != 0.0f) return false;
-          d[i + 1] = fsub2(d[i + 1], p);
-          e[mm] = fk(0.0f, 0.0f);
-          restart = true;
-          break;
-        }
-        s = fdiv2(f, r);
-        c = fdiv2(g, r);
-        g = fsub2(d[i + 1], p);
-        float2 cb = fmul2(c, b);
-        r = fadd2(fmul2(fsub2(d[i], g), s), fk(2.0f * cb.x, 2.0f * cb.y));
-        p = fmul2(s, r);
-        d[i + 1] = fadd2(g, p);
-        g = fsub2(fmul2(c, r), b);
-      }
-      if (restart) continue;
-      d[l] = fsub2(d[l], p);
-      e[l] = g;
-      e[mm] = fk(0.0f, 0.0f);
+// Eigenvalues of the complex-symmetric tridiagonal with diagonal a[0..m) and squared
+// off-diagonals b2[k] (coupling k and k+1; the squares are the products east_k west_{k+1},
+// so no square root is taken) by implicit QR sweeps in the root-free form of Pal,
+// Walker and Kahan (B. N. Parlett, The Symmetric Eigenvalue Problem, Sec. 8-15), applied
+// without conjugation, with a Wilkinson shift from the trailing 2x2 block and deflation
+// at the bottom of the unreduced block.  a is overwritten with the eigenvalues.
+// Returns false on a zero pivot or when the sweep budget is exhausted.
+__device__ bool qr_rootfree_eigenvalues(int m, cplx* a, cplx* b2) {
+  const double eps2 = 4.93038065763132e-32;          // (2^-52)^2
+  long long budget = 40LL * m + 100;
+  int hi = m - 1;
+  while (hi > 0) {
+    int lo = hi;
+    while (lo > 0 && cabs1(b2[lo - 1]) > eps2 * cabs1(a[lo - 1]) * cabs1(a[lo])) --lo;
+    if (lo == hi) {
+      --hi;
+      continue;
     }
+    if (--budget < 0) return false;
+    // shift: eigenvalue of the trailing 2x2 block nearest a[hi]
+    const cplx dlt = cscal(0.5, csub(a[hi - 1], a[hi]));
+    const cplx rt = csqrt_p(cadd(cmul(dlt, dlt), b2[hi - 1]));
+    const cplx dp = cadd(dlt, rt), dm = csub(dlt, rt);
+    const cplx den = (cabs2(dp) >= cabs2(dm)) ? dp : dm;
+    const cplx sigma = (den.x == 0.0 && den.y == 0.0) ? a[hi] : csub(a[hi], cmul(b2[hi - 1], crecip(den)));
+    // one root-free QR sweep over lo..hi
+    cplx c2 = cmk(1.0, 0.0), s2 = cmk(0.0, 0.0);
+    cplx gam = csub(a[lo], sigma);
+    cplx p = cmul(gam, gam);
+    for (int k = lo; k < hi; ++k) {
+      const cplx r = cadd(p, b2[k]);
+      if (r.x == 0.0 && r.y == 0.0) return false;
+      if (k > lo) b2[k - 1] = cmul(s2, r);
+      const cplx c2old = c2;
+      const cplx rinv = crecip(r);
+      c2 = cmul(p, rinv);
+      s2 = cmul(b2[k], rinv);
+      const cplx gold = gam;
+      const cplx alpha = csub(a[k + 1], sigma);
+      gam = csub(cmul(c2, alpha), cmul(s2, gold));
+      a[k] = cadd(csub(cadd(gold, alpha), gam), sigma);
+      p = (c2.x == 0.0 && c2.y == 0.0) ? cmul(c2old, b2[k]) : cmul(cmul(gam, gam), crecip(c2));
+    }
+    b2[hi - 1] = cmul(s2, p);
+    a[hi] = cadd(gam, sigma);
   }
   for (int k = 0; k < m; ++k)
-    if (!isfinite(d[k].x) || !isfinite(d[k].y)) return false;
+    if (!isfinite(a[k].x) || !isfinite(a[k].y)) return false;
   return true;
 }
 
@@ -344,10 +318,10 @@ __device__ cplx rayleigh_ratio(int m, const cplx* west, const cplx* east, const 
   return cdiv(num, den);
 }
 
-// Eigenvalue estimates by single-precision QL (thread 0), the n_b with the smallest
-// real part; then per state (thread q): FP64 inverse iteration at the estimate, Rayleigh-
-// quotient iteration to the FP64 eigenvalue, bilinear normalisation, and the paper's two
-// shift-and-invert steps.  Coinciding refined eigenvalues flag a failure.
+// Eigenvalues by root-free QR (thread 0), the n_b with the smallest real part; then per
+// state (thread q): inverse iteration at the eigenvalue, Rayleigh-quotient iteration,
+// bilinear normalisation, and the paper's two shift-and-invert steps.  Coinciding refined
+// eigenvalues flag a failure.
 __global__ void __launch_bounds__(32) k_bound_states(int m, const cplx* __restrict__ west,
                                                      const cplx* __restrict__ east, const cplx* __restrict__ diag,
                                                      const cplx* __restrict__ v, const cplx* __restrict__ w, int nb,
@@ -357,27 +331,25 @@ __global__ void __launch_bounds__(32) k_bound_states(int m, const cplx* __restri
   __shared__ cplx fin_l[MGC_MAX_NB];
   __shared__ int ok;
   const int q = threadIdx.x;
-  float2* d = reinterpret_cast<float2*>(scratch);          // m
-  float2* e = d + m;                                        // m
+  cplx* d = scratch;            // m
+  cplx* e2 = scratch + m;       // m
   if (q == 0) {
-    // symmetric form: e_k^2 = east_k * west_{k+1}
+    // squared off-diagonals of the symmetric form: e_k^2 = east_k * west_{k+1}
     for (int k = 0; k < m; ++k) {
-      cplx dk = cadd(diag[k], v[k]);
-      d[k] = fk((float)dk.x, (float)dk.y);
-      cplx ek = (k + 1 < m) ? csqrt_p(cmul(east[k], west[k + 1])) : cmk(0.0, 0.0);
-      e[k] = fk((float)ek.x, (float)ek.y);
+      d[k] = cadd(diag[k], v[k]);
+      e2[k] = (k + 1 < m) ? cmul(east[k], west[k + 1]) : cmk(0.0, 0.0);
     }
-    ok = ql_eigenvalues_f32(m, d, e) ? 1 : 0;
+    ok = qr_rootfree_eigenvalues(m, d, e2) ? 1 : 0;
     if (ok) {
       // the nb eigenvalues with the smallest real part, ascending (ties: lower index)
       for (int s = 0; s < nb; ++s) {
         int kb = -1;
         for (int k = 0; k < m; ++k) {
-          if (e[k].x == 1.0e30f) continue;            // already taken
+          if (e2[k].x == 1.0e300) continue;            // already taken
           if (kb < 0 || d[k].x < d[kb].x) kb = k;
         }
-        sel[s] = cmk((double)d[kb].x, (double)d[kb].y);
-        e[kb] = fk(1.0e30f, 0.0f);
+        sel[s] = d[kb];
+        e2[kb] = cmk(1.0e300, 0.0);
       }
     } else {
       atomicOr(status, MGC_ST_EIG);
@@ -385,16 +357,16 @@ __global__ void __launch_bounds__(32) k_bound_states(int m, const cplx* __restri
   }
   __syncthreads();
   if (ok && q < nb) {
-    cplx* base = scratch + m + (size_t)q * 5 * m;
+    cplx* base = scratch + 2 * m + (size_t)q * 5 * m;
     TriLU lu{base, base + m, base + 2 * m, base + 3 * m,
-             reinterpret_cast<int*>(scratch + m + (size_t)nb * 5 * m) + (size_t)q * m};
+             reinterpret_cast<int*>(scratch + 2 * m + (size_t)nb * 5 * m) + (size_t)q * m};
     cplx* x = base + 4 * m;
     double scale = 0.0;
     for (int k = 0; k < m; ++k) scale = fmax(scale, cabs1(cadd(diag[k], v[k])));
     const double tiny = 1e-300 + 1e-16 * scale;
     cplx lmb = sel[q];
     for (int k = 0; k < m; ++k) x[k] = cmk(1.0, 0.0);
-    // two inverse-iteration steps at the single-precision estimate
+    // two inverse-iteration steps at the QR eigenvalue
     tri_lu(m, west, east, diag, v, lmb, lu);
     for (int it = 0; it < 2; ++it) {
       tri_solve(m, lu, x, tiny);
@@ -632,9 +604,8 @@ cudaError_t launch_coarse_inverse(const StencilView& s, cplx* aug, cplx* Ainv, i
 }
 
 size_t bound_states_scratch(int m, int nb) {
-  // single-precision d, e (one complex128 slot per pair) + per state (u0, u1, u2, mu, x)
-  // + per state int pivots
-  return sizeof(cplx) * ((size_t)m + (size_t)nb * 5 * m) + sizeof(int) * (size_t)nb * m;
+  // d, e^2 + per state (u0, u1, u2, mu, x) + per state int pivots
+  return sizeof(cplx) * ((size_t)2 * m + (size_t)nb * 5 * m) + sizeof(int) * (size_t)nb * m;
 }
 
 cudaError_t launch_bound_states(int m, const cplx* west, const cplx* east, const cplx* diag, const cplx* v,

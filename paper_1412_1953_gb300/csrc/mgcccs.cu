@@ -2,6 +2,7 @@
 // recursion, CCCS sequence, solve loop and the C ABI declared in include/mgcccs.h.
 // Every numerical step runs in the kernels of kernels_*.cu; this file only orders
 // launches on the handle's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -20,6 +21,10 @@ struct LevelBufs {
   cplx *D, *Dinv;
   cplx *u, *f, *t, *r;     // level 0: only t, r (u and f belong to the caller)
   StencilView sv;
+  // complex64 copies for the mixed-precision preconditioner (precision == 1)
+  float2 *west_x32, *east_x32, *west_y32, *east_y32, *D32, *Dinv32;
+  float2 *u32, *f32, *t32, *r32;
+  StencilView32 sv32;
 };
 
 }  // namespace
@@ -43,6 +48,16 @@ struct mgcccs_handle {
   double* norm_out;
   int* status;
   cplx *hu, *hf;
+  cplx* wdot_part;         // partials of the weighted dot products
+  // mixed precision: complex64 states, projections and GMRES basis; FP64 outer residual
+  int mixed;
+  double inner_rtol;
+  float2 *phi32, *vphi32, *wphi32, *wvphi32;
+  CCView32 cc32;
+  float2 *V32, *Z32, *e32;
+  cplx* r64;
+  cudaGraphExec_t step_exec32[MGC_MAX_RESTART];
+  long long step_launches32[MGC_MAX_RESTART];
   // GMRES(m) outer solver
   int km;
   int kr_nblk;
@@ -87,6 +102,9 @@ bool valid_params(const mgcccs_params* p) {
   if (!(p->Lx > 0) || !(p->Ly > 0) || !std::isfinite(p->E) || !std::isfinite(p->omega)) return false;
   if (!std::isfinite(p->theta) || !std::isfinite(p->coarse_gamma)) return false;
   if (p->krylov_restart < 0 || p->krylov_restart > MGC_MAX_RESTART) return false;
+  if (p->precision < 0 || p->precision > 1) return false;
+  if (p->precision == 1 && p->krylov_restart < 1) return false;
+  if (!(p->inner_rtol >= 0.0) || !(p->inner_rtol < 1.0)) return false;
   return true;
 }
 
@@ -114,7 +132,19 @@ void layout(mgcccs_handle* h, Carver& cv) {
     } else {
       b.u = b.f = nullptr;
     }
+    if (p.precision == 1) {
+      b.west_x32 = cv.take<float2>(b.mx); b.east_x32 = cv.take<float2>(b.mx);
+      b.west_y32 = cv.take<float2>(b.my); b.east_y32 = cv.take<float2>(b.my);
+      b.D32 = cv.take<float2>(n2);
+      b.Dinv32 = cv.take<float2>(n2);
+      b.t32 = cv.take<float2>(n2);
+      b.r32 = cv.take<float2>(n2);
+      b.u32 = l > 0 ? cv.take<float2>(n2) : nullptr;
+      b.f32 = l > 0 ? cv.take<float2>(n2) : nullptr;
+    }
   }
+  h->mixed = p.precision == 1;
+  h->inner_rtol = p.inner_rtol > 0.0 ? p.inner_rtol : 1e-5;
   const LevelBufs& c = h->lv[L - 1];
   h->nc = c.mx * c.my;
   h->Ainv = cv.take<cplx>((size_t)h->nc * h->nc);
@@ -154,6 +184,7 @@ void layout(mgcccs_handle* h, Carver& cv) {
     CCView& cc = h->cc;
     cc.mx = mx; cc.my = my; cc.nb = nb;
     cc.wphi = h->wphi; cc.wvphi = h->wvphi; cc.phi = h->phi; cc.vphi = h->vphi;
+    cc.phi64 = h->phi; cc.vphi64 = h->vphi; cc.wvphi64 = h->wvphi;
     cc.Px_part = cv.take<cplx>((size_t)cc_tiles_x(mx) * nb * my);
     cc.Py_part = cv.take<cplx>((size_t)cc_tiles_y(my) * nb * mx);
     cc.Px = cv.take<cplx>((size_t)nb * my);
@@ -165,6 +196,19 @@ void layout(mgcccs_handle* h, Carver& cv) {
     cc.eB = cv.take<cplx>((size_t)nb * mx);
     h->crA.r = cc.rA; h->crA.e = cc.eA;
     h->crB.r = cc.rB; h->crB.e = cc.eB;
+    if (p.precision == 1) {
+      h->phi32 = cv.take<float2>((size_t)nb * mx);
+      h->vphi32 = cv.take<float2>((size_t)nb * my);
+      h->wphi32 = cv.take<float2>((size_t)nb * mx);
+      h->wvphi32 = cv.take<float2>((size_t)nb * my);
+      CCView32& c3 = h->cc32;
+      c3.mx = mx; c3.my = my; c3.nb = nb;
+      c3.wphi = h->wphi32; c3.wvphi = h->wvphi32; c3.phi = h->phi32; c3.vphi = h->vphi32;
+      c3.Px_part = cv.take<float2>((size_t)cc_tiles_x(mx) * nb * my);
+      c3.Py_part = cv.take<float2>((size_t)cc_tiles_y(my) * nb * mx);
+      c3.Px = cc.Px; c3.Py = cc.Py; c3.c = cc.c; c3.rA = cc.rA; c3.rB = cc.rB; c3.eA = cc.eA; c3.eB = cc.eB;
+      c3.phi64 = h->phi; c3.vphi64 = h->vphi; c3.wvphi64 = h->wvphi;
+    }
   }
   StencilView s0{};
   s0.mx = mx; s0.my = my;
@@ -176,8 +220,15 @@ void layout(mgcccs_handle* h, Carver& cv) {
   h->kr_nblk = krylov_blocks(N);
   if (h->km > 0) {
     const int m = h->km;
-    h->V = cv.take<cplx>((size_t)(m + 1) * N);
-    h->Z = cv.take<cplx>((size_t)m * N);
+    if (p.precision == 1) {
+      h->V32 = cv.take<float2>((size_t)(m + 1) * N);
+      h->Z32 = cv.take<float2>((size_t)m * N);
+      h->e32 = cv.take<float2>((size_t)N);
+      h->r64 = cv.take<cplx>((size_t)N);
+    } else {
+      h->V = cv.take<cplx>((size_t)(m + 1) * N);
+      h->Z = cv.take<cplx>((size_t)m * N);
+    }
     h->Hh = cv.take<cplx>((size_t)(m + 1) * m);
     h->cs = cv.take<cplx>(m);
     h->sn = cv.take<cplx>(m);
@@ -193,6 +244,7 @@ void layout(mgcccs_handle* h, Carver& cv) {
   h->status = cv.take<int>(4);
   h->hu = cv.take<cplx>((size_t)mx * my);
   h->hf = cv.take<cplx>((size_t)mx * my);
+  h->wdot_part = cv.take<cplx>(wdot_blocks((long long)mx * my));
 }
 
 // Number of leading interior nodes whose 3-point stencil lies on the unbent part of
@@ -305,65 +357,121 @@ int do_setup(mgcccs_handle* h, const cplx* v1, const cplx* v2, const cplx* v12) 
     MGC_LAUNCH(launch_channel_factor(h->crB, b.diag_x, v1, p.E, h->mu, h->VB, b.west_x, b.east_x, h->cr_scratch,
                                      h->status, st));
   }
+  int rc0 = read_status(h);
+  if (rc0 || !h->mixed) return rc0;
+  // complex64 copies of every level's operator and of the bound states
+  for (int l = 0; l < h->L; ++l) {
+    LevelBufs& b = h->lv[l];
+    const long long n2 = (long long)b.mx * b.my;
+    MGC_LAUNCH(launch_round_copy(b.mx, b.west_x, b.west_x32, st));
+    MGC_LAUNCH(launch_round_copy(b.mx, b.east_x, b.east_x32, st));
+    MGC_LAUNCH(launch_round_copy(b.my, b.west_y, b.west_y32, st));
+    MGC_LAUNCH(launch_round_copy(b.my, b.east_y, b.east_y32, st));
+    MGC_LAUNCH(launch_round_copy(n2, b.D, b.D32, st));
+    MGC_LAUNCH(launch_round_copy(n2, b.Dinv, b.Dinv32, st));
+    StencilView32& s3 = b.sv32;
+    s3.mx = b.mx; s3.my = b.my; s3.ux = b.sv.ux; s3.uy = b.sv.uy; s3.rbox = b.sv.rbox;
+    s3.cu = make_float2((float)b.sv.cu.x, (float)b.sv.cu.y);
+    s3.west_x = b.west_x32; s3.east_x = b.east_x32; s3.west_y = b.west_y32; s3.east_y = b.east_y32;
+    s3.D = b.D32; s3.Dinv = b.Dinv32;
+  }
+  if (h->nb > 0) {
+    const int nb = h->nb;
+    MGC_LAUNCH(launch_round_copy((long long)nb * h->lv[0].mx, h->phi, h->phi32, st));
+    MGC_LAUNCH(launch_round_copy((long long)nb * h->lv[0].my, h->vphi, h->vphi32, st));
+    MGC_LAUNCH(launch_round_copy((long long)nb * h->lv[0].mx, h->wphi, h->wphi32, st));
+    MGC_LAUNCH(launch_round_copy((long long)nb * h->lv[0].my, h->wvphi, h->wvphi32, st));
+  }
   return read_status(h);
 }
 
+// Typed views of a level's operator and buffers: complex128 for the plain path,
+// complex64 for the mixed-precision preconditioner.
+template <class C>
+struct LevelIO {
+  const StencilViewT<C>* sv;
+  C *u, *f, *t, *r;
+  int mx, my;
+};
+template <class C>
+LevelIO<C> level_io(mgcccs_handle* h, int l);
+template <>
+LevelIO<cplx> level_io<cplx>(mgcccs_handle* h, int l) {
+  LevelBufs& b = h->lv[l];
+  return LevelIO<cplx>{&b.sv, b.u, b.f, b.t, b.r, b.mx, b.my};
+}
+template <>
+LevelIO<float2> level_io<float2>(mgcccs_handle* h, int l) {
+  LevelBufs& b = h->lv[l];
+  return LevelIO<float2>{&b.sv32, b.u32, b.f32, b.t32, b.r32, b.mx, b.my};
+}
+template <class C>
+const CCViewT<C>& cc_view(mgcccs_handle* h);
+template <>
+const CCViewT<cplx>& cc_view<cplx>(mgcccs_handle* h) { return h->cc; }
+template <>
+const CCViewT<float2>& cc_view<float2>(mgcccs_handle* h) { return h->cc32; }
+
 // One V-cycle on level l.  `u` holds the initial guess unless zero_init; the result is
 // returned in *out (either u or the level's t buffer).
-int vcycle_rec(mgcccs_handle* h, int l, cplx* u, const cplx* f, bool zero_init, cplx** out) {
+template <class C>
+int vcycle_rec(mgcccs_handle* h, int l, C* u, const C* f, bool zero_init, C** out) {
   cudaStream_t st = h->st;
-  LevelBufs& b = h->lv[l];
+  LevelIO<C> b = level_io<C>(h, l);
   if (l == h->L - 1) {
     MGC_LAUNCH(launch_coarse_solve(h->nc, h->Ainv, f, u, st));
     *out = u;
     return MGCCCS_OK;
   }
-  cplx* cur = u;
-  cplx* oth = b.t;
+  C* cur = u;
+  C* oth = b.t;
   bool zero = zero_init;
   for (int s = 0; s < h->p.nu1; ++s) {
-    if (zero) MGC_LAUNCH(launch_jacobi_zero(b.sv, oth, f, st));
-    else MGC_LAUNCH(launch_jacobi(b.sv, cur, oth, f, st));
+    if (zero) MGC_LAUNCH(launch_jacobi_zero(*b.sv, oth, f, st));
+    else MGC_LAUNCH(launch_jacobi(*b.sv, (const C*)cur, oth, f, st));
     zero = false;
-    cplx* tmp = cur; cur = oth; oth = tmp;
+    C* tmp = cur; cur = oth; oth = tmp;
   }
   if (zero) {
     // no pre-smoothing and a zero guess: the residual is f itself
-    MGC_CUDA(cudaMemsetAsync(cur, 0, sizeof(cplx) * (size_t)b.mx * b.my, st));
+    MGC_CUDA(cudaMemsetAsync(cur, 0, sizeof(C) * (size_t)b.mx * b.my, st));
   }
-  LevelBufs& c = h->lv[l + 1];
-  MGC_LAUNCH(launch_residual(b.sv, cur, f, b.r, nullptr, st));
-  MGC_LAUNCH(launch_restrict(b.mx, b.my, b.r, c.f, st));
-  cplx* ec = nullptr;
-  int rc = vcycle_rec(h, l + 1, c.u, c.f, true, &ec);
+  LevelIO<C> c = level_io<C>(h, l + 1);
+  MGC_LAUNCH(launch_residual(*b.sv, (const C*)cur, f, b.r, (double*)nullptr, st));
+  MGC_LAUNCH(launch_restrict(b.mx, b.my, (const C*)b.r, c.f, st));
+  C* ec = nullptr;
+  int rc = vcycle_rec<C>(h, l + 1, c.u, c.f, true, &ec);
   if (rc) return rc;
-  MGC_LAUNCH(launch_prolong_add(b.mx, b.my, ec, cur, st));
+  MGC_LAUNCH(launch_prolong_add(b.mx, b.my, (const C*)ec, cur, st));
   for (int s = 0; s < h->p.nu2; ++s) {
-    MGC_LAUNCH(launch_jacobi(b.sv, cur, oth, f, st));
-    cplx* tmp = cur; cur = oth; oth = tmp;
+    MGC_LAUNCH(launch_jacobi(*b.sv, (const C*)cur, oth, f, st));
+    C* tmp = cur; cur = oth; oth = tmp;
   }
   *out = cur;
   return MGCCCS_OK;
 }
 
-int vcycle_fine(mgcccs_handle* h, cplx* u, const cplx* f, bool zero_init) {
-  cplx* res = nullptr;
-  int rc = vcycle_rec(h, 0, u, f, zero_init, &res);
+template <class C>
+int vcycle_fine(mgcccs_handle* h, C* u, const C* f, bool zero_init) {
+  C* res = nullptr;
+  int rc = vcycle_rec<C>(h, 0, u, f, zero_init, &res);
   if (rc) return rc;
   if (res != u) {
     const LevelBufs& b = h->lv[0];
-    MGC_CUDA(cudaMemcpyAsync(u, res, sizeof(cplx) * (size_t)b.mx * b.my, cudaMemcpyDeviceToDevice, h->st));
+    MGC_CUDA(cudaMemcpyAsync(u, res, sizeof(C) * (size_t)b.mx * b.my, cudaMemcpyDeviceToDevice, h->st));
   }
   return MGCCCS_OK;
 }
 
-int cccs_fine(mgcccs_handle* h, cplx* u, const cplx* f) {
+template <class C>
+int cccs_fine(mgcccs_handle* h, C* u, const C* f) {
   cudaStream_t st = h->st;
-  MGC_LAUNCH(launch_residual_project(h->lv[0].sv, h->cc, u, f, st));
-  MGC_LAUNCH(launch_cc_rhs(h->cc, st));
+  const CCViewT<C>& cc = cc_view<C>(h);
+  MGC_LAUNCH(launch_residual_project(*level_io<C>(h, 0).sv, cc, (const C*)u, f, st));
+  MGC_LAUNCH(launch_cc_rhs(cc, st));
   h->launches += 2;   // launch_cc_rhs issues three kernels
   MGC_LAUNCH(launch_channel_solve(h->crA, h->crB, st));
-  MGC_LAUNCH(launch_cccs_correct(h->cc, u, st));
+  MGC_LAUNCH(launch_cccs_correct(cc, u, st));
   return MGCCCS_OK;
 }
 
@@ -397,77 +505,130 @@ int read_double(mgcccs_handle* h, const double* dev, double* out) {
 }
 
 // z = M^{-1} r: one V-cycle from zero, then the CCCS.
-int precond(mgcccs_handle* h, cplx* z, const cplx* r) {
-  int rc = vcycle_fine(h, z, r, true);
+template <class C>
+int precond(mgcccs_handle* h, C* z, const C* r) {
+  int rc = vcycle_fine<C>(h, z, r, true);
   if (rc) return rc;
-  if (h->nb > 0) rc = cccs_fine(h, z, r);
+  if (h->nb > 0) rc = cccs_fine<C>(h, z, r);
   return rc;
 }
 
-// Arnoldi step j of GMRES(m): z_j = M^{-1} v_j, w = A z_j, classical Gram-Schmidt with
-// a DGKS-gated second pass, h_{j+1,j} = |w|, v_{j+1} = w / h_{j+1,j}, Givens rotation j,
-// and the residual estimate |g_{j+1}| copied to est_host[j].  Touches only buffers of
-// the handle, so the launch sequence of each j is fixed and can be replayed as a graph.
+// Krylov basis and graph cache of the two precisions.
+template <class C> C* kv_V(mgcccs_handle* h);
+template <class C> C* kv_Z(mgcccs_handle* h);
+template <> cplx* kv_V<cplx>(mgcccs_handle* h) { return h->V; }
+template <> cplx* kv_Z<cplx>(mgcccs_handle* h) { return h->Z; }
+template <> float2* kv_V<float2>(mgcccs_handle* h) { return h->V32; }
+template <> float2* kv_Z<float2>(mgcccs_handle* h) { return h->Z32; }
+template <class C> cudaGraphExec_t* step_cache(mgcccs_handle* h);
+template <> cudaGraphExec_t* step_cache<cplx>(mgcccs_handle* h) { return h->step_exec; }
+template <> cudaGraphExec_t* step_cache<float2>(mgcccs_handle* h) { return h->step_exec32; }
+template <class C> long long* step_count(mgcccs_handle* h);
+template <> long long* step_count<cplx>(mgcccs_handle* h) { return h->step_launches; }
+template <> long long* step_count<float2>(mgcccs_handle* h) { return h->step_launches32; }
+
+// Arnoldi step j of GMRES(m) with a basis of element type C: z_j = M^{-1} v_j,
+// w = A z_j, classical Gram-Schmidt with a cancellation-gated second pass,
+// h_{j+1,j} = |w|, v_{j+1} = w / h_{j+1,j}, Givens rotation j, and the residual estimate
+// |g_{j+1}| copied to est_host[j].  Touches only buffers of the handle, so the launch
+// sequence of each j is fixed and can be replayed as a graph.  The Hessenberg matrix,
+// rotations and inner products are FP64 in both precisions.
+template <class C>
 int issue_arnoldi_step(mgcccs_handle* h, int j) {
   cudaStream_t st = h->st;
   const int m = h->km;
-  const StencilView& s0 = h->lv[0].sv;
+  const StencilViewT<C>& s0 = *level_io<C>(h, 0).sv;
   const long long N = (long long)s0.mx * s0.my;
   const int nb = h->kr_nblk;
-  cplx* vj = h->V + (size_t)j * N;
-  cplx* w = h->V + (size_t)(j + 1) * N;
-  cplx* zj = h->Z + (size_t)j * N;
+  C* V = kv_V<C>(h);
+  C* vj = V + (size_t)j * N;
+  C* w = V + (size_t)(j + 1) * N;
+  C* zj = kv_Z<C>(h) + (size_t)j * N;
   cplx* col = h->Hh + (size_t)j * (m + 1);
-  int rc = precond(h, zj, vj);
+  int rc = precond<C>(h, zj, vj);
   if (rc) return rc;
   // w = A z_j, with |w|^2 for the reorthogonalisation test
-  MGC_LAUNCH(launch_apply(s0, zj, w, st, h->norm_part));
+  MGC_LAUNCH(launch_apply(s0, (const C*)zj, w, st, h->norm_part));
   MGC_LAUNCH(launch_sum_partials(h->norm_part, residual_norm_blocks(s0), h->norm_out + 3, st));
   // Gram-Schmidt, first pass: H(0:j, j) = V^H w ; w -= V H(0:j, j)
-  MGC_LAUNCH(launch_multidot(N, j + 1, h->V, N, w, h->dotpart, nb, nullptr, st));
+  MGC_LAUNCH(launch_multidot(N, j + 1, (const C*)V, N, (const C*)w, h->dotpart, nb, (const int*)nullptr, st));
   MGC_LAUNCH(launch_reduce_dots(nb, j + 1, h->dotpart, col, nullptr, st));
-  MGC_LAUNCH(launch_multiaxpy(N, j + 1, h->V, N, col, -1.0, w, h->norm_part, nb, nullptr, st));
+  MGC_LAUNCH(launch_multiaxpy(N, j + 1, (const C*)V, N, col, -1.0, w, h->norm_part, nb, (const int*)nullptr, st));
   MGC_LAUNCH(launch_sum_partials(h->norm_part, nb, h->norm_out + 1, st));
-  // second pass only when the first one cancelled more than half of |w|^2 (DGKS);
+  // second pass only when the first one cancelled |w| by more than 1e3;
   // the corrections are added into H(0:j, j)
   MGC_LAUNCH(launch_dgks(h->norm_out + 3, h->norm_out + 1, h->gate, st));
-  MGC_LAUNCH(launch_multidot(N, j + 1, h->V, N, w, h->dotpart, nb, h->gate, st));
+  MGC_LAUNCH(launch_multidot(N, j + 1, (const C*)V, N, (const C*)w, h->dotpart, nb, (const int*)h->gate, st));
   MGC_LAUNCH(launch_reduce_dots(nb, j + 1, h->dotpart, h->hc, col, st));
-  MGC_LAUNCH(launch_multiaxpy(N, j + 1, h->V, N, h->hc, -1.0, w, h->norm_part, nb, h->gate, st));
+  MGC_LAUNCH(launch_multiaxpy(N, j + 1, (const C*)V, N, h->hc, -1.0, w, h->norm_part, nb, (const int*)h->gate, st));
   MGC_LAUNCH(launch_sum_partials(h->norm_part, nb, h->norm_out + 1, st, h->gate));
-  MGC_LAUNCH(launch_scale_by_norm(N, w, w, h->norm_out + 1, col + j + 1, nb, st));
+  MGC_LAUNCH(launch_scale_by_norm(N, (const C*)w, w, h->norm_out + 1, col + j + 1, nb, st));
   MGC_LAUNCH(launch_givens(j, m, h->Hh, h->cs, h->sn, h->g, h->norm_out + 2, st));
   MGC_CUDA(cudaMemcpyAsync(h->est_host + j, h->norm_out + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
   return MGCCCS_OK;
 }
 
 // Launch Arnoldi step j: replay its graph, capturing it on first use.
+template <class C>
 int launch_arnoldi_step(mgcccs_handle* h, int j) {
-  if (!h->step_exec[j]) {
+  cudaGraphExec_t* cache = step_cache<C>(h);
+  long long* count = step_count<C>(h);
+  if (!cache[j]) {
     cudaStream_t orig = h->st;
     const long long before = h->launches;
     h->st = h->cap_st;
     MGC_CUDA(cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal));
-    int rc = issue_arnoldi_step(h, j);
+    int rc = issue_arnoldi_step<C>(h, j);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->cap_st, &g);
     h->st = orig;
-    h->step_launches[j] = h->launches - before;
+    count[j] = h->launches - before;
     h->launches = before;
     if (rc) {
       if (g) cudaGraphDestroy(g);
       return rc;
     }
     if (e != cudaSuccess) return MGCCCS_ECUDA;
-    e = cudaGraphInstantiate(&h->step_exec[j], g, 0);
+    e = cudaGraphInstantiate(&cache[j], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-      h->step_exec[j] = nullptr;
+      cache[j] = nullptr;
       return MGCCCS_ECUDA;
     }
   }
-  MGC_CUDA(cudaGraphLaunch(h->step_exec[j], h->st));
-  h->launches += h->step_launches[j];
+  MGC_CUDA(cudaGraphLaunch(cache[j], h->st));
+  h->launches += count[j];
+  return MGCCCS_OK;
+}
+
+// One GMRES(m) cycle on the basis of type C whose v_0 is already in place and whose
+// g = (beta, 0, ...): launches Arnoldi steps (the host checks step j-1 while step j
+// runs) until est/scale <= target or m steps or the step budget; returns the number k
+// of steps to use.  est/scale is recorded in history.
+template <class C>
+int arnoldi_cycle(mgcccs_handle* h, double scale, double target, int* steps, int max_iter, double* history,
+                  int* k_out, bool* nonfinite) {
+  cudaStream_t st = h->st;
+  const int m = h->km;
+  int k = 0;
+  *nonfinite = false;
+  for (int j = 0; j <= m; ++j) {
+    if (j < m) {
+      int rc = launch_arnoldi_step<C>(h, j);
+      if (rc) return rc;
+      MGC_CUDA(cudaEventRecord(h->ev[j & 1], st));
+    }
+    if (j == 0) continue;
+    // residual estimate of step j-1 (step j, if launched, runs meanwhile)
+    MGC_CUDA(cudaEventSynchronize(h->ev[(j - 1) & 1]));
+    const double est = h->est_host[j - 1] * scale;
+    if (history) history[*steps] = est;
+    ++*steps;
+    k = j;
+    if (!std::isfinite(est)) { *nonfinite = true; break; }
+    if (est <= target || *steps >= max_iter) break;
+  }
+  *k_out = k;
   return MGCCCS_OK;
 }
 
@@ -487,7 +648,7 @@ int gmres_impl(mgcccs_handle* h, cplx* u, const cplx* f, double fn, double rtol,
   double rr = INFINITY;
   for (;;) {
     // true residual r = f - A u into V_0
-    MGC_LAUNCH(launch_residual(s0, u, f, h->V, h->norm_part, st));
+    MGC_LAUNCH(launch_residual(s0, (const cplx*)u, f, h->V, h->norm_part, st));
     MGC_LAUNCH(launch_sum_partials(h->norm_part, residual_norm_blocks(s0), h->norm_out, st));
     double rn2 = 0.0;
     int rc = read_double(h, h->norm_out, &rn2);
@@ -500,25 +661,11 @@ int gmres_impl(mgcccs_handle* h, cplx* u, const cplx* f, double fn, double rtol,
     }
     if (rr <= rtol || steps >= max_iter) break;
     MGC_LAUNCH(launch_zero_c(m + 1, h->g, st));
-    MGC_LAUNCH(launch_scale_by_norm(N, h->V, h->V, h->norm_out, h->g, nb, st));
+    MGC_LAUNCH(launch_scale_by_norm(N, (const cplx*)h->V, h->V, h->norm_out, h->g, nb, st));
     int k = 0;
     bool nonfinite = false;
-    for (int j = 0; j <= m; ++j) {
-      if (j < m) {
-        rc = launch_arnoldi_step(h, j);
-        if (rc) return rc;
-        MGC_CUDA(cudaEventRecord(h->ev[j & 1], st));
-      }
-      if (j == 0) continue;
-      // residual estimate of step j-1 (step j, if launched, runs meanwhile)
-      MGC_CUDA(cudaEventSynchronize(h->ev[(j - 1) & 1]));
-      const double est = h->est_host[j - 1] / fn;
-      if (history) history[steps] = est;
-      ++steps;
-      k = j;
-      if (!std::isfinite(est)) { nonfinite = true; break; }
-      if (est <= rtol || steps >= max_iter) break;
-    }
+    rc = arnoldi_cycle<cplx>(h, 1.0 / fn, rtol, &steps, max_iter, history, &k, &nonfinite);
+    if (rc) return rc;
     if (nonfinite) {
       MGC_CUDA(cudaStreamSynchronize(st));
       if (iters) *iters = steps;
@@ -526,7 +673,65 @@ int gmres_impl(mgcccs_handle* h, cplx* u, const cplx* f, double fn, double rtol,
       return MGCCCS_ENONFINITE;
     }
     MGC_LAUNCH(launch_hess_solve(k, m, h->Hh, h->g, h->y, st));
-    MGC_LAUNCH(launch_multiaxpy(N, k, h->Z, N, h->y, 1.0, u, nullptr, nb, nullptr, st));
+    MGC_LAUNCH(launch_multiaxpy(N, k, (const cplx*)h->Z, N, h->y, 1.0, u, (double*)nullptr, nb, (const int*)nullptr, st));
+  }
+  if (iters) *iters = steps;
+  if (relres) *relres = rr;
+  return rr <= rtol ? MGCCCS_OK : MGCCCS_ENOTCONV;
+}
+
+// Mixed precision: iterative refinement in FP64 around one complex64 GMRES(m) cycle per
+// refinement step (GMRES-IR).  Each step forms the true residual r = f - A u in FP64,
+// rounds r/|r| to complex64 as v_0, runs one preconditioned GMRES cycle in complex64
+// (V-cycle, projections, corrections and the Krylov basis in complex64; coarsest solve,
+// channel solves, Hessenberg and rotations in FP64) until the cycle's estimate reaches
+// the inner tolerance, and adds |r| e to u in FP64.  Counts Arnoldi steps as iterations.
+int gmres_ir_impl(mgcccs_handle* h, cplx* u, const cplx* f, double fn, double rtol, int max_iter, int* iters,
+                  double* relres, double* history) {
+  cudaStream_t st = h->st;
+  const int m = h->km;
+  const StencilView& s0 = h->lv[0].sv;
+  const long long N = (long long)s0.mx * s0.my;
+  const int nb = h->kr_nblk;
+  int steps = 0;
+  double rr = INFINITY;
+  for (;;) {
+    MGC_LAUNCH(launch_residual(s0, (const cplx*)u, f, h->r64, h->norm_part, st));
+    MGC_LAUNCH(launch_sum_partials(h->norm_part, residual_norm_blocks(s0), h->norm_out, st));
+    double rn2 = 0.0;
+    int rc = read_double(h, h->norm_out, &rn2);
+    if (rc) return rc;
+    rr = std::sqrt(rn2) / fn;
+    if (!std::isfinite(rr)) {
+      if (iters) *iters = steps;
+      if (relres) *relres = rr;
+      return MGCCCS_ENONFINITE;
+    }
+    if (rr <= rtol || steps >= max_iter) break;
+    // v_0 = r/|r| in complex64, renormalised in the rounded precision; g = (|v_0|, 0, ...)
+    MGC_LAUNCH(launch_demote(N, h->r64, h->norm_out, h->V32, st));
+    MGC_LAUNCH(launch_norm2(h->V32, N, h->norm_part, norm2_blocks(N), st));
+    MGC_LAUNCH(launch_sum_partials(h->norm_part, norm2_blocks(N), h->norm_out + 1, st));
+    MGC_LAUNCH(launch_zero_c(m + 1, h->g, st));
+    MGC_LAUNCH(launch_scale_by_norm(N, (const float2*)h->V32, h->V32, h->norm_out + 1, h->g, nb, st));
+    // inner target: the cycle's own tolerance, and no deeper than the outer goal needs
+    const double beta = std::sqrt(rn2);
+    const double target = std::max(h->inner_rtol, 0.5 * rtol * fn / beta);
+    int k = 0;
+    bool nonfinite = false;
+    rc = arnoldi_cycle<float2>(h, beta / fn, target * beta / fn, &steps, max_iter, history, &k, &nonfinite);
+    if (rc) return rc;
+    if (nonfinite) {
+      MGC_CUDA(cudaStreamSynchronize(st));
+      if (iters) *iters = steps;
+      if (relres) *relres = NAN;
+      return MGCCCS_ENONFINITE;
+    }
+    MGC_LAUNCH(launch_hess_solve(k, m, h->Hh, h->g, h->y, st));
+    MGC_CUDA(cudaMemsetAsync(h->e32, 0, sizeof(float2) * (size_t)N, st));
+    MGC_LAUNCH(launch_multiaxpy(N, k, (const float2*)h->Z32, N, h->y, 1.0, h->e32, (double*)nullptr, nb,
+                                (const int*)nullptr, st));
+    MGC_LAUNCH(launch_promote_add(N, h->e32, h->norm_out, u, st));
   }
   if (iters) *iters = steps;
   if (relres) *relres = rr;
@@ -553,6 +758,7 @@ int solve_impl(mgcccs_handle* h, cplx* u, const cplx* f, double rtol, int max_it
     if (relres) *relres = 0.0;
     return MGCCCS_OK;
   }
+  if (h->km > 0 && h->mixed) return gmres_ir_impl(h, u, f, std::sqrt(fn2), rtol, max_iter, iters, relres, history);
   if (h->km > 0) return gmres_impl(h, u, f, std::sqrt(fn2), rtol, max_iter, iters, relres, history);
   double rr = INFINITY;
   int it = 0;
@@ -654,7 +860,14 @@ int mgcccs_solve_host(mgcccs_t h, mgcccs_c128* u_host, const mgcccs_c128* f_host
 
 int mgcccs_precond_apply(mgcccs_t h, mgcccs_c128* z, const mgcccs_c128* r) {
   if (!h || !z || !r || (const void*)z == (const void*)r) return MGCCCS_EINVAL;
-  return precond(h, reinterpret_cast<cplx*>(z), reinterpret_cast<const cplx*>(r));
+  if (!h->mixed) return precond(h, reinterpret_cast<cplx*>(z), reinterpret_cast<const cplx*>(r));
+  // mixed handle: the complex64 preconditioner between a rounding and a widening
+  const long long N = (long long)h->lv[0].mx * h->lv[0].my;
+  MGC_LAUNCH(launch_demote(N, reinterpret_cast<const cplx*>(r), nullptr, h->V32, h->st));
+  int rc = precond<float2>(h, h->Z32, h->V32);
+  if (rc) return rc;
+  MGC_LAUNCH(launch_promote(N, h->Z32, reinterpret_cast<cplx*>(z), h->st));
+  return MGCCCS_OK;
 }
 
 int mgcccs_matvec(mgcccs_t h, const mgcccs_c128* x, mgcccs_c128* y) {
@@ -727,6 +940,27 @@ int mgcccs_get_bound_states(mgcccs_t h, mgcccs_c128* lambda, mgcccs_c128* phi, m
   return MGCCCS_OK;
 }
 
+int mgcccs_weighted_dot(mgcccs_t h, const mgcccs_c128* a, const mgcccs_c128* b, const mgcccs_c128* d,
+                        mgcccs_c128 scale, mgcccs_c128* out) {
+  if (!h || !a || !b || !out) return MGCCCS_EINVAL;
+  const LevelBufs& l0 = h->lv[0];
+  MGC_LAUNCH(launch_weighted_dot(l0.mx, l0.my, l0.w_x, l0.w_y, reinterpret_cast<const cplx*>(a),
+                                 reinterpret_cast<const cplx*>(b), reinterpret_cast<const cplx*>(d),
+                                 cmk(scale.re, scale.im), h->wdot_part, reinterpret_cast<cplx*>(out), h->st));
+  h->launches++;   // two kernels
+  return MGCCCS_OK;
+}
+
+int mgcccs_weighted_product(mgcccs_t h, const mgcccs_c128* a, const mgcccs_c128* b, mgcccs_c128 scale,
+                            mgcccs_c128* out) {
+  if (!h || !a || !b || !out) return MGCCCS_EINVAL;
+  const LevelBufs& l0 = h->lv[0];
+  MGC_LAUNCH(launch_weighted_product(l0.mx, l0.my, l0.w_x, l0.w_y, reinterpret_cast<const cplx*>(a),
+                                     reinterpret_cast<const cplx*>(b), cmk(scale.re, scale.im),
+                                     reinterpret_cast<cplx*>(out), h->st));
+  return MGCCCS_OK;
+}
+
 long long mgcccs_launch_count(mgcccs_t h) { return h ? h->launches : -1; }
 
 const char* mgcccs_strerror(int code) {
@@ -744,8 +978,10 @@ const char* mgcccs_strerror(int code) {
 
 void mgcccs_destroy(mgcccs_t h) {
   if (!h) return;
-  for (int j = 0; j < MGC_MAX_RESTART; ++j)
+  for (int j = 0; j < MGC_MAX_RESTART; ++j) {
     if (h->step_exec[j]) cudaGraphExecDestroy(h->step_exec[j]);
+    if (h->step_exec32[j]) cudaGraphExecDestroy(h->step_exec32[j]);
+  }
   for (int q = 0; q < 2; ++q)
     if (h->ev[q]) cudaEventDestroy(h->ev[q]);
   if (h->cap_st) cudaStreamDestroy(h->cap_st);

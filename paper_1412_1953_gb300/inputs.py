@@ -122,3 +122,22 @@ def free_problem(n: int, L: float, R0: float, theta: float, E: float, f: np.ndar
     return Problem(n, n, L, L, R0, R0, theta, E, z0, z0.copy(),
                    np.zeros((n - 1, n - 1), dtype=np.complex128),
                    np.ascontiguousarray(f, dtype=np.complex128), name=f"free{n}")
+
+
+def tp_charge_derivative(n: int, L: float = 30.0, R0: float = 20.0, theta: float = math.pi / 6,
+                         ny: int | None = None) -> np.ndarray:
+    """d(V1 + V2)/dZ = -1/x - 1/y at the interior complex nodes, [j][i] (Temkin-Poet)."""
+    ny = n if ny is None else ny
+    _, zx = node_coordinates(n, L, R0, theta)
+    _, zy = node_coordinates(ny, L, R0, theta)
+    ZX, ZY = np.meshgrid(zx[1:-1], zy[1:-1])
+    return np.ascontiguousarray(-(1.0 / ZX + 1.0 / ZY), dtype=np.complex128)
+
+
+def gaussian_window(n: int, L: float, cx: float, cy: float, sigma: float, ny: int | None = None) -> np.ndarray:
+    """g(x, y) = exp(-((x-cx)^2 + (y-cy)^2) / (2 sigma^2)) at the interior real nodes, [j][i]."""
+    ny = n if ny is None else ny
+    x = np.arange(1, n) * (L / n)
+    y = np.arange(1, ny) * (L / ny)
+    X, Y = np.meshgrid(x, y)
+    return np.ascontiguousarray(np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2.0 * sigma ** 2)), dtype=np.complex128)

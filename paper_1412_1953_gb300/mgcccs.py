@@ -29,6 +29,10 @@ class MGCCCSError(RuntimeError):
         super().__init__(f"{where}: {mgcccs_strerror(code)} (code {code})")
 
 
+class mgcccs_c128(ctypes.Structure):
+    _fields_ = [("re", ctypes.c_double), ("im", ctypes.c_double)]
+
+
 class mgcccs_params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("Lx", ctypes.c_double), ("Ly", ctypes.c_double),
@@ -36,7 +40,8 @@ class mgcccs_params(ctypes.Structure):
                 ("theta", ctypes.c_double), ("E", ctypes.c_double),
                 ("levels", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("omega", ctypes.c_double), ("n_b", ctypes.c_int),
-                ("coarse_gamma", ctypes.c_double), ("krylov_restart", ctypes.c_int)]
+                ("coarse_gamma", ctypes.c_double), ("krylov_restart", ctypes.c_int),
+                ("precision", ctypes.c_int), ("inner_rtol", ctypes.c_double)]
 
 
 COARSE_GAMMA_DEFAULT = 14.6 * math.pi / 180.0
@@ -56,6 +61,8 @@ _SIGS = {
     "mgcccs_precond_apply": (_i, [_vp, _vp, _vp]),
     "mgcccs_residual": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(_d)]),
     "mgcccs_matvec": (_i, [_vp, _vp, _vp]),
+    "mgcccs_weighted_dot": (_i, [_vp, _vp, _vp, _vp, mgcccs_c128, _vp]),
+    "mgcccs_weighted_product": (_i, [_vp, _vp, _vp, mgcccs_c128, _vp]),
     "mgcccs_smooth": (_i, [_vp, _i, _vp, _vp, _i]),
     "mgcccs_level_residual": (_i, [_vp, _i, _vp, _vp, _vp]),
     "mgcccs_restrict": (_i, [_vp, _i, _vp, _vp]),
@@ -119,10 +126,11 @@ def mgcccs_norm2_noalloc(v, out, stream=None):
 
 
 def make_params(nx, ny, Lx, Ly, R0x, R0y, theta, E, levels=5, nu1=1, nu2=1, omega=2.0 / 3.0, n_b=3,
-                coarse_gamma=COARSE_GAMMA_DEFAULT, krylov_restart=0) -> mgcccs_params:
+                coarse_gamma=COARSE_GAMMA_DEFAULT, krylov_restart=0, precision=0,
+                inner_rtol=0.0) -> mgcccs_params:
     return mgcccs_params(int(nx), int(ny), float(Lx), float(Ly), float(R0x), float(R0y), float(theta),
                          float(E), int(levels), int(nu1), int(nu2), float(omega), int(n_b), float(coarse_gamma),
-                         int(krylov_restart))
+                         int(krylov_restart), int(precision), float(inner_rtol))
 
 
 def params_for(prob, **kw) -> mgcccs_params:
@@ -230,6 +238,18 @@ class Solver:
 
     def matvec(self, x, y):
         _check(lib().mgcccs_matvec(self.h, self._f(x, "x"), self._f(y, "y")), "mgcccs_matvec")
+
+    def weighted_dot(self, a, b, out, d=None, scale=1.0):
+        """out[0] = scale * sum_k w_k a_k b_k (d_k); out is a complex128 CUDA tensor."""
+        sc = mgcccs_c128(complex(scale).real, complex(scale).imag)
+        _check(lib().mgcccs_weighted_dot(self.h, self._f(a, "a"), self._f(b, "b"),
+                                         self._f(d, "d") if d is not None else None, sc,
+                                         _ptr(_dev_c128(out, out.numel(), "out"))), "mgcccs_weighted_dot")
+
+    def weighted_product(self, a, b, out, scale=1.0):
+        sc = mgcccs_c128(complex(scale).real, complex(scale).imag)
+        _check(lib().mgcccs_weighted_product(self.h, self._f(a, "a"), self._f(b, "b"), sc, self._f(out, "out")),
+               "mgcccs_weighted_product")
 
     # -- single steps
     def level_size(self, level: int) -> int:

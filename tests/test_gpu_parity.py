@@ -94,10 +94,10 @@ def test_coarse_solve_matches_dense_solve():
     assert rel(host(ud), ref) <= 1e-12
 
 
-@pytest.mark.parametrize("n,nb", [(64, 3), (128, 3), (128, 6)])
+@pytest.mark.parametrize("n,nb", [(64, 3), (128, 3), (128, 6), (512, 6)])
 def test_bound_states_match_oracle(n, nb):
     prob = tp_small(n) if n == 64 else inputs.temkin_poet(n)
-    so, sg = pair(prob, 3, nb)
+    so, sg = pair(prob, 3 if n <= 128 else n.bit_length() - 4, nb)
     lam, phi, mu, vphi = sg.bound_states()
     np.testing.assert_allclose(lam, so.ch.lam, rtol=0, atol=1e-12 * np.abs(so.ch.lam).max())
     np.testing.assert_allclose(mu, so.ch.mu, rtol=0, atol=1e-12 * np.abs(so.ch.mu).max())

@@ -442,3 +442,45 @@ def test_gmres_accelerates_mgcccs_on_tp_workload():
     s = O.Solver(O.params_from_problem(prob, levels=5, n_b=3), prob.v1, prob.v2, prob.v12)
     u, hist, rr = O.gmres(s, prob.f, m=20, rtol=1e-10, max_iter=300)
     assert rr <= 1e-10 and len(hist) <= 150
+
+
+# ------------------------------------------------------------------ adjoint gradients
+
+def _tp_direct(n, E, Z, dV):
+    L = 30.0 * n / 128
+    prob = inputs.temkin_poet(n, L=L, R0=2 * L / 3, theta=math.pi / 6, E=E, Z=Z, seed=4)
+    prob.v12 = prob.v12 + dV
+    lev = O.build_levels(O.params_from_problem(prob, levels=1, n_b=0), prob.v1, prob.v2, prob.v12)[0]
+    return prob, lev
+
+
+def test_adjoint_gradients_match_central_differences():
+    """dJ/dE, dJ/dZ and dJ/ddV_k from one adjoint solve equal central differences
+    (step 1e-6) of J computed with exact (LU) forward solves; f held fixed."""
+    n, E, Z = 24, 0.5, 1.0
+    dV = np.zeros((n - 1, n - 1), dtype=np.complex128)
+    prob, lev = _tp_direct(n, E, Z, dV)
+    f = prob.f
+    x = np.arange(1, n) * prob.Lx / n
+    g = np.exp(-((x[None, :] - 3.0) ** 2 + (x[:, None] - 3.0) ** 2) / 8.0).astype(np.complex128)
+    u = O.direct_solve(lev, f)
+    mu = O.direct_solve(lev, g)
+    zx = lev.ax.z[1:-1]
+    dAdZ = -(1.0 / zx[None, :] + 1.0 / zx[:, None])
+    dE, dZ, ddV = O.adjoint_gradients(lev, u, mu, dAdZ)
+
+    def J(E_, Z_, dV_):
+        p_, l_ = _tp_direct(n, E_, Z_, dV_)
+        return O.amplitude(l_, g, O.direct_solve(l_, f))
+    h = 1e-6
+    fdE = (J(E + h, Z, dV) - J(E - h, Z, dV)) / (2 * h)
+    fdZ = (J(E, Z + h, dV) - J(E, Z - h, dV)) / (2 * h)
+    assert abs(dE - fdE) <= 1e-6 * abs(fdE)
+    assert abs(dZ - fdZ) <= 1e-6 * abs(fdZ)
+    # a single-node derivative is ~1e-4 of J, so the difference quotient carries the
+    # relative rounding of J (about cond * eps) amplified by |J| / (2 h |dJ|): 1e-4 bound
+    for (j, i) in [(3, 4), (10, 2), (20, 21)]:
+        e = np.zeros_like(dV)
+        e[j, i] = h
+        fd = (J(E, Z, dV + e) - J(E, Z, dV - e)) / (2 * h)
+        assert abs(ddV[j, i] - fd) <= 1e-4 * abs(fd)
