@@ -329,7 +329,7 @@ def run_sweep(args):
                 for kr in (0, 20):
                     try:
                         sv = M.Solver(M.params_for(prob, levels=lv, n_b=nb, krylov_restart=kr), prob.v1, prob.v2,
-                                      prob.v12)
+                                      prob.v12, reuse_states=True)
                     except M.MGCCCSError as exc:
                         print(json.dumps({"mode": "sweep", "n": n, "E": E, "n_b": nb, "krylov": kr,
                                           "error": str(exc)}), flush=True)

@@ -110,6 +110,17 @@ int mgcccs_setup(mgcccs_t* out, const mgcccs_params* p,
                  const mgcccs_c128* v1, const mgcccs_c128* v2, const mgcccs_c128* v12,
                  void* workspace, size_t workspace_bytes, void* stream);
 
+/* mgcccs_setup with the bound states supplied instead of computed: lambda, mu are
+ * host arrays of n_b eigenvalues, phi, vphi device arrays [n_b][nx-1], [n_b][ny-1]
+ * as returned by mgcccs_get_bound_states of a handle with the same grid, ECS
+ * contour, V1 and V2 (the states do not depend on E or V12).  Lets energy sweeps and
+ * batches skip the eigen-solve.  Same conventions and errors as mgcccs_setup. */
+int mgcccs_setup_with_states(mgcccs_t* out, const mgcccs_params* p,
+                             const mgcccs_c128* v1, const mgcccs_c128* v2, const mgcccs_c128* v12,
+                             const mgcccs_c128* lambda, const mgcccs_c128* phi,
+                             const mgcccs_c128* mu, const mgcccs_c128* vphi,
+                             void* workspace, size_t workspace_bytes, void* stream);
+
 /* One V(nu1,nu2)-cycle on the fine level, u updated in place (Sec. 3.2).
  * u, f: device, (nx-1)*(ny-1).  Async. */
 int mgcccs_vcycle(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f);

@@ -279,7 +279,8 @@ int read_status(mgcccs_handle* h) {
   return MGCCCS_OK;
 }
 
-int do_setup(mgcccs_handle* h, const cplx* v1, const cplx* v2, const cplx* v12) {
+int do_setup(mgcccs_handle* h, const cplx* v1, const cplx* v2, const cplx* v12, const cplx* lam_in = nullptr,
+             const cplx* phi_in = nullptr, const cplx* mu_in = nullptr, const cplx* vphi_in = nullptr) {
   const mgcccs_params& p = h->p;
   cudaStream_t st = h->st;
   MGC_CUDA(cudaMemsetAsync(h->status, 0, 4 * sizeof(int), st));
@@ -328,24 +329,32 @@ int do_setup(mgcccs_handle* h, const cplx* v1, const cplx* v2, const cplx* v12) 
   if (h->nb > 0) {
     const LevelBufs& b = h->lv[0];
     const int nb = h->nb;
-    MGC_LAUNCH(launch_bound_states(b.mx, b.west_x, b.east_x, b.diag_x, v1, b.w_x, nb, h->lam, h->phi,
-                                   h->eig_scratch, h->status, st));
-    // the y eigenproblem is the x one when both axes and potentials coincide (square TP grids)
-    bool same = p.nx == p.ny && p.Lx == p.Ly && p.R0x == p.R0y;
-    if (same) {
-      int differs = 0;
-      MGC_CUDA(cudaMemsetAsync(h->status + 3, 0, sizeof(int), st));
-      MGC_LAUNCH(launch_compare(b.mx, v1, v2, h->status + 3, st));
-      MGC_CUDA(cudaMemcpyAsync(&differs, h->status + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
-      MGC_CUDA(cudaStreamSynchronize(st));
-      same = differs == 0;
-    }
-    if (same) {
-      MGC_CUDA(cudaMemcpyAsync(h->mu, h->lam, sizeof(cplx) * nb, cudaMemcpyDeviceToDevice, st));
-      MGC_CUDA(cudaMemcpyAsync(h->vphi, h->phi, sizeof(cplx) * nb * b.mx, cudaMemcpyDeviceToDevice, st));
+    if (lam_in) {
+      // states supplied by the caller (a previous setup on the same grid and V1, V2)
+      MGC_CUDA(cudaMemcpyAsync(h->lam, lam_in, sizeof(cplx) * nb, cudaMemcpyHostToDevice, st));
+      MGC_CUDA(cudaMemcpyAsync(h->mu, mu_in, sizeof(cplx) * nb, cudaMemcpyHostToDevice, st));
+      MGC_CUDA(cudaMemcpyAsync(h->phi, phi_in, sizeof(cplx) * nb * b.mx, cudaMemcpyDeviceToDevice, st));
+      MGC_CUDA(cudaMemcpyAsync(h->vphi, vphi_in, sizeof(cplx) * nb * b.my, cudaMemcpyDeviceToDevice, st));
     } else {
-      MGC_LAUNCH(launch_bound_states(b.my, b.west_y, b.east_y, b.diag_y, v2, b.w_y, nb, h->mu, h->vphi,
+      MGC_LAUNCH(launch_bound_states(b.mx, b.west_x, b.east_x, b.diag_x, v1, b.w_x, nb, h->lam, h->phi,
                                      h->eig_scratch, h->status, st));
+      // the y eigenproblem is the x one when both axes and potentials coincide (square TP grids)
+      bool same = p.nx == p.ny && p.Lx == p.Ly && p.R0x == p.R0y;
+      if (same) {
+        int differs = 0;
+        MGC_CUDA(cudaMemsetAsync(h->status + 3, 0, sizeof(int), st));
+        MGC_LAUNCH(launch_compare(b.mx, v1, v2, h->status + 3, st));
+        MGC_CUDA(cudaMemcpyAsync(&differs, h->status + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MGC_CUDA(cudaStreamSynchronize(st));
+        same = differs == 0;
+      }
+      if (same) {
+        MGC_CUDA(cudaMemcpyAsync(h->mu, h->lam, sizeof(cplx) * nb, cudaMemcpyDeviceToDevice, st));
+        MGC_CUDA(cudaMemcpyAsync(h->vphi, h->phi, sizeof(cplx) * nb * b.mx, cudaMemcpyDeviceToDevice, st));
+      } else {
+        MGC_LAUNCH(launch_bound_states(b.my, b.west_y, b.east_y, b.diag_y, v2, b.w_y, nb, h->mu, h->vphi,
+                                       h->eig_scratch, h->status, st));
+      }
     }
     MGC_LAUNCH(launch_weight_states(b.mx, nb, b.w_x, h->phi, h->wphi, st));
     MGC_LAUNCH(launch_weight_states(b.my, nb, b.w_y, h->vphi, h->wvphi, st));
@@ -819,6 +828,36 @@ int mgcccs_setup(mgcccs_t* out, const mgcccs_params* p, const mgcccs_c128* v1, c
   layout(h, cv);
   int rc = do_setup(h, reinterpret_cast<const cplx*>(v1), reinterpret_cast<const cplx*>(v2),
                     reinterpret_cast<const cplx*>(v12));
+  if (!rc && h->km > 0) rc = create_krylov_objects(h);
+  if (rc) {
+    mgcccs_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return MGCCCS_OK;
+}
+
+int mgcccs_setup_with_states(mgcccs_t* out, const mgcccs_params* p, const mgcccs_c128* v1, const mgcccs_c128* v2,
+                             const mgcccs_c128* v12, const mgcccs_c128* lambda, const mgcccs_c128* phi,
+                             const mgcccs_c128* mu, const mgcccs_c128* vphi, void* workspace, size_t workspace_bytes,
+                             void* stream) {
+  if (!out || !valid_params(p) || !v1 || !v2 || !v12 || !workspace) return MGCCCS_EINVAL;
+  if (p->n_b > 0 && (!lambda || !phi || !mu || !vphi)) return MGCCCS_EINVAL;
+  *out = nullptr;
+  size_t need = mgcccs_workspace_size(p);
+  if (workspace_bytes < need) return MGCCCS_ENOSPACE;
+  if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return MGCCCS_EINVAL;
+  mgcccs_handle* h = new (std::nothrow) mgcccs_handle();
+  if (!h) return MGCCCS_EINVAL;
+  h->p = *p;
+  h->L = p->levels;
+  h->st = reinterpret_cast<cudaStream_t>(stream);
+  Carver cv{reinterpret_cast<char*>(workspace)};
+  layout(h, cv);
+  int rc = do_setup(h, reinterpret_cast<const cplx*>(v1), reinterpret_cast<const cplx*>(v2),
+                    reinterpret_cast<const cplx*>(v12), reinterpret_cast<const cplx*>(lambda),
+                    reinterpret_cast<const cplx*>(phi), reinterpret_cast<const cplx*>(mu),
+                    reinterpret_cast<const cplx*>(vphi));
   if (!rc && h->km > 0) rc = create_krylov_objects(h);
   if (rc) {
     mgcccs_destroy(h);

@@ -54,6 +54,8 @@ _SIGS = {
     "mgcccs_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(mgcccs_params)]),
     "mgcccs_setup": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(mgcccs_params), _vp, _vp, _vp, _vp,
                           ctypes.c_size_t, _vp]),
+    "mgcccs_setup_with_states": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(mgcccs_params), _vp, _vp, _vp,
+                                      _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "mgcccs_vcycle": (_i, [_vp, _vp, _vp]),
     "mgcccs_cccs": (_i, [_vp, _vp, _vp]),
     "mgcccs_solve": (_i, [_vp, _vp, _vp, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d), _vp]),
@@ -154,11 +156,27 @@ def _dev_c128(t, n: int, name: str):
     return t
 
 
+# Bound states by (grid, contour, n_b, V1, V2): they do not depend on E or V12, so a
+# handle for another energy on the same grid reuses them (mgcccs_setup_with_states).
+_STATE_CACHE: dict = {}
+
+
+def _state_key(p: mgcccs_params, v1, v2):
+    import hashlib
+    h = hashlib.sha1()
+    for a in (v1, v2):
+        arr = a.detach().cpu().numpy() if hasattr(a, "detach") else np.asarray(a)
+        h.update(np.ascontiguousarray(arr, dtype=np.complex128).tobytes())
+    return (p.nx, p.ny, p.Lx, p.Ly, p.R0x, p.R0y, p.theta, p.n_b, h.hexdigest())
+
+
 class Solver:
     """A setup handle plus its workspace.  u, f, r, z are complex128 CUDA tensors of
-    shape (ny-1, nx-1) (or any contiguous shape with that many elements)."""
+    shape (ny-1, nx-1) (or any contiguous shape with that many elements).  With
+    reuse_states, bound states of an earlier handle on the same grid and V1, V2 are
+    supplied to the setup instead of being recomputed."""
 
-    def __init__(self, p: mgcccs_params, v1, v2, v12, stream=None):
+    def __init__(self, p: mgcccs_params, v1, v2, v12, stream=None, reuse_states=False):
         import torch
         self.p = p
         self.mx, self.my = p.nx - 1, p.ny - 1
@@ -176,9 +194,20 @@ class Solver:
         self._ws_ptr = (base + 255) // 256 * 256
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
         h = ctypes.c_void_p()
-        _check(lib().mgcccs_setup(ctypes.byref(h), ctypes.byref(p), _ptr(v1d), _ptr(v2d), _ptr(v12d),
-                                  self._ws_ptr, nbytes, self.stream.cuda_stream), "mgcccs_setup")
+        key = _state_key(p, v1, v2) if (reuse_states and p.n_b > 0) else None
+        cached = _STATE_CACHE.get(key) if key is not None else None
+        if cached is not None:
+            lam, phi, mu, vphi = cached
+            _check(lib().mgcccs_setup_with_states(ctypes.byref(h), ctypes.byref(p), _ptr(v1d), _ptr(v2d),
+                                                  _ptr(v12d), lam.ctypes.data, phi.data_ptr(), mu.ctypes.data,
+                                                  vphi.data_ptr(), self._ws_ptr, nbytes, self.stream.cuda_stream),
+                   "mgcccs_setup_with_states")
+        else:
+            _check(lib().mgcccs_setup(ctypes.byref(h), ctypes.byref(p), _ptr(v1d), _ptr(v2d), _ptr(v12d),
+                                      self._ws_ptr, nbytes, self.stream.cuda_stream), "mgcccs_setup")
         self.h = h
+        if key is not None and cached is None:
+            _STATE_CACHE[key] = self.bound_states()
 
     # -- lifecycle
     def close(self):

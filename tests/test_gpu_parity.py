@@ -167,6 +167,25 @@ def test_solve_128_to_1e10_matches_oracle():
     assert np.linalg.norm(u - uo) <= 1e-8 * np.linalg.norm(uo)
 
 
+def test_setup_with_cached_states_reproduces_solve():
+    """A second handle on the same grid and V1, V2 at another energy reuses the bound
+    states (mgcccs_setup_with_states); its solve is bit-identical to a fresh setup's."""
+    p1 = tp_small(64, E=0.5, seed=3)
+    p2 = tp_small(64, E=0.9, seed=3)
+    M._STATE_CACHE.clear()
+    s1 = M.Solver(M.params_for(p1, levels=4, n_b=3, krylov_restart=20), p1.v1, p1.v2, p1.v12, reuse_states=True)
+    assert len(M._STATE_CACHE) == 1
+    s2 = M.Solver(M.params_for(p2, levels=4, n_b=3, krylov_restart=20), p2.v1, p2.v2, p2.v12, reuse_states=True)
+    s3 = M.Solver(M.params_for(p2, levels=4, n_b=3, krylov_restart=20), p2.v1, p2.v2, p2.v12)
+    f = dev(p2.f)
+    u2, u3 = torch.zeros_like(f), torch.zeros_like(f)
+    its2, _ = s2.solve(u2, f, rtol=1e-10, max_iter=400)
+    its3, _ = s3.solve(u3, f, rtol=1e-10, max_iter=400)
+    assert its2 == its3
+    assert torch.equal(u2, u3)
+    M._STATE_CACHE.clear()
+
+
 def test_solve_host_matches_device_solve():
     prob = tp_small(64, seed=6)
     _, sg = pair(prob, 4, 3)
