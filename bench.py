@@ -54,11 +54,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--box", type=float, default=30.0, help="box length L of [0,L]^2")
     ap.add_argument("--R0", type=float, default=20.0, help="ECS start")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
-    ap.add_argument("--mode", choices=["bench", "solve-only", "kernel", "adjoint", "sweep", "precision"],
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default=None,
+                    help="default: fp64 (mixed for --mode batch)")
+    ap.add_argument("--mode", choices=["bench", "solve-only", "kernel", "adjoint", "sweep", "precision", "batch"],
                     default="bench",
                     help="solve-only: setup + warm-up + timed solves, nothing else (for launch lists); "
                          "kernel: setup + 6 launches of one kernel (for ncu captures)")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--autotune", action="store_true", help="batch: tune (levels, nu1, nu2) per grid size")
     ap.add_argument("--kernel", choices=["jacobi", "residual_project", "multidot"], default="jacobi")
     return ap.parse_args()
 
@@ -392,6 +395,89 @@ def run_precision(args):
                       "speedup": res["fp64"]["seconds"] / res["mixed"]["seconds"]}), flush=True)
 
 
+def run_batch(args):
+    """Batching form: 64 energies in [0.1, 2.0] on grids n in {256, ..., 1024} (drawn with
+    seed 1; L = 30 n / 512, ECS beyond 2L/3), mixed precision, n_b = 3, autotuned
+    (levels, nu1, nu2) per grid size.  Times the batch graph (one launch solves all 64)
+    and, beside it, the host lock-step driver and one-at-a-time solves of a sample.
+    Reports solves/s, unknowns/s, setup time per energy and every problem's iterations
+    and relative residual."""
+    import torch
+    from paper_1412_1953_gb300 import batch as BT
+    from paper_1412_1953_gb300 import build as B
+    from paper_1412_1953_gb300 import inputs
+    from paper_1412_1953_gb300 import mgcccs as M
+    B.build()
+    prec = 0 if args.precision == "fp64" else 1
+    problems = inputs.batching_problems(count=args.batch_count)
+    sizes = sorted({p.nx for p in problems})
+    t0 = time.perf_counter()
+    sched = {n: (BT.autotune(n, precision=prec, E=1.0, n_b=args.nb) if args.autotune else BT.default_schedule(n))
+             for n in sizes}
+    t_tune = time.perf_counter() - t0
+    M._STATE_CACHE.clear()          # setup time below includes one bound-state solve per grid size
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bs = BT.BatchSolver(problems, sched, n_b=args.nb, precision=prec)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    graph = bs.graph()
+    t_graph = time.perf_counter() - t0
+
+    def timed(run):
+        out = []
+        for _ in range(max(1, args.steps)):
+            for u in bs.u:
+                u.zero_()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            res = run()
+            torch.cuda.synchronize()
+            out.append(time.perf_counter() - t)
+        return statistics.median(out), res
+
+    for _ in range(max(1, args.warmup)):
+        for u in bs.u:
+            u.zero_()
+        graph.run(rtol=args.rtol, max_iter=args.max_iter)
+    sec, (its, rr, st) = timed(lambda: graph.run(rtol=args.rtol, max_iter=args.max_iter))
+    u_graph = [u.clone() for u in bs.u]
+    bs.solve(rtol=args.rtol, max_iter=5)              # capture the per-step graphs of the host driver
+    sec_ls, (its_ls, _, _) = timed(lambda: bs.solve(rtol=args.rtol, max_iter=args.max_iter, zero=False))
+    same_ls = its_ls == its and all(torch.equal(a, b) for a, b in zip(u_graph, bs.u))
+    sample = list(range(0, len(problems), max(1, len(problems) // 8)))
+    t_single, same = 0.0, True
+    for k in sample:
+        u1 = torch.zeros_like(bs.f[k])
+        bs.solvers[k].solve(u1, bs.f[k], rtol=args.rtol, max_iter=5, raise_on_notconv=False)
+        u1.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        k1, r1 = bs.solvers[k].solve(u1, bs.f[k], rtol=args.rtol, max_iter=args.max_iter, raise_on_notconv=False)
+        torch.cuda.synchronize()
+        t_single += time.perf_counter() - t
+        same = same and k1 == its[k] and bool(torch.equal(u1, u_graph[k]))
+    t_single_unknowns = sum(problems[k].n_unknowns for k in sample)
+    out = {"mode": "batch", "workload": f"tp_ecs_batch{len(problems)}", "problems": len(problems),
+           "grid_sizes": sizes, "precision": "complex64 inner cycles in FP64 refinement" if prec else "complex128",
+           "n_b": args.nb, "rtol": args.rtol,
+           "solves_per_s": len(problems) / sec, "unknowns_per_s": bs.unknowns / sec, "seconds": sec,
+           "all_converged": all(s == 0 for s in st), "max_relres": max(rr), "total_steps": sum(its),
+           "lockstep_host_driver": {"seconds": sec_ls, "solves_per_s": len(problems) / sec_ls,
+                                    "identical_to_graph": same_ls},
+           "one_at_a_time_sample": {"problems": sample, "unknowns_per_s": t_single_unknowns / t_single,
+                                    "identical_to_graph": same},
+           "schedules": {str(n): {k: sched[n][k] for k in ("levels", "nu1", "nu2")} for n in sizes},
+           "autotune_seconds": t_tune, "setup_seconds": t_setup, "graph_build_seconds": t_graph,
+           "solves_per_s_with_setup": len(problems) / (sec + t_setup),
+           "per_problem": [{"n": p.nx, "E": round(p.E, 6), "iterations": k, "relres": r}
+                           for p, k, r in zip(problems, its, rr)]}
+    print(json.dumps(out), flush=True)
+    graph.close()
+    bs.close()
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -577,6 +663,8 @@ def main():
         run_sweep(args)
     elif args.mode == "precision":
         run_precision(args)
+    elif args.mode == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

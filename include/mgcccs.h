@@ -41,6 +41,7 @@ extern "C" {
 
 typedef struct { double re, im; } mgcccs_c128;
 typedef struct mgcccs_handle* mgcccs_t;
+typedef struct mgcccs_batch* mgcccs_batch_t;
 
 enum {
   MGCCCS_OK = 0,
@@ -144,7 +145,14 @@ int mgcccs_cccs(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f);
  * doubles receiving the relative residual (GMRES: its least-squares estimate)
  * after each iteration, may be NULL.  Synchronous.  Returns ENOTCONV when
  * max_iter is reached (u, relres valid), ENONFINITE if the residual is not
- * finite. */
+ * finite.
+ * GMRES solves without history run device-driven by default: the whole solve is
+ * one CUDA graph whose conditional nodes (while / if / switch) carry the restart
+ * loop, the Arnoldi loop and the stop tests, so the host launches it once and
+ * waits once.  The graph is built on the first call for a given (u, f) pair of
+ * pointers and replayed while they stay the same.  With history, or after
+ * mgcccs_set_solve_driver(h, MGCCCS_DRIVER_HOST), the host drives the cycles
+ * (one replayed graph per Arnoldi step; the same arithmetic in the same order). */
 int mgcccs_solve(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f, double rtol,
                  int max_iter, int* iters, double* relres, double* history);
 
@@ -153,6 +161,42 @@ int mgcccs_solve(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f, double rtol,
  * Synchronous. */
 int mgcccs_solve_host(mgcccs_t h, mgcccs_c128* u_host, const mgcccs_c128* f_host,
                       double rtol, int max_iter, int* iters, double* relres);
+
+/* Solve drivers for mgcccs_set_solve_driver. */
+enum { MGCCCS_DRIVER_GRAPH = 0, MGCCCS_DRIVER_HOST = 1 };
+int mgcccs_set_solve_driver(mgcccs_t h, int driver);
+
+/* Batched device-driven solves: one CUDA graph holding the device-driven solves of
+ * `count` problems (one handle each, krylov_restart >= 1, any mix of grids, energies
+ * and precisions) as independent branches, so that one launch runs them all
+ * concurrently.  u[k], f[k]: device arrays of problem k, fixed for the life of the
+ * batch (the graph holds the pointers).  stream: the stream that run() launches on.
+ * The batch uses the handles' buffers: run no other call on its handles while a
+ * batch runs, and destroy the batch before its handles.  EINVAL for a handle listed
+ * twice, a handle without GMRES, or NULL pointers; ECUDA if the graph cannot be
+ * built. */
+int mgcccs_batch_create(mgcccs_batch_t* out, mgcccs_t* handles, int count, mgcccs_c128* const* u,
+                        const mgcccs_c128* const* f, void* stream);
+/* One launch of the batch graph: every problem from its current u until
+ * ||f - (H-E)u|| / ||f|| <= rtol or max_iter Arnoldi steps.  iters, relres, status:
+ * host arrays of count entries, may be NULL (status[k]: OK, ENOTCONV or ENONFINITE).
+ * Synchronous.  Returns the worst status. */
+int mgcccs_batch_run(mgcccs_batch_t b, double rtol, int max_iter, int* iters, double* relres, int* status);
+void mgcccs_batch_destroy(mgcccs_batch_t b);
+
+/* Batched solve of `count` independent problems, one handle each (handles with
+ * krylov_restart >= 1, any mix of grids, energies and precisions; give every handle
+ * its own stream at setup so that their work overlaps).  GMRES cycles of all unfinished
+ * problems advance in lock-step: each cycle starts from the true residual, then the
+ * Arnoldi steps of all problems are launched round-robin (each a replayed CUDA graph on
+ * its handle's stream), and each problem keeps the first step whose residual estimate
+ * met its target.  A problem leaves the batch when ||f - (H-E)u|| / ||f|| <= rtol or
+ * after max_iter used steps.  u[k], f[k]: device arrays of problem k (u in/out).
+ * iters, relres, status: host arrays of count entries, may be NULL (status[k] is
+ * MGCCCS_OK, ENOTCONV or ENONFINITE).  Synchronous.  Returns the worst status, or
+ * EINVAL (a handle listed twice, a handle without GMRES, NULL pointers). */
+int mgcccs_batch_solve(mgcccs_t* handles, int count, mgcccs_c128* const* u, const mgcccs_c128* const* f,
+                       double rtol, int max_iter, int* iters, double* relres, int* status);
 
 /* Preconditioner application z = M^{-1} r (Sec. 6: one V-cycle, then the
  * CCCS when n_b > 0, from a zero initial guess).  z, r: device, distinct.

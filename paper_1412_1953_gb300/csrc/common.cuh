@@ -161,13 +161,33 @@ cudaError_t launch_multidot(long long n, int k, const C* V, long long ld, const 
 cudaError_t launch_reduce_dots(int nblk, int k, const cplx* partial, cplx* out, cplx* acc_into, cudaStream_t st);
 template <class C>
 cudaError_t launch_multiaxpy(long long n, int k, const C* V, long long ld, const cplx* coef, double sgn,
-                             C* w, double* norm_part, int nblk, const int* gate, cudaStream_t st);
+                             C* w, double* norm_part, int nblk, const int* gate, cudaStream_t st,
+                             const int* dk = nullptr);
 cudaError_t launch_dgks(const double* before, const double* after, int* gate, cudaStream_t st);
 template <class C>
 cudaError_t launch_scale_by_norm(long long n, const C* w, C* out, const double* norm2, cplx* store,
                                  int nblk, cudaStream_t st);
 cudaError_t launch_givens(int j, int m, cplx* H, cplx* cs, cplx* sn, cplx* g, double* est, cudaStream_t st);
-cudaError_t launch_hess_solve(int k, int m, const cplx* H, const cplx* g, cplx* y, cudaStream_t st);
+cudaError_t launch_hess_solve(int k, int m, const cplx* H, const cplx* g, cplx* y, cudaStream_t st,
+                              const int* dk = nullptr);
+
+// Control record of a device-driven GMRES solve (one per handle, in its workspace).
+// The host writes the inputs before each launch of the solve graph; the control kernels
+// keep the counters and the outcome.
+enum { SOLVECTL_RUNNING = 0, SOLVECTL_CONVERGED = 1, SOLVECTL_MAXITER = 2, SOLVECTL_NONFINITE = 3,
+       SOLVECTL_ZERO_RHS = 4 };
+struct SolveCtl {
+  double fn2;          // |f|^2, written inside the graph
+  double rtol, inner_rtol;
+  int max_iter, mixed, m, pad0;
+  int steps, k, j, cycles, outer, status;
+  double rr, scale, target;
+};
+cudaError_t launch_outer_control(SolveCtl* c, const double* rn2, cudaGraphConditionalHandle h_outer,
+                                 cudaGraphConditionalHandle h_cycle, cudaGraphConditionalHandle h_inner,
+                                 cudaGraphConditionalHandle h_switch, cudaStream_t st);
+cudaError_t launch_step_control(SolveCtl* c, const double* est, cudaGraphConditionalHandle h_inner,
+                                cudaGraphConditionalHandle h_switch, cudaStream_t st);
 cudaError_t launch_zero_c(int n, cplx* a, cudaStream_t st);
 
 // kernels_cccs.cu
@@ -245,6 +265,7 @@ cudaError_t launch_compare(int n, const cplx* a, const cplx* b, int* flag, cudaS
 cudaError_t launch_setup_diag(int mx, int my, int stride, int fine_mx, const cplx* dx, const cplx* dy,
                               const cplx* v1, const cplx* v2, const cplx* v12, double E, double omega,
                               cplx* D, cplx* Dinv, int* status, cudaStream_t st);
+size_t coarse_inverse_scratch(int nc);                       // complex entries of aug
 cudaError_t launch_coarse_inverse(const StencilView& s, cplx* aug, cplx* Ainv, int* status, cudaStream_t st);
 cudaError_t launch_bound_states(int m, const cplx* west, const cplx* east, const cplx* diag, const cplx* v,
                                 const cplx* w, int nb, cplx* lam, cplx* phi, cplx* scratch, int* status,

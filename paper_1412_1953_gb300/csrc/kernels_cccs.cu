@@ -97,23 +97,31 @@ __global__ void __launch_bounds__(TX * WY) k_residual_project(StencilViewT<C> s,
   }
 }
 
-// Sum the per-tile partials in tile order (in FP64 for either partial type).
+// Sum the per-tile partials (in FP64 for either partial type): eight lanes per output
+// each sum a strided subset of tiles, then a fixed shuffle tree adds the eight.
 template <class C>
 __global__ void __launch_bounds__(256) k_reduce_partials(int nb, int mx, int my, int ntx, int nty,
                                                          const C* __restrict__ Px_part,
                                                          const C* __restrict__ Py_part,
                                                          cplx* __restrict__ Px, cplx* __restrict__ Py) {
-  const int t = blockIdx.x * 256 + threadIdx.x;
+  const int g = blockIdx.x * 256 + threadIdx.x;
+  const int t = g >> 3, sub = g & 7;
   const int nx_tot = nb * my, ny_tot = nb * mx;
+  cplx acc = cmk(0.0, 0.0);
   if (t < nx_tot) {
-    cplx acc = cmk(0.0, 0.0);
-    for (int k = 0; k < ntx; ++k) acc = cadd(acc, to_c128(Px_part[(size_t)k * nx_tot + t]));
-    Px[t] = acc;
+    for (int k = sub; k < ntx; k += 8) acc = cadd(acc, to_c128(Px_part[(size_t)k * nx_tot + t]));
   } else if (t < nx_tot + ny_tot) {
     const int q = t - nx_tot;
-    cplx acc = cmk(0.0, 0.0);
-    for (int k = 0; k < nty; ++k) acc = cadd(acc, to_c128(Py_part[(size_t)k * ny_tot + q]));
-    Py[q] = acc;
+    for (int k = sub; k < nty; k += 8) acc = cadd(acc, to_c128(Py_part[(size_t)k * ny_tot + q]));
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    acc.x += __shfl_down_sync(0xffffffffu, acc.x, o, 8);
+    acc.y += __shfl_down_sync(0xffffffffu, acc.y, o, 8);
+  }
+  if (sub == 0) {
+    if (t < nx_tot) Px[t] = acc;
+    else if (t < nx_tot + ny_tot) Py[t - nx_tot] = acc;
   }
 }
 
@@ -161,18 +169,31 @@ __global__ void __launch_bounds__(256) k_cc_split(int nb, int mx, int my, const 
 // Cyclic-reduction solve of one coupled-channel system with the setup-time factors:
 // forward, level by level, X_i -= alpha_i X_{i-s} + gamma_i X_{i+s} on the kept rows;
 // root Y = P X; backward, Y_j = P_j X_j - Q_j Y_{j-s} - R_j Y_{j+s} on the rows each
-// level eliminated.  Block 0 solves channel A (along y), block 1 channel B (along x);
-// each level is one parallel pass over (row, component) pairs.
-__global__ void __launch_bounds__(512) k_channel_solve(CRSystem SA, CRSystem SB) {
-  const CRSystem& S = blockIdx.x == 0 ? SA : SB;
+// level eliminated.  Each system is solved by one thread-block cluster of CR_CLUSTER
+// CTAs (cluster 0: channel A along y, cluster 1: channel B along x); every level is one
+// pass over (row, component) pairs split across the cluster, separated by cluster
+// barriers (release/acquire at cluster scope orders the global-memory traffic).
+constexpr int CR_CLUSTER = 8;
+constexpr int CR_THREADS = 256;
+
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+__global__ void __cluster_dims__(CR_CLUSTER, 1, 1) __launch_bounds__(CR_THREADS)
+k_channel_solve(CRSystem SA, CRSystem SB) {
+  const int sys = blockIdx.x / CR_CLUSTER;
+  const int rank = blockIdx.x % CR_CLUSTER;
+  const CRSystem& S = sys == 0 ? SA : SB;
   const int nb = S.nb, nb2 = nb * nb, M = S.M, q = S.q, m = S.m;
-  const int t0 = threadIdx.x, nt = blockDim.x;
+  const int t0 = rank * CR_THREADS + threadIdx.x, nt = CR_CLUSTER * CR_THREADS;
   for (int idx = t0; idx < (M + 2) * nb; idx += nt) {
     const int row = idx / nb, comp = idx % nb;
     S.X[idx] = (row >= 1 && row <= m) ? S.r[comp * m + row - 1] : cmk(0.0, 0.0);
     S.Y[idx] = cmk(0.0, 0.0);
   }
-  __syncthreads();
+  cluster_barrier();
   for (int l = 1; l < q; ++l) {
     const int s = 1 << (l - 1);
     const int nk = (1 << (q - l)) - 1;
@@ -188,7 +209,7 @@ __global__ void __launch_bounds__(512) k_channel_solve(CRSystem SA, CRSystem SB)
       }
       S.X[i * nb + comp] = acc;
     }
-    __syncthreads();
+    cluster_barrier();
   }
   const int root = 1 << (q - 1);
   if (t0 < nb) {
@@ -197,7 +218,7 @@ __global__ void __launch_bounds__(512) k_channel_solve(CRSystem SA, CRSystem SB)
     for (int p = 0; p < nb; ++p) acc = cfma(Pr[p], S.X[root * nb + p], acc);
     S.Y[root * nb + t0] = acc;
   }
-  __syncthreads();
+  cluster_barrier();
   for (int l = q - 1; l >= 1; --l) {
     const int s = 1 << (l - 1);
     const int ne = 1 << (q - l);           // odd multiples of s in 1..M
@@ -214,7 +235,7 @@ __global__ void __launch_bounds__(512) k_channel_solve(CRSystem SA, CRSystem SB)
       }
       S.Y[j * nb + comp] = acc;
     }
-    __syncthreads();
+    cluster_barrier();
   }
   for (int idx = t0; idx < m * nb; idx += nt) {
     const int comp = idx / m, k = idx % m;
@@ -282,8 +303,8 @@ cudaError_t launch_residual_project(const StencilViewT<C>& s, const CCViewT<C>& 
 template <class C>
 cudaError_t launch_cc_rhs(const CCViewT<C>& c, cudaStream_t st) {
   int tot = c.nb * (c.mx + c.my);
-  k_reduce_partials<C><<<(tot + 255) / 256, 256, 0, st>>>(c.nb, c.mx, c.my, cc_tiles_x(c.mx), cc_tiles_y(c.my),
-                                                           c.Px_part, c.Py_part, c.Px, c.Py);
+  k_reduce_partials<C><<<(8 * tot + 255) / 256, 256, 0, st>>>(c.nb, c.mx, c.my, cc_tiles_x(c.mx), cc_tiles_y(c.my),
+                                                               c.Px_part, c.Py_part, c.Px, c.Py);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_cc_coef<<<c.nb * c.nb, 256, 0, st>>>(c.nb, c.my, c.wvphi64, c.Px, c.c);
@@ -300,7 +321,7 @@ int cr_levels(int m) {
 }
 
 cudaError_t launch_channel_solve(const CRSystem& A, const CRSystem& B, cudaStream_t st) {
-  k_channel_solve<<<2, 512, 0, st>>>(A, B);
+  k_channel_solve<<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B);
   return cudaGetLastError();
 }
 

@@ -70,10 +70,12 @@ __global__ void __launch_bounds__(NT) k_reduce_dots(int nblk, const cplx* __rest
 template <class C>
 __global__ void __launch_bounds__(NT) k_multiaxpy(long long n, int k, const C* __restrict__ V, long long ld,
                                                   const cplx* __restrict__ coef, double sgn, C* __restrict__ w,
-                                                  double* __restrict__ norm_part, const int* __restrict__ gate) {
+                                                  double* __restrict__ norm_part, const int* __restrict__ gate,
+                                                  const int* __restrict__ dk) {
   __shared__ C sc[64];
   __shared__ double sh[NT / 32];
   if (gate && *gate == 0) return;
+  if (dk) k = min(k, *dk);
   for (int i = threadIdx.x; i < k; i += NT) {
     const cplx q = cscal(sgn, coef[i]);
     sc[i] = CT<C>::make(q.x, q.y);
@@ -145,8 +147,9 @@ __global__ void k_givens(int j, int m, cplx* __restrict__ H, cplx* __restrict__ 
 
 // Back substitution R y = g[0..k-1] with the rotated (upper-triangular) H.
 __global__ void k_hess_solve(int k, int m, const cplx* __restrict__ H, const cplx* __restrict__ g,
-                             cplx* __restrict__ y) {
+                             cplx* __restrict__ y, const int* __restrict__ dk) {
   if (threadIdx.x != 0) return;
+  if (dk) k = min(k, *dk);
   for (int i = k - 1; i >= 0; --i) {
     cplx t = g[i];
     for (int q = i + 1; q < k; ++q) t = cfms(H[(size_t)q * (m + 1) + i], y[q], t);
@@ -161,6 +164,66 @@ __global__ void k_hess_solve(int k, int m, const cplx* __restrict__ H, const cpl
 // close to v_j and a first pass routinely removes half of |w|^2, harmlessly.)
 __global__ void k_dgks(const double* __restrict__ before, const double* __restrict__ after, int* __restrict__ gate) {
   if (threadIdx.x == 0) *gate = (*after < 1e-6 * *before) ? 1 : 0;
+}
+
+// ---- device-driven GMRES: stop tests that steer the conditional nodes of a solve graph.
+// One thread each; every value a test needs lives in the SolveCtl record.
+
+// After the true residual |r|^2 of a restart: stop (converged, out of steps, non-finite,
+// or a zero right-hand side) or open the next cycle with its estimate scale and target.
+__global__ void k_outer_control(SolveCtl* __restrict__ c, const double* __restrict__ rn2p,
+                                cudaGraphConditionalHandle h_outer, cudaGraphConditionalHandle h_cycle,
+                                cudaGraphConditionalHandle h_inner, cudaGraphConditionalHandle h_switch) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  c->outer += 1;
+  const double fn = sqrt(c->fn2);
+  const double rn2 = *rn2p;
+  bool stop = true;
+  if (fn == 0.0) {
+    c->rr = 0.0;
+    c->status = SOLVECTL_ZERO_RHS;
+  } else {
+    const double rr = sqrt(rn2) / fn;
+    c->rr = rr;
+    if (!isfinite(rr)) {
+      c->status = SOLVECTL_NONFINITE;
+    } else if (rr <= c->rtol) {
+      c->status = SOLVECTL_CONVERGED;
+    } else if (c->steps >= c->max_iter) {
+      c->status = SOLVECTL_MAXITER;
+    } else {
+      const double beta = sqrt(rn2);
+      if (c->mixed) {
+        c->scale = beta / fn;
+        c->target = fmax(c->inner_rtol, 0.5 * c->rtol * fn / beta) * beta / fn;
+      } else {
+        c->scale = 1.0 / fn;
+        c->target = c->rtol;
+      }
+      c->j = 0;
+      c->k = 0;
+      c->cycles += 1;
+      stop = false;
+    }
+  }
+  cudaGraphSetConditional(h_outer, stop ? 0u : 1u);
+  cudaGraphSetConditional(h_cycle, stop ? 0u : 1u);
+  cudaGraphSetConditional(h_inner, stop ? 0u : 1u);
+  cudaGraphSetConditional(h_switch, 0u);
+}
+
+// After Arnoldi step j: count it, and run step j+1 unless its residual estimate met the
+// target, the step budget is spent, the cycle is full, or the estimate is not finite.
+__global__ void k_step_control(SolveCtl* __restrict__ c, const double* __restrict__ est_raw,
+                               cudaGraphConditionalHandle h_inner, cudaGraphConditionalHandle h_switch) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double est = *est_raw * c->scale;
+  c->steps += 1;
+  c->j += 1;
+  c->k = c->j;
+  const bool cont = isfinite(est) && est > c->target && c->steps < c->max_iter && c->j < c->m;
+  cudaGraphSetConditional(h_switch, (unsigned)c->j);
+  cudaGraphSetConditional(h_inner, cont ? 1u : 0u);
 }
 
 __global__ void k_zero_c(int n, cplx* __restrict__ a) {
@@ -189,8 +252,8 @@ cudaError_t launch_reduce_dots(int nblk, int k, const cplx* partial, cplx* out, 
 
 template <class C>
 cudaError_t launch_multiaxpy(long long n, int k, const C* V, long long ld, const cplx* coef, double sgn,
-                             C* w, double* norm_part, int nblk, const int* gate, cudaStream_t st) {
-  k_multiaxpy<C><<<nblk, NT, 0, st>>>(n, k, V, ld, coef, sgn, w, norm_part, gate);
+                             C* w, double* norm_part, int nblk, const int* gate, cudaStream_t st, const int* dk) {
+  k_multiaxpy<C><<<nblk, NT, 0, st>>>(n, k, V, ld, coef, sgn, w, norm_part, gate, dk);
   return cudaGetLastError();
 }
 
@@ -205,7 +268,7 @@ cudaError_t launch_scale_by_norm(long long n, const C* w, C* out, const double* 
   template cudaError_t launch_multidot<C>(long long, int, const C*, long long, const C*, cplx*, int,        \
                                          const int*, cudaStream_t);                                       \
   template cudaError_t launch_multiaxpy<C>(long long, int, const C*, long long, const cplx*, double, C*,   \
-                                          double*, int, const int*, cudaStream_t);                        \
+                                          double*, int, const int*, cudaStream_t, const int*);            \
   template cudaError_t launch_scale_by_norm<C>(long long, const C*, C*, const double*, cplx*, int,         \
                                               cudaStream_t);
 MGC_INSTANTIATE(double2)
@@ -217,13 +280,27 @@ cudaError_t launch_givens(int j, int m, cplx* H, cplx* cs, cplx* sn, cplx* g, do
   return cudaGetLastError();
 }
 
-cudaError_t launch_hess_solve(int k, int m, const cplx* H, const cplx* g, cplx* y, cudaStream_t st) {
-  k_hess_solve<<<1, 32, 0, st>>>(k, m, H, g, y);
+cudaError_t launch_hess_solve(int k, int m, const cplx* H, const cplx* g, cplx* y, cudaStream_t st,
+                              const int* dk) {
+  k_hess_solve<<<1, 32, 0, st>>>(k, m, H, g, y, dk);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dgks(const double* before, const double* after, int* gate, cudaStream_t st) {
   k_dgks<<<1, 32, 0, st>>>(before, after, gate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_outer_control(SolveCtl* c, const double* rn2, cudaGraphConditionalHandle h_outer,
+                                 cudaGraphConditionalHandle h_cycle, cudaGraphConditionalHandle h_inner,
+                                 cudaGraphConditionalHandle h_switch, cudaStream_t st) {
+  k_outer_control<<<1, 32, 0, st>>>(c, rn2, h_outer, h_cycle, h_inner, h_switch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_control(SolveCtl* c, const double* est, cudaGraphConditionalHandle h_inner,
+                                cudaGraphConditionalHandle h_switch, cudaStream_t st) {
+  k_step_control<<<1, 32, 0, st>>>(c, est, h_inner, h_switch);
   return cudaGetLastError();
 }
 

@@ -13,6 +13,8 @@
 //    and a bilinear Rayleigh quotient (Sec. 5.1.2, Sec. 5.2).
 //  * Channel potentials V^A, V^B (Sec. 4.2) and the cyclic-reduction factors of the
 //    coupled-channel systems (Eqs. (28)-(29)).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace {
@@ -80,78 +82,93 @@ __global__ void k_box_real_check(int mx, int ux, int uy, const cplx* __restrict_
 }
 
 // Dense inverse of the coarsest operator by Gauss-Jordan elimination with partial
-// pivoting on the augmented matrix [A | I] (nc x 2nc, in global memory), one block.
-__global__ void __launch_bounds__(1024) k_coarse_inverse(StencilView s, cplx* __restrict__ aug,
-                                                         cplx* __restrict__ Ainv, int* status) {
+// pivoting on the augmented matrix [A | I] (nc x 2nc, row-major, in global memory),
+// one pivot per pair of launches: k_gj_pivot (one block: pivot search, row swap, row
+// scaling, multiplier column) and k_gj_eliminate (all SMs: rank-1 update of the
+// columns right of the pivot).  A zero pivot sets MGC_ST_PIVOT and every later launch
+// of the elimination returns at once.
+
+__global__ void k_gj_assemble(StencilView s, cplx* __restrict__ aug) {
+  const int nc = s.mx * s.my;
+  const long long w2 = 2LL * nc;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nc * w2;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(q / w2), c = (int)(q % w2);
+    const int i = p % s.mx, j = p / s.mx;
+    cplx v = cmk(0.0, 0.0);
+    if (c == p) v = s.D[p];
+    else if (i > 0 && c == p - 1) v = s.west_x[i];
+    else if (i + 1 < s.mx && c == p + 1) v = s.east_x[i];
+    else if (j > 0 && c == p - s.mx) v = s.west_y[j];
+    else if (j + 1 < s.my && c == p + s.mx) v = s.east_y[j];
+    else if (c == nc + p) v = cmk(1.0, 0.0);
+    aug[q] = v;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_gj_pivot(int nc, cplx* __restrict__ aug, cplx* __restrict__ fac, int k,
+                                                   int* __restrict__ status) {
   __shared__ double sval[1024];
   __shared__ int sidx[1024];
-  __shared__ cplx fac[MGC_MAX_COARSE];
-  const int nc = s.mx * s.my;
-  const int w2 = 2 * nc;
   const int t = threadIdx.x;
-  // assemble [A | I]
-  for (long long q = t; q < (long long)nc * w2; q += blockDim.x) aug[q] = cmk(0.0, 0.0);
-  __syncthreads();
-  for (int p = t; p < nc; p += blockDim.x) {
-    const int i = p % s.mx, j = p / s.mx;
-    cplx* row = aug + (size_t)p * w2;
-    row[p] = s.D[p];
-    if (i > 0) row[p - 1] = s.west_x[i];
-    if (i + 1 < s.mx) row[p + 1] = s.east_x[i];
-    if (j > 0) row[p - s.mx] = s.west_y[j];
-    if (j + 1 < s.my) row[p + s.mx] = s.east_y[j];
-    row[nc + p] = cmk(1.0, 0.0);
+  const long long w2 = 2LL * nc;
+  if (*status & MGC_ST_PIVOT) return;
+  // pivot search over rows k..nc-1 (largest modulus, lowest index on ties)
+  double best = -1.0;
+  int bi = k;
+  for (int r = k + t; r < nc; r += blockDim.x) {
+    const double v = cmod(aug[r * w2 + k]);
+    if (v > best) { best = v; bi = r; }
   }
+  sval[t] = best;
+  sidx[t] = bi;
   __syncthreads();
-  for (int k = 0; k < nc; ++k) {
-    // pivot search over rows k..nc-1 (largest modulus, lowest index on ties)
-    double best = -1.0;
-    int bi = k;
-    for (int r = k + t; r < nc; r += blockDim.x) {
-      double v = cmod(aug[(size_t)r * w2 + k]);
-      if (v > best) { best = v; bi = r; }
-    }
-    sval[t] = best;
-    sidx[t] = bi;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if (t < o) {
-        double v2 = sval[t + o];
-        int i2 = sidx[t + o];
-        if (v2 > sval[t] || (v2 == sval[t] && i2 < sidx[t])) { sval[t] = v2; sidx[t] = i2; }
-      }
-      __syncthreads();
-    }
-    const int piv = sidx[0];
-    const double pmod = sval[0];
-    __syncthreads();
-    if (pmod == 0.0) {
-      if (t == 0) atomicOr(status, MGC_ST_PIVOT);
-      return;
-    }
-    if (piv != k) {
-      for (int c = t; c < w2; c += blockDim.x) {
-        cplx a = aug[(size_t)k * w2 + c];
-        aug[(size_t)k * w2 + c] = aug[(size_t)piv * w2 + c];
-        aug[(size_t)piv * w2 + c] = a;
-      }
-    }
-    __syncthreads();
-    const cplx pv = aug[(size_t)k * w2 + k];
-    __syncthreads();
-    for (int c = t; c < w2; c += blockDim.x) aug[(size_t)k * w2 + c] = cdiv(aug[(size_t)k * w2 + c], pv);
-    for (int r = t; r < nc; r += blockDim.x) fac[r] = aug[(size_t)r * w2 + k];
-    __syncthreads();
-    for (long long q = t; q < (long long)nc * w2; q += blockDim.x) {
-      const int r = (int)(q / w2), c = (int)(q % w2);
-      if (r == k) continue;
-      aug[q] = cfms(fac[r], aug[(size_t)k * w2 + c], aug[q]);
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (t < o) {
+      const double v2 = sval[t + o];
+      const int i2 = sidx[t + o];
+      if (v2 > sval[t] || (v2 == sval[t] && i2 < sidx[t])) { sval[t] = v2; sidx[t] = i2; }
     }
     __syncthreads();
   }
-  for (long long q = t; q < (long long)nc * nc; q += blockDim.x) {
-    const int r = (int)(q / nc), c = (int)(q % nc);
-    Ainv[q] = aug[(size_t)r * w2 + nc + c];
+  const int piv = sidx[0];
+  if (sval[0] == 0.0) {
+    if (t == 0) atomicOr(status, MGC_ST_PIVOT);
+    return;
+  }
+  if (piv != k)
+    for (int c = k + t; c < w2; c += blockDim.x) {
+      const cplx a = aug[k * w2 + c];
+      aug[k * w2 + c] = aug[piv * w2 + c];
+      aug[piv * w2 + c] = a;
+    }
+  __syncthreads();
+  const cplx pv = aug[k * w2 + k];
+  __syncthreads();
+  for (int c = k + t; c < w2; c += blockDim.x) aug[k * w2 + c] = cdiv(aug[k * w2 + c], pv);
+  for (int r = t; r < nc; r += blockDim.x) fac[r] = r == k ? cmk(0.0, 0.0) : aug[r * w2 + k];
+}
+
+__global__ void k_gj_eliminate(int nc, cplx* __restrict__ aug, const cplx* __restrict__ fac, int k,
+                               const int* __restrict__ status) {
+  if (*status & MGC_ST_PIVOT) return;
+  const long long w2 = 2LL * nc;
+  const long long w = w2 - k - 1;                    // columns right of the pivot
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nc * w;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(q / w);
+    if (r == k) continue;
+    const long long c = k + 1 + q % w;
+    aug[r * w2 + c] = cfms(fac[r], aug[k * w2 + c], aug[r * w2 + c]);
+  }
+}
+
+__global__ void k_gj_extract(int nc, const cplx* __restrict__ aug, cplx* __restrict__ Ainv) {
+  const long long w2 = 2LL * nc;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < (long long)nc * nc;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long r = q / nc, c = q % nc;
+    Ainv[q] = aug[r * w2 + nc + c];
   }
 }
 
@@ -598,8 +615,24 @@ cudaError_t launch_box_real_check(const StencilView& s, int* flag, cudaStream_t 
   return cudaGetLastError();
 }
 
+size_t coarse_inverse_scratch(int nc) { return (size_t)nc * 2 * nc + nc; }
+
 cudaError_t launch_coarse_inverse(const StencilView& s, cplx* aug, cplx* Ainv, int* status, cudaStream_t st) {
-  k_coarse_inverse<<<1, 1024, 0, st>>>(s, aug, Ainv, status);
+  const int nc = s.mx * s.my;
+  cplx* fac = aug + (size_t)nc * 2 * nc;
+  const long long total = 2LL * nc * nc;
+  const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 8);
+  k_gj_assemble<<<grid, 256, 0, st>>>(s, aug);
+  cudaError_t e = cudaGetLastError();
+  for (int k = 0; k < nc && e == cudaSuccess; ++k) {
+    k_gj_pivot<<<1, 1024, 0, st>>>(nc, aug, fac, k, status);
+    const long long work = (long long)nc * (2LL * nc - k - 1);
+    const int g = (int)std::max<long long>(1, std::min<long long>((work + 255) / 256, 152LL * 8));
+    k_gj_eliminate<<<g, 256, 0, st>>>(nc, aug, fac, k, status);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return e;
+  k_gj_extract<<<grid, 256, 0, st>>>(nc, aug, Ainv);
   return cudaGetLastError();
 }
 

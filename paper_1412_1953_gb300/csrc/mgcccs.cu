@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 
@@ -67,7 +68,18 @@ struct mgcccs_handle {
   cudaGraphExec_t step_exec[MGC_MAX_RESTART];
   long long step_launches[MGC_MAX_RESTART];
   cudaEvent_t ev[2];
-  double* est_host;                          // pinned, one residual estimate per step
+  double* est_host;                          // pinned, one residual estimate per step + |r|^2
+  // device-driven solves: control record, its pinned staging copy, capture streams, and
+  // the kernel counts of the solve graph's parts (prologue, restart, cycle, step)
+  SolveCtl* ctl;
+  SolveCtl* ctl_host;
+  cudaStream_t gst[2];
+  bool device_loop;
+  int driver;                                // MGCCCS_DRIVER_GRAPH or MGCCCS_DRIVER_HOST
+  cudaGraphExec_t solve_exec[4];             // device-driven solve graphs by (u, f) pointers
+  const void *solve_u[4], *solve_f[4];
+  int solve_next;
+  long long sg_pro, sg_outer, sg_cycle, sg_step;
   long long launches;
 };
 
@@ -148,7 +160,7 @@ void layout(mgcccs_handle* h, Carver& cv) {
   const LevelBufs& c = h->lv[L - 1];
   h->nc = c.mx * c.my;
   h->Ainv = cv.take<cplx>((size_t)h->nc * h->nc);
-  h->aug = cv.take<cplx>((size_t)h->nc * 2 * h->nc);
+  h->aug = cv.take<cplx>(coarse_inverse_scratch(h->nc));
   const int nb = p.n_b, mx = h->lv[0].mx, my = h->lv[0].my;
   h->nb = nb;
   if (nb > 0) {
@@ -237,6 +249,7 @@ void layout(mgcccs_handle* h, Carver& cv) {
     h->hc = cv.take<cplx>(m + 1);
     h->dotpart = cv.take<cplx>((size_t)(m + 1) * h->kr_nblk);
     h->gate = cv.take<int>(4);
+    h->ctl = cv.take<SolveCtl>(1);
     if (h->kr_nblk > h->norm_nparts) h->norm_nparts = h->kr_nblk;
   }
   h->norm_part = cv.take<double>(h->norm_nparts);
@@ -573,7 +586,8 @@ int issue_arnoldi_step(mgcccs_handle* h, int j) {
   MGC_LAUNCH(launch_sum_partials(h->norm_part, nb, h->norm_out + 1, st, h->gate));
   MGC_LAUNCH(launch_scale_by_norm(N, (const C*)w, w, h->norm_out + 1, col + j + 1, nb, st));
   MGC_LAUNCH(launch_givens(j, m, h->Hh, h->cs, h->sn, h->g, h->norm_out + 2, st));
-  MGC_CUDA(cudaMemcpyAsync(h->est_host + j, h->norm_out + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (!h->device_loop)
+    MGC_CUDA(cudaMemcpyAsync(h->est_host + j, h->norm_out + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
   return MGCCCS_OK;
 }
 
@@ -747,16 +761,410 @@ int gmres_ir_impl(mgcccs_handle* h, cplx* u, const cplx* f, double fn, double rt
   return rr <= rtol ? MGCCCS_OK : MGCCCS_ENOTCONV;
 }
 
+// ---- batched solves: per-problem GMRES cycles advanced in lock-step ---------------
+// The cycle of gmres_impl / gmres_ir_impl split into phases so that the host can
+// interleave many handles, each on its own stream: (1) every unfinished problem
+// enqueues its true residual and norm read-back, then the host reads them all;
+// (2) Arnoldi step j is launched for every problem still in its cycle, and the
+// estimate of step j-1 of each is checked while step j runs; (3) every problem
+// solves its Hessenberg system and updates u.
+
+struct BatchItem {
+  mgcccs_handle* h;
+  cplx* u;
+  const cplx* f;
+  double fn, rr, scale, target;
+  int steps, k;
+  bool active, in_cycle;
+  int status;
+};
+
+int batch_residual_enqueue(BatchItem& it) {
+  mgcccs_handle* h = it.h;
+  const StencilView& s0 = h->lv[0].sv;
+  cplx* rbuf = h->mixed ? h->r64 : h->V;
+  MGC_LAUNCH(launch_residual(s0, (const cplx*)it.u, it.f, rbuf, h->norm_part, h->st));
+  MGC_LAUNCH(launch_sum_partials(h->norm_part, residual_norm_blocks(s0), h->norm_out, h->st));
+  MGC_CUDA(cudaMemcpyAsync(h->est_host + MGC_MAX_RESTART, h->norm_out, sizeof(double), cudaMemcpyDeviceToHost,
+                           h->st));
+  return MGCCCS_OK;
+}
+
+// Stop test on the residual read back by batch_residual_enqueue; if the problem goes
+// on, v_0 and g of its next cycle are enqueued.
+int batch_cycle_begin(BatchItem& it, double rtol, int max_iter) {
+  mgcccs_handle* h = it.h;
+  cudaStream_t st = h->st;
+  MGC_CUDA(cudaStreamSynchronize(st));
+  const double rn2 = h->est_host[MGC_MAX_RESTART];
+  it.rr = std::sqrt(rn2) / it.fn;
+  it.in_cycle = false;
+  if (!std::isfinite(it.rr)) {
+    it.active = false;
+    it.status = MGCCCS_ENONFINITE;
+    return MGCCCS_OK;
+  }
+  if (it.rr <= rtol || it.steps >= max_iter) {
+    it.active = false;
+    it.status = it.rr <= rtol ? MGCCCS_OK : MGCCCS_ENOTCONV;
+    return MGCCCS_OK;
+  }
+  const StencilView& s0 = h->lv[0].sv;
+  const long long N = (long long)s0.mx * s0.my;
+  const int nb = h->kr_nblk;
+  const double beta = std::sqrt(rn2);
+  MGC_LAUNCH(launch_zero_c(h->km + 1, h->g, st));
+  if (h->mixed) {
+    MGC_LAUNCH(launch_demote(N, h->r64, h->norm_out, h->V32, st));
+    MGC_LAUNCH(launch_norm2(h->V32, N, h->norm_part, norm2_blocks(N), st));
+    MGC_LAUNCH(launch_sum_partials(h->norm_part, norm2_blocks(N), h->norm_out + 1, st));
+    MGC_LAUNCH(launch_scale_by_norm(N, (const float2*)h->V32, h->V32, h->norm_out + 1, h->g, nb, st));
+    it.scale = beta / it.fn;
+    it.target = std::max(h->inner_rtol, 0.5 * rtol * it.fn / beta) * beta / it.fn;
+  } else {
+    MGC_LAUNCH(launch_scale_by_norm(N, (const cplx*)h->V, h->V, h->norm_out, h->g, nb, st));
+    it.scale = 1.0 / it.fn;
+    it.target = rtol;
+  }
+  it.in_cycle = true;
+  it.k = 0;
+  return MGCCCS_OK;
+}
+
+int batch_cycle_end(BatchItem& it) {
+  mgcccs_handle* h = it.h;
+  cudaStream_t st = h->st;
+  const StencilView& s0 = h->lv[0].sv;
+  const long long N = (long long)s0.mx * s0.my;
+  const int nb = h->kr_nblk;
+  MGC_LAUNCH(launch_hess_solve(it.k, h->km, h->Hh, h->g, h->y, st));
+  if (h->mixed) {
+    MGC_CUDA(cudaMemsetAsync(h->e32, 0, sizeof(float2) * (size_t)N, st));
+    MGC_LAUNCH(launch_multiaxpy(N, it.k, (const float2*)h->Z32, N, h->y, 1.0, h->e32, (double*)nullptr, nb,
+                                (const int*)nullptr, st));
+    MGC_LAUNCH(launch_promote_add(N, h->e32, h->norm_out, it.u, st));
+  } else {
+    MGC_LAUNCH(launch_multiaxpy(N, it.k, (const cplx*)h->Z, N, h->y, 1.0, it.u, (double*)nullptr, nb,
+                                (const int*)nullptr, st));
+  }
+  return MGCCCS_OK;
+}
+
+int batch_solve_impl(std::vector<BatchItem>& items, double rtol, int max_iter) {
+  for (;;) {
+    for (auto& it : items)
+      if (it.active) {
+        int rc = batch_residual_enqueue(it);
+        if (rc) return rc;
+      }
+    bool any = false;
+    int mmax = 0;
+    for (auto& it : items)
+      if (it.active) {
+        int rc = batch_cycle_begin(it, rtol, max_iter);
+        if (rc) return rc;
+        if (it.in_cycle) {
+          any = true;
+          mmax = std::max(mmax, it.h->km);
+        }
+      }
+    if (!any) return MGCCCS_OK;
+    for (int j = 0; j <= mmax; ++j) {
+      for (auto& it : items) {
+        if (!it.in_cycle || j >= it.h->km) continue;
+        mgcccs_handle* h = it.h;
+        int rc = h->mixed ? launch_arnoldi_step<float2>(h, j) : launch_arnoldi_step<cplx>(h, j);
+        if (rc) return rc;
+        MGC_CUDA(cudaEventRecord(h->ev[j & 1], h->st));
+      }
+      if (j == 0) continue;
+      for (auto& it : items) {
+        if (!it.in_cycle || it.k != j - 1) continue;
+        mgcccs_handle* h = it.h;
+        MGC_CUDA(cudaEventSynchronize(h->ev[(j - 1) & 1]));
+        const double est = h->est_host[j - 1] * it.scale;
+        ++it.steps;
+        it.k = j;
+        if (!std::isfinite(est)) {
+          MGC_CUDA(cudaStreamSynchronize(h->st));
+          it.in_cycle = it.active = false;
+          it.status = MGCCCS_ENONFINITE;
+          it.rr = NAN;
+          continue;
+        }
+        if (est <= it.target || it.steps >= max_iter || j == h->km) {
+          int rc = batch_cycle_end(it);
+          if (rc) return rc;
+          it.in_cycle = false;
+        }
+      }
+    }
+  }
+}
+
+
+// ---- device-driven solves: a whole GMRES(m) solve as one CUDA graph ------------------
+// Conditional graph nodes carry the solver's control flow, so a solve is one graph
+// launch and the host neither waits nor decides between steps:
+//
+//   |f|^2 -> ctl.fn2
+//   WHILE (outer):                          one restart
+//     r = f - A u, |r|^2; k_outer_control   (stop test; opens the next cycle)
+//     IF (cycle):
+//       v_0 = r/|r| (complex64 in the mixed form), g = (|v_0|, 0, ...)
+//       WHILE (inner):
+//         SWITCH (j): Arnoldi step j        (the same launches as the host-driven step j)
+//         k_step_control                    (count the step; continue unless done)
+//       y = R^{-1} g (k = ctl.k columns); u += Z y   (mixed: u += promote(Z32 y))
+//
+// Several problems are independent root branches of one graph (batched solves).
+
+struct CaptureGuard {          // ends a capture on error so that the stream stays usable
+  cudaStream_t s;
+  bool open;
+  ~CaptureGuard() {
+    if (open) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(s, &g);
+    }
+  }
+};
+
+int capture_into(CaptureGuard& cg, cudaGraph_t g) {
+  MGC_CUDA(cudaStreamBeginCaptureToGraph(cg.s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cg.open = true;
+  return MGCCCS_OK;
+}
+
+int capture_end(CaptureGuard& cg) {
+  cudaGraph_t g = nullptr;
+  cg.open = false;
+  MGC_CUDA(cudaStreamEndCapture(cg.s, &g));
+  return MGCCCS_OK;
+}
+
+// Appends a conditional node after the capture's current tail; returns its body graphs.
+int add_conditional(cudaStream_t s, cudaGraphConditionalHandle hd, cudaGraphConditionalNodeType type,
+                    unsigned size, cudaGraph_t** bodies) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  MGC_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive) return MGCCCS_ECUDA;
+  cudaGraphNodeParams prm{};
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = hd;
+  prm.conditional.type = type;
+  prm.conditional.size = size;
+  cudaGraphNode_t node;
+  MGC_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, nd, &prm));
+  *bodies = prm.conditional.phGraph_out;
+  MGC_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return MGCCCS_OK;
+}
+
+template <class C>
+int append_steps(mgcccs_handle* h, cudaGraph_t* bodies, cudaStream_t s) {
+  cudaStream_t orig = h->st;
+  h->st = s;
+  h->device_loop = true;
+  int rc = MGCCCS_OK;
+  for (int j = 0; j < h->km && rc == MGCCCS_OK; ++j) {
+    CaptureGuard cg{s, false};
+    rc = capture_into(cg, bodies[j]);
+    const long long before = h->launches;
+    if (rc == MGCCCS_OK) rc = issue_arnoldi_step<C>(h, j);
+    if (j == 0) h->sg_step = h->launches - before;
+    if (rc == MGCCCS_OK) rc = capture_end(cg);
+  }
+  h->st = orig;
+  h->device_loop = false;
+  return rc;
+}
+
+// Adds one problem's solve (u, f on handle h) to graph G as an independent branch.
+int append_solve(mgcccs_handle* h, cplx* u, const cplx* f, cudaGraph_t G) {
+  const StencilView& s0 = h->lv[0].sv;
+  const long long N = (long long)s0.mx * s0.my;
+  const int m = h->km, nb = h->kr_nblk;
+  cudaStream_t S = h->gst[0];
+  cudaGraphConditionalHandle h_outer, h_cycle, h_inner, h_switch;
+  MGC_CUDA(cudaGraphConditionalHandleCreate(&h_outer, G, 1, cudaGraphCondAssignDefault));
+  MGC_CUDA(cudaGraphConditionalHandleCreate(&h_cycle, G, 0, 0));
+  MGC_CUDA(cudaGraphConditionalHandleCreate(&h_inner, G, 0, 0));
+  MGC_CUDA(cudaGraphConditionalHandleCreate(&h_switch, G, 0, 0));
+  const long long base = h->launches;
+  cudaGraph_t* b1 = nullptr;
+  {
+    CaptureGuard cg{S, false};
+    int rc = capture_into(cg, G);
+    if (rc) return rc;
+    const int nbk = norm2_blocks(N);
+    MGC_LAUNCH(launch_norm2(f, N, h->norm_part, nbk, S));
+    MGC_LAUNCH(launch_sum_partials(h->norm_part, nbk, &h->ctl->fn2, S));
+    rc = add_conditional(S, h_outer, cudaGraphCondTypeWhile, 1, &b1);
+    if (rc) return rc;
+    rc = capture_end(cg);
+    if (rc) return rc;
+  }
+  h->sg_pro = h->launches - base;
+  cudaGraph_t* b2 = nullptr;
+  {
+    const long long b0 = h->launches;
+    CaptureGuard cg{S, false};
+    int rc = capture_into(cg, b1[0]);
+    if (rc) return rc;
+    cplx* rbuf = h->mixed ? h->r64 : h->V;
+    MGC_LAUNCH(launch_residual(s0, (const cplx*)u, f, rbuf, h->norm_part, S));
+    MGC_LAUNCH(launch_sum_partials(h->norm_part, residual_norm_blocks(s0), h->norm_out, S));
+    MGC_LAUNCH(launch_outer_control(h->ctl, h->norm_out, h_outer, h_cycle, h_inner, h_switch, S));
+    rc = add_conditional(S, h_cycle, cudaGraphCondTypeIf, 1, &b2);
+    if (rc) return rc;
+    rc = capture_end(cg);
+    if (rc) return rc;
+    h->sg_outer = h->launches - b0;
+  }
+  cudaGraph_t* b3 = nullptr;
+  {
+    const long long b0 = h->launches;
+    CaptureGuard cg{S, false};
+    int rc = capture_into(cg, b2[0]);
+    if (rc) return rc;
+    MGC_LAUNCH(launch_zero_c(m + 1, h->g, S));
+    if (h->mixed) {
+      MGC_LAUNCH(launch_demote(N, h->r64, h->norm_out, h->V32, S));
+      MGC_LAUNCH(launch_norm2(h->V32, N, h->norm_part, norm2_blocks(N), S));
+      MGC_LAUNCH(launch_sum_partials(h->norm_part, norm2_blocks(N), h->norm_out + 1, S));
+      MGC_LAUNCH(launch_scale_by_norm(N, (const float2*)h->V32, h->V32, h->norm_out + 1, h->g, nb, S));
+    } else {
+      MGC_LAUNCH(launch_scale_by_norm(N, (const cplx*)h->V, h->V, h->norm_out, h->g, nb, S));
+    }
+    rc = add_conditional(S, h_inner, cudaGraphCondTypeWhile, 1, &b3);
+    if (rc) return rc;
+    MGC_LAUNCH(launch_hess_solve(m, m, h->Hh, h->g, h->y, S, &h->ctl->k));
+    if (h->mixed) {
+      MGC_CUDA(cudaMemsetAsync(h->e32, 0, sizeof(float2) * (size_t)N, S));
+      MGC_LAUNCH(launch_multiaxpy(N, m, (const float2*)h->Z32, N, h->y, 1.0, h->e32, (double*)nullptr, nb,
+                                  (const int*)nullptr, S, &h->ctl->k));
+      MGC_LAUNCH(launch_promote_add(N, h->e32, h->norm_out, u, S));
+    } else {
+      MGC_LAUNCH(launch_multiaxpy(N, m, (const cplx*)h->Z, N, h->y, 1.0, u, (double*)nullptr, nb,
+                                  (const int*)nullptr, S, &h->ctl->k));
+    }
+    rc = capture_end(cg);
+    if (rc) return rc;
+    h->sg_cycle = h->launches - b0;
+  }
+  cudaGraph_t* b4 = nullptr;
+  {
+    CaptureGuard cg{S, false};
+    int rc = capture_into(cg, b3[0]);
+    if (rc) return rc;
+    rc = add_conditional(S, h_switch, cudaGraphCondTypeSwitch, (unsigned)m, &b4);
+    if (rc) return rc;
+    MGC_LAUNCH(launch_step_control(h->ctl, h->norm_out + 2, h_inner, h_switch, S));
+    rc = capture_end(cg);
+    if (rc) return rc;
+  }
+  int rc = h->mixed ? append_steps<float2>(h, b4, h->gst[1]) : append_steps<cplx>(h, b4, h->gst[1]);
+  if (rc) return rc;
+  h->sg_step += 1;                     // + k_step_control
+  h->launches = base;                  // capture is not execution
+  return MGCCCS_OK;
+}
+
+int instantiate_solves(mgcccs_handle* const* hs, cplx* const* u, const cplx* const* f, int count,
+                       cudaGraphExec_t* exec) {
+  cudaGraph_t G = nullptr;
+  if (cudaGraphCreate(&G, 0) != cudaSuccess) return MGCCCS_ECUDA;
+  int rc = MGCCCS_OK;
+  for (int k = 0; k < count && rc == MGCCCS_OK; ++k) rc = append_solve(hs[k], u[k], f[k], G);
+  if (rc == MGCCCS_OK && cudaGraphInstantiate(exec, G, 0) != cudaSuccess) {
+    *exec = nullptr;
+    rc = MGCCCS_ECUDA;
+  }
+  cudaGraphDestroy(G);
+  return rc;
+}
+
+// Inputs of the control record, staged through pinned memory on stream st.
+int stage_ctl(mgcccs_handle* h, double rtol, int max_iter, cudaStream_t st) {
+  SolveCtl c{};
+  c.rtol = rtol;
+  c.inner_rtol = h->inner_rtol;
+  c.max_iter = max_iter;
+  c.mixed = h->mixed;
+  c.m = h->km;
+  *h->ctl_host = c;
+  MGC_CUDA(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(SolveCtl), cudaMemcpyHostToDevice, st));
+  return MGCCCS_OK;
+}
+
+int fetch_ctl(mgcccs_handle* h, cudaStream_t st) {
+  MGC_CUDA(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, st));
+  return MGCCCS_OK;
+}
+
+// Outcome of a finished device-driven solve (ctl_host already fetched and synchronised).
+int finish_ctl(mgcccs_handle* h, cplx* u, int* iters, double* relres) {
+  const SolveCtl& c = *h->ctl_host;
+  h->launches += h->sg_pro + (long long)c.outer * h->sg_outer + (long long)c.cycles * h->sg_cycle +
+                 (long long)c.steps * h->sg_step;
+  if (iters) *iters = c.steps;
+  if (relres) *relres = c.rr;
+  switch (c.status) {
+    case SOLVECTL_CONVERGED: return MGCCCS_OK;
+    case SOLVECTL_ZERO_RHS:
+      MGC_CUDA(cudaMemsetAsync(u, 0, sizeof(cplx) * (size_t)h->lv[0].mx * h->lv[0].my, h->st));
+      MGC_CUDA(cudaStreamSynchronize(h->st));
+      return MGCCCS_OK;
+    case SOLVECTL_MAXITER: return MGCCCS_ENOTCONV;
+    case SOLVECTL_NONFINITE: return MGCCCS_ENONFINITE;
+    default: return MGCCCS_ECUDA;
+  }
+}
+
+int graph_solve(mgcccs_handle* h, cplx* u, const cplx* f, double rtol, int max_iter, int* iters, double* relres) {
+  int slot = -1;
+  for (int q = 0; q < 4; ++q)
+    if (h->solve_exec[q] && h->solve_u[q] == u && h->solve_f[q] == f) slot = q;
+  if (slot < 0) {
+    slot = h->solve_next;
+    h->solve_next = (h->solve_next + 1) % 4;
+    if (h->solve_exec[slot]) cudaGraphExecDestroy(h->solve_exec[slot]);
+    h->solve_exec[slot] = nullptr;
+    mgcccs_handle* hs[1] = {h};
+    cplx* us[1] = {u};
+    const cplx* fs[1] = {f};
+    int rc = instantiate_solves(hs, us, fs, 1, &h->solve_exec[slot]);
+    if (rc) return rc;
+    h->solve_u[slot] = u;
+    h->solve_f[slot] = f;
+  }
+  int rc = stage_ctl(h, rtol, max_iter, h->st);
+  if (rc) return rc;
+  MGC_CUDA(cudaGraphLaunch(h->solve_exec[slot], h->st));
+  rc = fetch_ctl(h, h->st);
+  if (rc) return rc;
+  MGC_CUDA(cudaStreamSynchronize(h->st));
+  return finish_ctl(h, u, iters, relres);
+}
+
 int create_krylov_objects(mgcccs_handle* h) {
   MGC_CUDA(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
   for (int q = 0; q < 2; ++q) MGC_CUDA(cudaEventCreateWithFlags(&h->ev[q], cudaEventDisableTiming));
-  MGC_CUDA(cudaMallocHost(reinterpret_cast<void**>(&h->est_host), sizeof(double) * MGC_MAX_RESTART));
+  MGC_CUDA(cudaMallocHost(reinterpret_cast<void**>(&h->est_host), sizeof(double) * (MGC_MAX_RESTART + 1)));
+  MGC_CUDA(cudaMallocHost(reinterpret_cast<void**>(&h->ctl_host), sizeof(SolveCtl)));
+  for (int q = 0; q < 2; ++q) MGC_CUDA(cudaStreamCreateWithFlags(&h->gst[q], cudaStreamNonBlocking));
   return MGCCCS_OK;
 }
 
 int solve_impl(mgcccs_handle* h, cplx* u, const cplx* f, double rtol, int max_iter, int* iters, double* relres,
                double* history) {
   if (max_iter < 1) return MGCCCS_EINVAL;
+  if (h->km > 0 && !history && h->driver == MGCCCS_DRIVER_GRAPH)
+    return graph_solve(h, u, f, rtol, max_iter, iters, relres);
   double fn2 = 0.0;
   int rc = vec_norm2(h, f, &fn2);
   if (rc) return rc;
@@ -1000,6 +1408,120 @@ int mgcccs_weighted_product(mgcccs_t h, const mgcccs_c128* a, const mgcccs_c128*
   return MGCCCS_OK;
 }
 
+int mgcccs_batch_solve(mgcccs_t* handles, int count, mgcccs_c128* const* u, const mgcccs_c128* const* f,
+                       double rtol, int max_iter, int* iters, double* relres, int* status) {
+  if (!handles || count < 1 || !u || !f || max_iter < 1 || !(rtol >= 0.0)) return MGCCCS_EINVAL;
+  std::vector<BatchItem> items(count);
+  for (int k = 0; k < count; ++k) {
+    mgcccs_handle* h = handles[k];
+    if (!h || h->km < 1 || !u[k] || !f[k]) return MGCCCS_EINVAL;
+    for (int q = 0; q < k; ++q)
+      if (handles[q] == h) return MGCCCS_EINVAL;   // a handle's buffers serve one problem
+    items[k] = BatchItem{h, reinterpret_cast<cplx*>(u[k]), reinterpret_cast<const cplx*>(f[k]), 0.0, INFINITY,
+                         1.0, rtol, 0, 0, true, false, MGCCCS_OK};
+  }
+  for (auto& it : items) {
+    double fn2 = 0.0;
+    int rc = vec_norm2(it.h, it.f, &fn2);
+    if (rc) return rc;
+    it.fn = std::sqrt(fn2);
+    if (fn2 == 0.0) {
+      const LevelBufs& b = it.h->lv[0];
+      MGC_CUDA(cudaMemsetAsync(it.u, 0, sizeof(cplx) * (size_t)b.mx * b.my, it.h->st));
+      it.active = false;
+      it.rr = 0.0;
+    } else if (!std::isfinite(it.fn)) {
+      it.active = false;
+      it.rr = NAN;
+      it.status = MGCCCS_ENONFINITE;
+    }
+  }
+  int rc = batch_solve_impl(items, rtol, max_iter);
+  if (rc) return rc;
+  int worst = MGCCCS_OK;
+  for (int k = 0; k < count; ++k) {
+    MGC_CUDA(cudaStreamSynchronize(items[k].h->st));
+    if (iters) iters[k] = items[k].steps;
+    if (relres) relres[k] = items[k].rr;
+    if (status) status[k] = items[k].status;
+    if (items[k].status == MGCCCS_ENONFINITE) worst = MGCCCS_ENONFINITE;
+    else if (items[k].status == MGCCCS_ENOTCONV && worst == MGCCCS_OK) worst = MGCCCS_ENOTCONV;
+  }
+  return worst;
+}
+
+int mgcccs_set_solve_driver(mgcccs_t h, int driver) {
+  if (!h || (driver != MGCCCS_DRIVER_GRAPH && driver != MGCCCS_DRIVER_HOST)) return MGCCCS_EINVAL;
+  h->driver = driver;
+  return MGCCCS_OK;
+}
+
+struct mgcccs_batch {
+  std::vector<mgcccs_handle*> hs;
+  std::vector<cplx*> u;
+  cudaStream_t st;
+  cudaGraphExec_t exec;
+};
+
+int mgcccs_batch_create(mgcccs_batch_t* out, mgcccs_t* handles, int count, mgcccs_c128* const* u,
+                        const mgcccs_c128* const* f, void* stream) {
+  if (!out || !handles || count < 1 || !u || !f) return MGCCCS_EINVAL;
+  *out = nullptr;
+  std::vector<mgcccs_handle*> hs(count);
+  std::vector<cplx*> us(count);
+  std::vector<const cplx*> fs(count);
+  for (int k = 0; k < count; ++k) {
+    hs[k] = handles[k];
+    us[k] = reinterpret_cast<cplx*>(u[k]);
+    fs[k] = reinterpret_cast<const cplx*>(f[k]);
+    if (!hs[k] || hs[k]->km < 1 || !us[k] || !fs[k]) return MGCCCS_EINVAL;
+    for (int q = 0; q < k; ++q)
+      if (hs[q] == hs[k]) return MGCCCS_EINVAL;
+  }
+  mgcccs_batch* b = new (std::nothrow) mgcccs_batch();
+  if (!b) return MGCCCS_EINVAL;
+  b->hs = hs;
+  b->u = us;
+  b->st = reinterpret_cast<cudaStream_t>(stream);
+  b->exec = nullptr;
+  int rc = instantiate_solves(hs.data(), us.data(), fs.data(), count, &b->exec);
+  if (rc) {
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return MGCCCS_OK;
+}
+
+int mgcccs_batch_run(mgcccs_batch_t b, double rtol, int max_iter, int* iters, double* relres, int* status) {
+  if (!b || max_iter < 1 || !(rtol >= 0.0)) return MGCCCS_EINVAL;
+  for (mgcccs_handle* h : b->hs) {
+    int rc = stage_ctl(h, rtol, max_iter, b->st);
+    if (rc) return rc;
+  }
+  if (cudaGraphLaunch(b->exec, b->st) != cudaSuccess) return MGCCCS_ECUDA;
+  for (mgcccs_handle* h : b->hs) {
+    int rc = fetch_ctl(h, b->st);
+    if (rc) return rc;
+  }
+  if (cudaStreamSynchronize(b->st) != cudaSuccess) return MGCCCS_ECUDA;
+  int worst = MGCCCS_OK;
+  for (size_t k = 0; k < b->hs.size(); ++k) {
+    int s = finish_ctl(b->hs[k], b->u[k], iters ? iters + k : nullptr, relres ? relres + k : nullptr);
+    if (s == MGCCCS_ECUDA) return s;
+    if (status) status[k] = s;
+    if (s == MGCCCS_ENONFINITE) worst = MGCCCS_ENONFINITE;
+    else if (s == MGCCCS_ENOTCONV && worst == MGCCCS_OK) worst = MGCCCS_ENOTCONV;
+  }
+  return worst;
+}
+
+void mgcccs_batch_destroy(mgcccs_batch_t b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  delete b;
+}
+
 long long mgcccs_launch_count(mgcccs_t h) { return h ? h->launches : -1; }
 
 const char* mgcccs_strerror(int code) {
@@ -1023,8 +1545,13 @@ void mgcccs_destroy(mgcccs_t h) {
   }
   for (int q = 0; q < 2; ++q)
     if (h->ev[q]) cudaEventDestroy(h->ev[q]);
+  for (int q = 0; q < 4; ++q)
+    if (h->solve_exec[q]) cudaGraphExecDestroy(h->solve_exec[q]);
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
+  for (int q = 0; q < 2; ++q)
+    if (h->gst[q]) cudaStreamDestroy(h->gst[q]);
   if (h->est_host) cudaFreeHost(h->est_host);
+  if (h->ctl_host) cudaFreeHost(h->ctl_host);
   delete h;
 }
 

@@ -141,3 +141,23 @@ def gaussian_window(n: int, L: float, cx: float, cy: float, sigma: float, ny: in
     y = np.arange(1, ny) * (L / ny)
     X, Y = np.meshgrid(x, y)
     return np.ascontiguousarray(np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2.0 * sigma ** 2)), dtype=np.complex128)
+
+
+BATCH_SIZES = (256, 384, 512, 768, 1024)
+
+
+def batching_problems(count: int = 64, E_min: float = 0.1, E_max: float = 2.0, size_seed: int = 1,
+                      sizes=BATCH_SIZES, theta: float = math.pi / 6) -> list[Problem]:
+    """Many-energy workload: E_k evenly spaced in [E_min, E_max]; problem k on its own
+    n_k x n_k grid drawn from `sizes` by default_rng(size_seed); L = 30 n / 512 (the same
+    spacing h = 30/512 on every grid), ECS beyond R0 = 2L/3; source noise seed k."""
+    n_k = np.random.default_rng(size_seed).choice(np.asarray(sizes), size=count)
+    E_k = np.linspace(E_min, E_max, count)
+    out = []
+    for k in range(count):
+        n = int(n_k[k])
+        L = 30.0 * n / 512
+        p = temkin_poet(n, L=L, R0=2.0 * L / 3.0, theta=theta, E=float(E_k[k]), seed=k)
+        p.name = f"tp{n}_E{E_k[k]:.4f}"
+        out.append(p)
+    return out

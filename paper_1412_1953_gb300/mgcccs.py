@@ -61,6 +61,13 @@ _SIGS = {
     "mgcccs_solve": (_i, [_vp, _vp, _vp, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d), _vp]),
     "mgcccs_solve_host": (_i, [_vp, _vp, _vp, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
     "mgcccs_precond_apply": (_i, [_vp, _vp, _vp]),
+    "mgcccs_set_solve_driver": (_i, [_vp, _i]),
+    "mgcccs_batch_create": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp),
+                                 ctypes.POINTER(_vp), _vp]),
+    "mgcccs_batch_run": (_i, [_vp, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d), ctypes.POINTER(_i)]),
+    "mgcccs_batch_destroy": (None, [_vp]),
+    "mgcccs_batch_solve": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _i,
+                                ctypes.POINTER(_i), ctypes.POINTER(_d), ctypes.POINTER(_i)]),
     "mgcccs_residual": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(_d)]),
     "mgcccs_matvec": (_i, [_vp, _vp, _vp]),
     "mgcccs_weighted_dot": (_i, [_vp, _vp, _vp, _vp, mgcccs_c128, _vp]),
@@ -319,3 +326,63 @@ class Solver:
 
     def launch_count(self) -> int:
         return int(lib().mgcccs_launch_count(self.h))
+
+
+def mgcccs_batch_solve(solvers, us, fs, rtol=1e-10, max_iter=1000):
+    """Solve the problems of several Solver handles together (see include/mgcccs.h).
+    Returns (iterations, relres, status) lists; raises only on argument errors."""
+    K = len(solvers)
+    hs = (_vp * K)(*[s.h.value for s in solvers])
+    up = (_vp * K)(*[s._f(u, "u") for s, u in zip(solvers, us)])
+    fp = (_vp * K)(*[s._f(f, "f") for s, f in zip(solvers, fs)])
+    its = (_i * K)()
+    rr = (_d * K)()
+    st = (_i * K)()
+    code = lib().mgcccs_batch_solve(hs, K, up, fp, float(rtol), int(max_iter), its, rr, st)
+    if code not in (OK, ENOTCONV, ENONFINITE):
+        raise MGCCCSError(code, "mgcccs_batch_solve")
+    return list(its), list(rr), list(st)
+
+
+DRIVER_GRAPH, DRIVER_HOST = 0, 1
+
+
+def mgcccs_set_solve_driver(solver, driver: int):
+    _check(lib().mgcccs_set_solve_driver(solver.h, int(driver)), "mgcccs_set_solve_driver")
+
+
+class Batch:
+    """mgcccs_batch_create / _run / _destroy: the device-driven solves of several Solver
+    handles as one CUDA graph, launched once per run()."""
+
+    def __init__(self, solvers, us, fs, stream=None):
+        import torch
+        self.solvers, self.us, self.fs = list(solvers), list(us), list(fs)
+        K = len(self.solvers)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        hs = (_vp * K)(*[s.h.value for s in self.solvers])
+        up = (_vp * K)(*[s._f(u, "u") for s, u in zip(self.solvers, self.us)])
+        fp = (_vp * K)(*[s._f(f, "f") for s, f in zip(self.solvers, self.fs)])
+        b = _vp()
+        _check(lib().mgcccs_batch_create(ctypes.byref(b), hs, K, up, fp, self.stream.cuda_stream),
+               "mgcccs_batch_create")
+        self.b = b
+
+    def run(self, rtol=1e-10, max_iter=1000):
+        K = len(self.solvers)
+        its, rr, st = (_i * K)(), (_d * K)(), (_i * K)()
+        code = lib().mgcccs_batch_run(self.b, float(rtol), int(max_iter), its, rr, st)
+        if code not in (OK, ENOTCONV, ENONFINITE):
+            raise MGCCCSError(code, "mgcccs_batch_run")
+        return list(its), list(rr), list(st)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().mgcccs_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
