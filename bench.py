@@ -60,6 +60,8 @@ def parse():
                     default="bench",
                     help="solve-only: setup + warm-up + timed solves, nothing else (for launch lists); "
                          "kernel: setup + 6 launches of one kernel (for ncu captures)")
+    ap.add_argument("--driver", choices=["graph", "host"], default="graph",
+                    help="GMRES control: one device-driven graph per solve, or host-driven cycles")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--autotune", action="store_true", help="batch: tune (levels, nu1, nu2) per grid size")
     ap.add_argument("--kernel", choices=["jacobi", "residual_project", "multidot"], default="jacobi")
@@ -75,7 +77,9 @@ def workload(args):
            "precision": "complex64 inner cycles in FP64 refinement" if args.precision == "mixed" else "complex128",
            "n_b": args.nb, "levels": args.levels, "cycle": "V(1,1), omega=2/3 Jacobi, FW, bilinear",
            "coarse_contour_deg": 14.6, "rtol": args.rtol,
-           "outer": f"GMRES({args.krylov}) right-preconditioned by one MG-CCCS iteration" if args.krylov
+           "outer": f"GMRES({args.krylov}) right-preconditioned by one MG-CCCS iteration, "
+                    f"{'device-driven (one graph launch per solve)' if args.driver == 'graph' else 'host-driven cycles'}"
+           if args.krylov
            else "stand-alone MG-CCCS iteration", "source": "TP impact source + 1e-3 complex noise, seed 0"}
     return prob, cfg
 
@@ -204,7 +208,7 @@ def measured_peaks():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("kernels_mg.cu", "common.cuh"):
+    for f in ("kernels_mg.cu",):
         h.update(open(os.path.join(ROOT, "paper_1412_1953_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -495,6 +499,8 @@ def run_ours(args):
     solver = M.Solver(M.params_for(prob, levels=args.levels, n_b=args.nb, krylov_restart=args.krylov,
                                    precision=1 if args.precision == "mixed" else 0),
                       prob.v1, prob.v2, prob.v12)
+    if args.driver == "host":
+        M.mgcccs_set_solve_driver(solver, M.DRIVER_HOST)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     stream = solver.stream

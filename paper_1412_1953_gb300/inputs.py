@@ -10,7 +10,7 @@ Node coordinates follow exterior complex scaling (Sec. 2.5): the real grid
 x_i = i*L/n (i = 0..n) is kept for x_i <= R0 and bent into the complex plane
 beyond, z(x) = R0 + (x - R0) e^{i theta}.  Potentials and the source are
 evaluated at these complex nodes (analytic continuation, as the paper does for
-the incoming wave of Eq. (31)).
+the incoming wave of Sec. 3.1).
 
 Array layout everywhere: interior nodes only, row-major [j][i] with x (index i)
 fastest; v1 has nx-1 entries, v2 has ny-1, v12 and f have (ny-1)*(nx-1).
@@ -77,7 +77,7 @@ def temkin_poet(n: int, L: float = 30.0, R0: float = 20.0, theta: float = math.p
 
     2x e^{-x} is the normalised hydrogenic ground state, so f is the potential
     (V2 + V12) acting on an incoming wave phi_1(x) sin(k y), the impact-ionisation
-    form of Eq. (31) with k = sqrt(2E) as the workload fixes it.
+    form of Sec. 3.1 with k = sqrt(2E) as the workload fixes it.
     """
     ny = n if ny is None else ny
     x, zx = node_coordinates(n, L, R0, theta)
