@@ -115,6 +115,22 @@ struct StencilViewT {
 typedef StencilViewT<cplx> StencilView;
 typedef StencilViewT<float2> StencilView32;
 
+// One level of the fused coarse-level V-cycle (k_vcycle_tail): stencil, iterate,
+// right-hand side, smoother scratch and residual.
+template <class C>
+struct TailLevel {
+  StencilViewT<C> sv;
+  C *u, *f, *t, *r;
+};
+// Levels l0..L-1 of a hierarchy (lv[0] = level l0, lv[n-1] = the coarsest).
+template <class C>
+struct TailArgs {
+  int n, nu1, nu2, zero_init, nc;
+  const cplx* Ainv;
+  TailLevel<C> lv[MGC_MAX_LEVELS];
+};
+constexpr int TAIL_THREADS = 1024;
+
 // Error bits written by kernels into the handle's device status word.
 enum {
   MGC_ST_PIVOT = 1,        // zero pivot in a dense or block factorisation
@@ -140,6 +156,8 @@ cudaError_t launch_restrict(int mx, int my, const C* r, C* rc, cudaStream_t st);
 template <class C>
 cudaError_t launch_prolong_add(int mx, int my, const C* ec, C* u, cudaStream_t st);
 template <class C>
+cudaError_t launch_vcycle_tail(const TailArgs<C>& a, cudaStream_t st);
+template <class C>
 cudaError_t launch_coarse_solve(int nc, const cplx* Ainv, const C* f, C* u, cudaStream_t st);
 template <class C>
 cudaError_t launch_apply(const StencilViewT<C>& s, const C* x, C* y, cudaStream_t st, double* norm_part = nullptr);
@@ -155,6 +173,7 @@ cudaError_t launch_promote(long long n, const float2* x, cplx* y, cudaStream_t s
 
 // kernels_krylov.cu
 int krylov_blocks(long long n);
+int multidot_blocks(long long n, int k);
 template <class C>
 cudaError_t launch_multidot(long long n, int k, const C* V, long long ld, const C* w, cplx* partial,
                             int nblk, const int* gate, cudaStream_t st);
@@ -210,6 +229,8 @@ struct CCViewT {
   cplx* rB;                // [nb][mx]
   cplx* eA;                // [nb][my]
   cplx* eB;                // [nb][mx]
+  const C* eAc;            // eA, eB in the element precision (the same arrays for complex128)
+  const C* eBc;
   const cplx* phi64;       // [nb][mx] FP64 states for the channel right-hand sides
   const cplx* vphi64;      // [nb][my]
   const cplx* wvphi64;     // [nb][my]
@@ -235,6 +256,7 @@ struct CRSystem {
   cplx* Y;                 // [(M+2)*nb] solution, rows 0 and M+1 zero (solve scratch)
   const cplx* r;           // [nb][m] right-hand side
   cplx* e;                 // [nb][m] solution
+  float2* e32;             // [nb][m] solution rounded to complex64 (mixed precision), or null
 };
 int cr_levels(int m);
 __host__ __device__ inline int cr_fwd_offset(int q, int l) {

@@ -239,29 +239,27 @@ k_channel_solve(CRSystem SA, CRSystem SB) {
   }
   for (int idx = t0; idx < m * nb; idx += nt) {
     const int comp = idx / m, k = idx % m;
-    S.e[idx] = S.Y[(k + 1) * nb + comp];
+    const cplx v = S.Y[(k + 1) * nb + comp];
+    S.e[idx] = v;
+    if (S.e32) S.e32[idx] = make_float2((float)v.x, (float)v.y);
   }
 }
 
+// u += sum_m phi_m(x) e^A_m(y) + sum_l e^B_l(x) vphi_l(y) in the element precision
+// (the channel solutions arrive already rounded to it).
 template <int NB, class C>
 __global__ void __launch_bounds__(256) k_cccs_correct(int mx, int my, const C* __restrict__ phi,
-                                                      const C* __restrict__ vphi, const cplx* __restrict__ eA,
-                                                      const cplx* __restrict__ eB, C* __restrict__ u) {
+                                                      const C* __restrict__ vphi, const C* __restrict__ eA,
+                                                      const C* __restrict__ eB, C* __restrict__ u) {
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y * 8 + threadIdx.y;
   if (i >= mx || j >= my) return;
   const int p = j * mx + i;
   C v = u[p];
 #pragma unroll
-  for (int m = 0; m < NB; ++m) {
-    const cplx e = __ldg(eA + m * my + j);
-    v = cfma(__ldg(phi + m * mx + i), CT<C>::make(e.x, e.y), v);
-  }
+  for (int m = 0; m < NB; ++m) v = cfma(__ldg(phi + m * mx + i), __ldg(eA + m * my + j), v);
 #pragma unroll
-  for (int l = 0; l < NB; ++l) {
-    const cplx e = __ldg(eB + l * mx + i);
-    v = cfma(CT<C>::make(e.x, e.y), __ldg(vphi + l * my + j), v);
-  }
+  for (int l = 0; l < NB; ++l) v = cfma(__ldg(eB + l * mx + i), __ldg(vphi + l * my + j), v);
   u[p] = v;
 }
 
@@ -275,7 +273,7 @@ cudaError_t rp_launch(const StencilViewT<C>& s, const CCViewT<C>& c, const C* u,
 template <int NB, class C>
 cudaError_t corr_launch(const CCViewT<C>& c, C* u, cudaStream_t st) {
   dim3 g((c.mx + 31) / 32, (c.my + 7) / 8);
-  k_cccs_correct<NB, C><<<g, dim3(32, 8), 0, st>>>(c.mx, c.my, c.phi, c.vphi, c.eA, c.eB, u);
+  k_cccs_correct<NB, C><<<g, dim3(32, 8), 0, st>>>(c.mx, c.my, c.phi, c.vphi, c.eAc, c.eBc, u);
   return cudaGetLastError();
 }
 

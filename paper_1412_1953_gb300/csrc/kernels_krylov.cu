@@ -12,15 +12,18 @@ namespace {
 
 constexpr int NT = 256;
 
-template <int NTH>
-__device__ __forceinline__ cplx block_sum_c(cplx v, double (*sh)[NTH / 32]) {
+// Block sum of a complex value: warp sums in the element precision, the per-warp totals
+// in FP64 by thread 0 (fixed order).  Complex64 data keeps the FP64 pipe out of the
+// per-thread work.
+template <int NTH, class C>
+__device__ __forceinline__ cplx block_sum_c(C v, double (*sh)[NTH / 32]) {
   const int t = threadIdx.x;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     v.x += __shfl_down_sync(0xffffffffu, v.x, o);
     v.y += __shfl_down_sync(0xffffffffu, v.y, o);
   }
-  if ((t & 31) == 0) { sh[0][t >> 5] = v.x; sh[1][t >> 5] = v.y; }
+  if ((t & 31) == 0) { sh[0][t >> 5] = (double)v.x; sh[1][t >> 5] = (double)v.y; }
   __syncthreads();
   cplx tot = cmk(0.0, 0.0);
   if (t == 0)
@@ -48,7 +51,7 @@ __global__ void __launch_bounds__(NT) k_multidot(long long n, const C* __restric
     acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
     acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
   }
-  cplx tot = block_sum_c<NT>(to_c128(acc), sh);
+  cplx tot = block_sum_c<NT>(acc, sh);
   if (threadIdx.x == 0) partial[(size_t)i * gridDim.x + blockIdx.x] = tot;
 }
 
@@ -81,17 +84,17 @@ __global__ void __launch_bounds__(NT) k_multiaxpy(long long n, int k, const C* _
     sc[i] = CT<C>::make(q.x, q.y);
   }
   __syncthreads();
-  double n2 = 0.0;
+  typename CT<C>::R n2 = 0;
   for (long long p = blockIdx.x * (long long)NT + threadIdx.x; p < n; p += (long long)gridDim.x * NT) {
     C acc = w[p];
     for (int i = 0; i < k; ++i) acc = cfma(sc[i], __ldg(V + (size_t)i * ld + p), acc);
     w[p] = acc;
-    n2 += (double)cabs2(acc);
+    n2 += cabs2(acc);
   }
   if (norm_part) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) n2 += __shfl_down_sync(0xffffffffu, n2, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = n2;
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)n2;
     __syncthreads();
     if (threadIdx.x == 0) {
       double tot = 0.0;
@@ -105,8 +108,14 @@ __global__ void __launch_bounds__(NT) k_multiaxpy(long long n, int k, const C* _
 template <class C>
 __global__ void __launch_bounds__(NT) k_scale_by_norm(long long n, const C* __restrict__ w, C* __restrict__ out,
                                                       const double* __restrict__ norm2, cplx* __restrict__ store) {
-  const double beta = sqrt(*norm2);
-  const double s = beta > 0.0 ? 1.0 / beta : 0.0;
+  __shared__ double sb[2];
+  if (threadIdx.x == 0) {
+    const double b = sqrt(*norm2);
+    sb[0] = b;
+    sb[1] = b > 0.0 ? 1.0 / b : 0.0;
+  }
+  __syncthreads();
+  const double beta = sb[0], s = sb[1];
   const long long p0 = blockIdx.x * (long long)NT + threadIdx.x;
   if (p0 == 0 && store) *store = cmk(beta, 0.0);
   for (long long p = p0; p < n; p += (long long)gridDim.x * NT) out[p] = cscal((typename CT<C>::R)s, w[p]);
@@ -236,6 +245,16 @@ __global__ void k_zero_c(int n, cplx* __restrict__ a) {
 int krylov_blocks(long long n) {
   long long b = (n + NT - 1) / NT;
   return (int)(b < 608 ? (b < 1 ? 1 : b) : 608);
+}
+
+// Blocks per vector of a k-vector multi-dot: about one full wave (152 SMs x 8 blocks)
+// over all k vectors, so that each thread folds many elements before its share of the
+// block reduction; never more than krylov_blocks(n), never fewer than 64.
+int multidot_blocks(long long n, int k) {
+  const int cap = krylov_blocks(n);
+  int b = 1216 / (k < 1 ? 1 : k);
+  if (b < 64) b = 64;
+  return b < cap ? b : cap;
 }
 
 template <class C>

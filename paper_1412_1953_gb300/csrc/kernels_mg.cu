@@ -14,19 +14,28 @@ namespace {
 
 constexpr int BX = 32, BY = 8;
 
-template <class C>
+// Loads of arrays a kernel may also write: through the read-only path (NC) in the
+// one-step kernels, plain loads in the fused coarse-level kernel (which rewrites them
+// between its stages).  Stencil coefficients always use the read-only path.
+template <bool NC, class T>
+__device__ __forceinline__ T ldm(const T* __restrict__ a) {
+  if constexpr (NC) return __ldg(a);
+  else return *a;
+}
+
+template <bool NC, class C>
 __device__ __forceinline__ C ldz(const C* __restrict__ a, int p, bool ok) {
-  return ok ? __ldg(a + p) : CT<C>::make(0.0, 0.0);
+  return ok ? ldm<NC>(a + p) : CT<C>::make(0.0, 0.0);
 }
 
 // (H - E) u at interior node (i, j), given the centre value uc.
-template <class C>
+template <bool NC, class C>
 __device__ __forceinline__ C apply_op(const StencilViewT<C>& s, const C* __restrict__ u, int i, int j, C uc) {
   const int p = j * s.mx + i;
-  C uw = ldz(u, p - 1, i > 0);
-  C ue = ldz(u, p + 1, i + 1 < s.mx);
-  C us = ldz(u, p - s.mx, j > 0);
-  C un = ldz(u, p + s.mx, j + 1 < s.my);
+  C uw = ldz<NC>(u, p - 1, i > 0);
+  C ue = ldz<NC>(u, p + 1, i + 1 < s.mx);
+  C us = ldz<NC>(u, p - s.mx, j > 0);
+  C un = ldz<NC>(u, p + s.mx, j + 1 < s.my);
   C a = cmul(__ldg(s.D + p), uc);
   if (i < s.ux && j < s.uy) {
     C sum = cadd(cadd(uw, ue), cadd(us, un));
@@ -47,11 +56,11 @@ __device__ __forceinline__ typename CT<C>::R ldre(const C* __restrict__ a, int p
 }
 
 // (H - E) u in the real box: real coefficient cu.x and real diagonal.
-template <class C>
+template <bool NC, class C>
 __device__ __forceinline__ C apply_op_rbox(const StencilViewT<C>& s, const C* __restrict__ u, int i, int j, C uc) {
   const int p = j * s.mx + i;
-  C sum = cadd(cadd(ldz(u, p - 1, i > 0), ldz(u, p + 1, i + 1 < s.mx)),
-               cadd(ldz(u, p - s.mx, j > 0), ldz(u, p + s.mx, j + 1 < s.my)));
+  C sum = cadd(cadd(ldz<NC>(u, p - 1, i > 0), ldz<NC>(u, p + 1, i + 1 < s.mx)),
+               cadd(ldz<NC>(u, p - s.mx, j > 0), ldz<NC>(u, p + s.mx, j + 1 < s.my)));
   const typename CT<C>::R d = ldre(s.D, p);
   C a;
   a.x = fma(s.cu.x, sum.x, d * uc.x);
@@ -59,9 +68,90 @@ __device__ __forceinline__ C apply_op_rbox(const StencilViewT<C>& s, const C* __
   return a;
 }
 
-template <class C>
+template <bool NC, class C>
 __device__ __forceinline__ C apply_any(const StencilViewT<C>& s, const C* __restrict__ u, int i, int j, C uc) {
-  return (s.rbox && i < s.ux && j < s.uy) ? apply_op_rbox(s, u, i, j, uc) : apply_op(s, u, i, j, uc);
+  return (s.rbox && i < s.ux && j < s.uy) ? apply_op_rbox<NC>(s, u, i, j, uc) : apply_op<NC>(s, u, i, j, uc);
+}
+
+// ---- per-node arithmetic shared by the one-step kernels and the fused coarse-level kernel
+
+// One omega-Jacobi update at (i, j): u + (omega/D)(f - (H-E)u).
+template <bool NC, class C>
+__device__ __forceinline__ C jacobi_pt(const StencilViewT<C>& s, const C* __restrict__ u_in,
+                                       const C* __restrict__ f, int i, int j) {
+  const int p = j * s.mx + i;
+  C uc = ldm<NC>(u_in + p);
+  if (s.rbox && i < s.ux && j < s.uy) {
+    C r = csub(ldm<NC>(f + p), apply_op_rbox<NC>(s, u_in, i, j, uc));
+    const typename CT<C>::R di = ldre(s.Dinv, p);
+    C o;
+    o.x = fma(di, r.x, uc.x);
+    o.y = fma(di, r.y, uc.y);
+    return o;
+  }
+  C r = csub(ldm<NC>(f + p), apply_op<NC>(s, u_in, i, j, uc));
+  return cfma(__ldg(s.Dinv + p), r, uc);
+}
+
+template <bool NC, class C>
+__device__ __forceinline__ C residual_pt(const StencilViewT<C>& s, const C* __restrict__ u, const C* __restrict__ f,
+                                         int i, int j) {
+  const int p = j * s.mx + i;
+  return csub(ldm<NC>(f + p), apply_any<NC>(s, u, i, j, ldm<NC>(u + p)));
+}
+
+// Full weighting 1/16 [1 2 1; 2 4 2; 1 2 1] onto coarse interior node (I, J), which sits
+// on fine interior node (2I+1, 2J+1); all nine taps are interior nodes.
+template <bool NC, class C>
+__device__ __forceinline__ C restrict_pt(int mx, const C* __restrict__ r, int I, int J) {
+  typedef typename CT<C>::R R;
+  const int c = (2 * J + 1) * mx + (2 * I + 1);
+  C corners = cadd(cadd(ldm<NC>(r + c - mx - 1), ldm<NC>(r + c - mx + 1)),
+                   cadd(ldm<NC>(r + c + mx - 1), ldm<NC>(r + c + mx + 1)));
+  C edges = cadd(cadd(ldm<NC>(r + c - 1), ldm<NC>(r + c + 1)), cadd(ldm<NC>(r + c - mx), ldm<NC>(r + c + mx)));
+  C centre = ldm<NC>(r + c);
+  C acc;
+  acc.x = fma(R(2), edges.x, fma(R(4), centre.x, corners.x));
+  acc.y = fma(R(2), edges.y, fma(R(4), centre.y, corners.y));
+  return cscal(R(0.0625), acc);
+}
+
+template <bool NC, class C>
+__device__ __forceinline__ C coarse_at(const C* __restrict__ ec, int mcx, int mcy, int K, int Kp) {
+  // coarse node (K, Kp), 0..mc+1; boundary nodes carry zero
+  return (K >= 1 && K <= mcx && Kp >= 1 && Kp <= mcy) ? ldm<NC>(ec + (Kp - 1) * mcx + (K - 1))
+                                                       : CT<C>::make(0.0, 0.0);
+}
+
+// Bilinear interpolation of the coarse correction at fine interior node (i, j).
+template <bool NC, class C>
+__device__ __forceinline__ C prolong_pt(int mcx, int mcy, const C* __restrict__ ec, int i, int j) {
+  typedef typename CT<C>::R R;
+  const int kx = i + 1, ky = j + 1;
+  const int Kx = kx >> 1, Ky = ky >> 1;
+  if (!(kx & 1) && !(ky & 1)) return coarse_at<NC>(ec, mcx, mcy, Kx, Ky);
+  if (!(ky & 1))
+    return cscal(R(0.5), cadd(coarse_at<NC>(ec, mcx, mcy, Kx, Ky), coarse_at<NC>(ec, mcx, mcy, Kx + 1, Ky)));
+  if (!(kx & 1))
+    return cscal(R(0.5), cadd(coarse_at<NC>(ec, mcx, mcy, Kx, Ky), coarse_at<NC>(ec, mcx, mcy, Kx, Ky + 1)));
+  return cscal(R(0.25), cadd(cadd(coarse_at<NC>(ec, mcx, mcy, Kx, Ky), coarse_at<NC>(ec, mcx, mcy, Kx + 1, Ky)),
+                             cadd(coarse_at<NC>(ec, mcx, mcy, Kx, Ky + 1),
+                                  coarse_at<NC>(ec, mcx, mcy, Kx + 1, Ky + 1))));
+}
+
+// Row `row` of the coarsest solve u = A_c^{-1} f by one warp (FP64 inverse, FP64 sums).
+template <bool NC, class C>
+__device__ __forceinline__ void coarse_row(int nc, const cplx* __restrict__ Ainv, const C* __restrict__ f,
+                                           C* __restrict__ u, int row, int lane) {
+  cplx acc = cmk(0.0, 0.0);
+  const cplx* a = Ainv + (size_t)row * nc;
+  for (int c = lane; c < nc; c += 32) acc = cfma(__ldg(a + c), to_c128(ldm<NC>(f + c)), acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+  }
+  if (lane == 0) u[row] = CT<C>::make(acc.x, acc.y);
 }
 
 template <class C>
@@ -70,19 +160,7 @@ __global__ void __launch_bounds__(BX * BY) k_jacobi(StencilViewT<C> s, const C* 
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   if (i >= s.mx || j >= s.my) return;
-  const int p = j * s.mx + i;
-  C uc = __ldg(u_in + p);
-  if (s.rbox && i < s.ux && j < s.uy) {
-    C r = csub(__ldg(f + p), apply_op_rbox(s, u_in, i, j, uc));
-    const typename CT<C>::R di = ldre(s.Dinv, p);
-    C o;
-    o.x = fma(di, r.x, uc.x);
-    o.y = fma(di, r.y, uc.y);
-    u_out[p] = o;
-  } else {
-    C r = csub(__ldg(f + p), apply_op(s, u_in, i, j, uc));
-    u_out[p] = cfma(__ldg(s.Dinv + p), r, uc);
-  }
+  u_out[j * s.mx + i] = jacobi_pt<true>(s, u_in, f, i, j);
 }
 
 // First sweep from a zero initial guess: u = omega D^{-1} f.
@@ -93,7 +171,24 @@ __global__ void __launch_bounds__(256) k_jacobi_zero(long long n, const C* __res
   if (p < n) u_out[p] = cmul(__ldg(Dinv + p), __ldg(f + p));
 }
 
-// Deterministic block reduction of one double (fixed tree order).
+// Deterministic block reduction (fixed tree order): warp sums in the value's own
+// precision R, the per-warp totals summed in FP64 by thread 0.  For complex64 data this
+// keeps the FP64 pipe (1/64 of the FP32 rate here) out of the per-element work.
+template <int NT, class R>
+__device__ __forceinline__ double block_sum_r(R v, double* sh) {
+  const int t = threadIdx.x + threadIdx.y * blockDim.x;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((t & 31) == 0) sh[t >> 5] = (double)v;
+  __syncthreads();
+  double tot = 0.0;
+  if (t == 0) {
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) tot += sh[w];
+  }
+  return tot;
+}
+
 template <int NT>
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   const int t = threadIdx.x + threadIdx.y * blockDim.x;
@@ -116,69 +211,37 @@ __global__ void __launch_bounds__(BX * BY) k_residual(StencilViewT<C> s, const C
   __shared__ double sh[BX * BY / 32];
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
-  double n2 = 0.0;
+  typename CT<C>::R n2 = 0;
   if (i < s.mx && j < s.my) {
     const int p = j * s.mx + i;
-    C rv = csub(__ldg(f + p), apply_any(s, u, i, j, __ldg(u + p)));
+    C rv = residual_pt<true>(s, u, f, i, j);
     if (r) r[p] = rv;
-    n2 = (double)cabs2(rv);
+    n2 = cabs2(rv);
   }
   if (norm_part) {
-    double tot = block_sum<BX * BY>(n2, sh);
+    double tot = block_sum_r<BX * BY>(n2, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) norm_part[blockIdx.y * gridDim.x + blockIdx.x] = tot;
   }
 }
 
-// Full weighting 1/16 [1 2 1; 2 4 2; 1 2 1] onto the coincident nodes: coarse interior
-// (I, J) sits on fine interior (2I+1, 2J+1); all nine taps are interior nodes.
 template <class C>
 __global__ void __launch_bounds__(256) k_restrict(int mx, int mcx, int mcy, const C* __restrict__ r,
                                                   C* __restrict__ rc) {
-  typedef typename CT<C>::R R;
   const int I = blockIdx.x * 32 + threadIdx.x;
   const int J = blockIdx.y * 8 + threadIdx.y;
   if (I >= mcx || J >= mcy) return;
-  const int c = (2 * J + 1) * mx + (2 * I + 1);
-  C corners = cadd(cadd(__ldg(r + c - mx - 1), __ldg(r + c - mx + 1)),
-                   cadd(__ldg(r + c + mx - 1), __ldg(r + c + mx + 1)));
-  C edges = cadd(cadd(__ldg(r + c - 1), __ldg(r + c + 1)), cadd(__ldg(r + c - mx), __ldg(r + c + mx)));
-  C centre = __ldg(r + c);
-  C acc;
-  acc.x = fma(R(2), edges.x, fma(R(4), centre.x, corners.x));
-  acc.y = fma(R(2), edges.y, fma(R(4), centre.y, corners.y));
-  rc[J * mcx + I] = cscal(R(0.0625), acc);
-}
-
-template <class C>
-__device__ __forceinline__ C coarse_at(const C* __restrict__ ec, int mcx, int mcy, int K, int Kp) {
-  // coarse node (K, Kp), 0..mc+1; boundary nodes carry zero
-  return (K >= 1 && K <= mcx && Kp >= 1 && Kp <= mcy) ? __ldg(ec + (Kp - 1) * mcx + (K - 1))
-                                                       : CT<C>::make(0.0, 0.0);
+  rc[J * mcx + I] = restrict_pt<true>(mx, r, I, J);
 }
 
 // u += bilinear interpolation of the coarse correction (fine node k = i+1).
 template <class C>
 __global__ void __launch_bounds__(BX * BY) k_prolong_add(int mx, int my, int mcx, int mcy, const C* __restrict__ ec,
                                                          C* __restrict__ u) {
-  typedef typename CT<C>::R R;
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   if (i >= mx || j >= my) return;
-  const int kx = i + 1, ky = j + 1;
-  const int Kx = kx >> 1, Ky = ky >> 1;
-  C v;
-  if (!(kx & 1) && !(ky & 1)) {
-    v = coarse_at(ec, mcx, mcy, Kx, Ky);
-  } else if (!(ky & 1)) {
-    v = cscal(R(0.5), cadd(coarse_at(ec, mcx, mcy, Kx, Ky), coarse_at(ec, mcx, mcy, Kx + 1, Ky)));
-  } else if (!(kx & 1)) {
-    v = cscal(R(0.5), cadd(coarse_at(ec, mcx, mcy, Kx, Ky), coarse_at(ec, mcx, mcy, Kx, Ky + 1)));
-  } else {
-    v = cscal(R(0.25), cadd(cadd(coarse_at(ec, mcx, mcy, Kx, Ky), coarse_at(ec, mcx, mcy, Kx + 1, Ky)),
-                            cadd(coarse_at(ec, mcx, mcy, Kx, Ky + 1), coarse_at(ec, mcx, mcy, Kx + 1, Ky + 1))));
-  }
   const int p = j * mx + i;
-  u[p] = cadd(u[p], v);
+  u[p] = cadd(u[p], prolong_pt<true>(mcx, mcy, ec, i, j));
 }
 
 // Coarsest level: u = A_c^{-1} f with the FP64 dense inverse built at setup; one warp
@@ -187,17 +250,74 @@ template <class C>
 __global__ void __launch_bounds__(256) k_coarse_solve(int nc, const cplx* __restrict__ Ainv, const C* __restrict__ f,
                                                       C* __restrict__ u) {
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
   if (row >= nc) return;
-  cplx acc = cmk(0.0, 0.0);
-  const cplx* a = Ainv + (size_t)row * nc;
-  for (int c = lane; c < nc; c += 32) acc = cfma(__ldg(a + c), to_c128(__ldg(f + c)), acc);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
-    acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+  coarse_row<true>(nc, Ainv, f, u, row, threadIdx.x & 31);
+}
+
+// ---- fused coarse levels: the V-cycle below a size threshold in one CTA ----------
+// Levels 0..n-1 of `a` are consecutive multigrid levels ending at the coarsest.  The
+// kernel runs the same steps as the one-step kernels in the same order (pre-smoothing,
+// residual, restriction, ..., the dense coarsest solve, prolongation, post-smoothing)
+// with __syncthreads() between steps instead of kernel boundaries, so a V-cycle's
+// coarse tail costs one launch instead of six per level.  The result is left in lv[0].u.
+template <class C>
+__global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_constant__ TailArgs<C> a) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  C* cur[MGC_MAX_LEVELS];
+  C* oth[MGC_MAX_LEVELS];
+  for (int l = 0; l < a.n - 1; ++l) {
+    const TailLevel<C>& L = a.lv[l];
+    const int mx = L.sv.mx, np = L.sv.mx * L.sv.my;
+    C* c = L.u;
+    C* o = L.t;
+    bool zero = l == 0 ? a.zero_init != 0 : true;
+    for (int sw = 0; sw < a.nu1; ++sw) {
+      for (int p = tid; p < np; p += nth)
+        o[p] = zero ? cmul(__ldg(L.sv.Dinv + p), ldm<false>(L.f + p))
+                    : jacobi_pt<false>(L.sv, c, L.f, p % mx, p / mx);
+      zero = false;
+      C* x = c; c = o; o = x;
+      __syncthreads();
+    }
+    if (zero) {
+      for (int p = tid; p < np; p += nth) c[p] = CT<C>::make(0.0, 0.0);
+      __syncthreads();
+    }
+    for (int p = tid; p < np; p += nth) L.r[p] = residual_pt<false>(L.sv, c, L.f, p % mx, p / mx);
+    __syncthreads();
+    const TailLevel<C>& Lc = a.lv[l + 1];
+    const int mcx = Lc.sv.mx, ncp = Lc.sv.mx * Lc.sv.my;
+    for (int q = tid; q < ncp; q += nth) Lc.f[q] = restrict_pt<false>(mx, L.r, q % mcx, q / mcx);
+    __syncthreads();
+    cur[l] = c;
+    oth[l] = o;
   }
-  if (lane == 0) u[row] = CT<C>::make(acc.x, acc.y);
+  {
+    const TailLevel<C>& Lc = a.lv[a.n - 1];
+    for (int row = tid >> 5; row < a.nc; row += nth >> 5) coarse_row<false>(a.nc, a.Ainv, Lc.f, Lc.u, row, tid & 31);
+    __syncthreads();
+  }
+  const C* ec = a.lv[a.n - 1].u;
+  for (int l = a.n - 2; l >= 0; --l) {
+    const TailLevel<C>& L = a.lv[l];
+    const int mx = L.sv.mx, np = L.sv.mx * L.sv.my;
+    const int mcx = a.lv[l + 1].sv.mx, mcy = a.lv[l + 1].sv.my;
+    C* c = cur[l];
+    C* o = oth[l];
+    for (int p = tid; p < np; p += nth) c[p] = cadd(c[p], prolong_pt<false>(mcx, mcy, ec, p % mx, p / mx));
+    __syncthreads();
+    for (int sw = 0; sw < a.nu2; ++sw) {
+      for (int p = tid; p < np; p += nth) o[p] = jacobi_pt<false>(L.sv, c, L.f, p % mx, p / mx);
+      C* x = c; c = o; o = x;
+      __syncthreads();
+    }
+    cur[l] = c;
+    ec = c;
+  }
+  if (cur[0] != a.lv[0].u) {
+    const int np = a.lv[0].sv.mx * a.lv[0].sv.my;
+    for (int p = tid; p < np; p += nth) a.lv[0].u[p] = cur[0][p];
+  }
 }
 
 // Sum of n partials in a fixed order (one block), result to out[0]; skipped when
@@ -215,10 +335,10 @@ __global__ void __launch_bounds__(256) k_sum_partials(const double* __restrict__
 template <class C>
 __global__ void __launch_bounds__(256) k_norm2(const C* __restrict__ v, long long n, double* __restrict__ part) {
   __shared__ double sh[8];
-  double acc = 0.0;
+  typename CT<C>::R acc = 0;
   for (long long p = blockIdx.x * 256LL + threadIdx.x; p < n; p += (long long)gridDim.x * 256)
-    acc += (double)cabs2(__ldg(v + p));
-  double tot = block_sum<256>(acc, sh);
+    acc += cabs2(__ldg(v + p));
+  double tot = block_sum_r<256>(acc, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
@@ -228,15 +348,15 @@ __global__ void __launch_bounds__(BX * BY) k_apply(StencilViewT<C> s, const C* _
   __shared__ double sh[BX * BY / 32];
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
-  double n2 = 0.0;
+  typename CT<C>::R n2 = 0;
   if (i < s.mx && j < s.my) {
     const int p = j * s.mx + i;
-    C v = apply_any(s, x, i, j, __ldg(x + p));
+    C v = apply_any<true>(s, x, i, j, __ldg(x + p));
     y[p] = v;
-    n2 = (double)cabs2(v);
+    n2 = cabs2(v);
   }
   if (norm_part) {
-    double tot = block_sum<BX * BY>(n2, sh);
+    double tot = block_sum_r<BX * BY>(n2, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) norm_part[blockIdx.y * gridDim.x + blockIdx.x] = tot;
   }
 }
@@ -244,7 +364,10 @@ __global__ void __launch_bounds__(BX * BY) k_apply(StencilViewT<C> s, const C* _
 // y32 = (x64 * scale) rounded to complex64, scale = 1/sqrt(*norm2) (1 when norm2 is null).
 __global__ void __launch_bounds__(256) k_demote(long long n, const cplx* __restrict__ x, const double* __restrict__ norm2,
                                                 float2* __restrict__ y) {
-  const double s = norm2 ? (*norm2 > 0.0 ? 1.0 / sqrt(*norm2) : 0.0) : 1.0;
+  __shared__ double s_sh;
+  if (threadIdx.x == 0) s_sh = norm2 ? (*norm2 > 0.0 ? 1.0 / sqrt(*norm2) : 0.0) : 1.0;
+  __syncthreads();
+  const double s = s_sh;
   for (long long p = blockIdx.x * 256LL + threadIdx.x; p < n; p += (long long)gridDim.x * 256) {
     cplx v = __ldg(x + p);
     y[p] = make_float2((float)(s * v.x), (float)(s * v.y));
@@ -254,7 +377,10 @@ __global__ void __launch_bounds__(256) k_demote(long long n, const cplx* __restr
 // u64 += sqrt(*norm2) * e32 (the iterative-refinement update in FP64).
 __global__ void __launch_bounds__(256) k_promote_add(long long n, const float2* __restrict__ e,
                                                      const double* __restrict__ norm2, cplx* __restrict__ u) {
-  const double s = sqrt(*norm2);
+  __shared__ double s_sh;
+  if (threadIdx.x == 0) s_sh = sqrt(*norm2);
+  __syncthreads();
+  const double s = s_sh;
   for (long long p = blockIdx.x * 256LL + threadIdx.x; p < n; p += (long long)gridDim.x * 256) {
     float2 v = __ldg(e + p);
     cplx a = u[p];
@@ -330,6 +456,12 @@ cudaError_t launch_coarse_solve(int nc, const cplx* Ainv, const C* f, C* u, cuda
 }
 
 template <class C>
+cudaError_t launch_vcycle_tail(const TailArgs<C>& a, cudaStream_t st) {
+  k_vcycle_tail<C><<<1, TAIL_THREADS, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <class C>
 cudaError_t launch_apply(const StencilViewT<C>& s, const C* x, C* y, cudaStream_t st, double* norm_part) {
   k_apply<C><<<grid2(s.mx, s.my), dim3(BX, BY), 0, st>>>(s, x, y, norm_part);
   return cudaGetLastError();
@@ -350,6 +482,7 @@ cudaError_t launch_norm2(const C* v, long long n, double* part, int nblocks, cud
   template cudaError_t launch_restrict<C>(int, int, const C*, C*, cudaStream_t);                          \
   template cudaError_t launch_prolong_add<C>(int, int, const C*, C*, cudaStream_t);                       \
   template cudaError_t launch_coarse_solve<C>(int, const cplx*, const C*, C*, cudaStream_t);              \
+  template cudaError_t launch_vcycle_tail<C>(const TailArgs<C>&, cudaStream_t);                           \
   template cudaError_t launch_apply<C>(const StencilViewT<C>&, const C*, C*, cudaStream_t, double*);      \
   template cudaError_t launch_norm2<C>(const C*, long long, double*, int, cudaStream_t);
 MGC_INSTANTIATE(double2)

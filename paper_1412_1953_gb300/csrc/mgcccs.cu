@@ -34,6 +34,7 @@ struct mgcccs_handle {
   mgcccs_params p;
   cudaStream_t st;
   int L;
+  int tail64, tail32;      // first level of the fused coarse-level kernel (L: none)
   LevelBufs lv[MGC_MAX_LEVELS];
   int nc;
   cplx* Ainv;
@@ -159,6 +160,15 @@ void layout(mgcccs_handle* h, Carver& cv) {
   h->inner_rtol = p.inner_rtol > 0.0 ? p.inner_rtol : 1e-5;
   const LevelBufs& c = h->lv[L - 1];
   h->nc = c.mx * c.my;
+  // Fused coarse-level kernel (one CTA): from the first level with at most 64^2 nodes in
+  // complex64 (FP32 pipe), 16^2 in complex128 (the FP64 pipe of one SM is 1/152 of the
+  // GPU's, so larger FP64 levels stay on the one-step kernels).
+  h->tail64 = h->tail32 = L;
+  for (int l = L - 2; l >= 0; --l) {
+    const long long pts = (long long)h->lv[l].mx * h->lv[l].my;
+    if (pts <= 16 * 16) h->tail64 = l;
+    if (pts <= 64 * 64) h->tail32 = l;
+  }
   h->Ainv = cv.take<cplx>((size_t)h->nc * h->nc);
   h->aug = cv.take<cplx>(coarse_inverse_scratch(h->nc));
   const int nb = p.n_b, mx = h->lv[0].mx, my = h->lv[0].my;
@@ -206,8 +216,9 @@ void layout(mgcccs_handle* h, Carver& cv) {
     cc.rB = cv.take<cplx>((size_t)nb * mx);
     cc.eA = cv.take<cplx>((size_t)nb * my);
     cc.eB = cv.take<cplx>((size_t)nb * mx);
-    h->crA.r = cc.rA; h->crA.e = cc.eA;
-    h->crB.r = cc.rB; h->crB.e = cc.eB;
+    cc.eAc = cc.eA; cc.eBc = cc.eB;
+    h->crA.r = cc.rA; h->crA.e = cc.eA; h->crA.e32 = nullptr;
+    h->crB.r = cc.rB; h->crB.e = cc.eB; h->crB.e32 = nullptr;
     if (p.precision == 1) {
       h->phi32 = cv.take<float2>((size_t)nb * mx);
       h->vphi32 = cv.take<float2>((size_t)nb * my);
@@ -219,6 +230,11 @@ void layout(mgcccs_handle* h, Carver& cv) {
       c3.Px_part = cv.take<float2>((size_t)cc_tiles_x(mx) * nb * my);
       c3.Py_part = cv.take<float2>((size_t)cc_tiles_y(my) * nb * mx);
       c3.Px = cc.Px; c3.Py = cc.Py; c3.c = cc.c; c3.rA = cc.rA; c3.rB = cc.rB; c3.eA = cc.eA; c3.eB = cc.eB;
+      float2* eA32 = cv.take<float2>((size_t)nb * my);
+      float2* eB32 = cv.take<float2>((size_t)nb * mx);
+      c3.eAc = eA32; c3.eBc = eB32;
+      h->crA.e32 = eA32;
+      h->crB.e32 = eB32;
       c3.phi64 = h->phi; c3.vphi64 = h->vphi; c3.wvphi64 = h->wvphi;
     }
   }
@@ -436,10 +452,40 @@ const CCViewT<float2>& cc_view<float2>(mgcccs_handle* h) { return h->cc32; }
 
 // One V-cycle on level l.  `u` holds the initial guess unless zero_init; the result is
 // returned in *out (either u or the level's t buffer).
+template <class C> int tail_level(const mgcccs_handle* h);
+template <> int tail_level<cplx>(const mgcccs_handle* h) { return h->tail64; }
+template <> int tail_level<float2>(const mgcccs_handle* h) { return h->tail32; }
+
+// Levels l..L-1 in one launch of the fused coarse-level kernel; the result lands in u.
+template <class C>
+int vcycle_tail(mgcccs_handle* h, int l, C* u, const C* f, bool zero_init) {
+  TailArgs<C> a{};
+  a.n = h->L - l;
+  a.nu1 = h->p.nu1;
+  a.nu2 = h->p.nu2;
+  a.zero_init = zero_init ? 1 : 0;
+  a.nc = h->nc;
+  a.Ainv = h->Ainv;
+  for (int k = 0; k < a.n; ++k) {
+    LevelIO<C> b = level_io<C>(h, l + k);
+    a.lv[k].sv = *b.sv;
+    a.lv[k].u = k == 0 ? u : b.u;
+    a.lv[k].f = k == 0 ? const_cast<C*>(f) : b.f;
+    a.lv[k].t = b.t;
+    a.lv[k].r = b.r;
+  }
+  MGC_LAUNCH(launch_vcycle_tail(a, h->st));
+  return MGCCCS_OK;
+}
+
 template <class C>
 int vcycle_rec(mgcccs_handle* h, int l, C* u, const C* f, bool zero_init, C** out) {
   cudaStream_t st = h->st;
   LevelIO<C> b = level_io<C>(h, l);
+  if (l == tail_level<C>(h) && l < h->L - 1) {
+    *out = u;
+    return vcycle_tail<C>(h, l, u, f, zero_init);
+  }
   if (l == h->L - 1) {
     MGC_LAUNCH(launch_coarse_solve(h->nc, h->Ainv, f, u, st));
     *out = u;
@@ -573,15 +619,16 @@ int issue_arnoldi_step(mgcccs_handle* h, int j) {
   MGC_LAUNCH(launch_apply(s0, (const C*)zj, w, st, h->norm_part));
   MGC_LAUNCH(launch_sum_partials(h->norm_part, residual_norm_blocks(s0), h->norm_out + 3, st));
   // Gram-Schmidt, first pass: H(0:j, j) = V^H w ; w -= V H(0:j, j)
-  MGC_LAUNCH(launch_multidot(N, j + 1, (const C*)V, N, (const C*)w, h->dotpart, nb, (const int*)nullptr, st));
-  MGC_LAUNCH(launch_reduce_dots(nb, j + 1, h->dotpart, col, nullptr, st));
+  const int nbd = multidot_blocks(N, j + 1);
+  MGC_LAUNCH(launch_multidot(N, j + 1, (const C*)V, N, (const C*)w, h->dotpart, nbd, (const int*)nullptr, st));
+  MGC_LAUNCH(launch_reduce_dots(nbd, j + 1, h->dotpart, col, nullptr, st));
   MGC_LAUNCH(launch_multiaxpy(N, j + 1, (const C*)V, N, col, -1.0, w, h->norm_part, nb, (const int*)nullptr, st));
   MGC_LAUNCH(launch_sum_partials(h->norm_part, nb, h->norm_out + 1, st));
   // second pass only when the first one cancelled |w| by more than 1e3;
   // the corrections are added into H(0:j, j)
   MGC_LAUNCH(launch_dgks(h->norm_out + 3, h->norm_out + 1, h->gate, st));
-  MGC_LAUNCH(launch_multidot(N, j + 1, (const C*)V, N, (const C*)w, h->dotpart, nb, (const int*)h->gate, st));
-  MGC_LAUNCH(launch_reduce_dots(nb, j + 1, h->dotpart, h->hc, col, st));
+  MGC_LAUNCH(launch_multidot(N, j + 1, (const C*)V, N, (const C*)w, h->dotpart, nbd, (const int*)h->gate, st));
+  MGC_LAUNCH(launch_reduce_dots(nbd, j + 1, h->dotpart, h->hc, col, st));
   MGC_LAUNCH(launch_multiaxpy(N, j + 1, (const C*)V, N, h->hc, -1.0, w, h->norm_part, nb, (const int*)h->gate, st));
   MGC_LAUNCH(launch_sum_partials(h->norm_part, nb, h->norm_out + 1, st, h->gate));
   MGC_LAUNCH(launch_scale_by_norm(N, (const C*)w, w, h->norm_out + 1, col + j + 1, nb, st));
