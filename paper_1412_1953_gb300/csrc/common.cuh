@@ -182,7 +182,8 @@ template <class C>
 cudaError_t launch_multiaxpy(long long n, int k, const C* V, long long ld, const cplx* coef, double sgn,
                              C* w, double* norm_part, int nblk, const int* gate, cudaStream_t st,
                              const int* dk = nullptr);
-cudaError_t launch_dgks(const double* before, const double* after, int* gate, cudaStream_t st);
+cudaError_t launch_dgks(const double* before, const double* after, int* gate, cudaStream_t st,
+                        cudaGraphConditionalHandle hd = 0, int* fired = nullptr);
 template <class C>
 cudaError_t launch_scale_by_norm(long long n, const C* w, C* out, const double* norm2, cplx* store,
                                  int nblk, cudaStream_t st);
@@ -201,6 +202,7 @@ struct SolveCtl {
   int max_iter, mixed, m, pad0;
   int steps, k, j, cycles, outer, status;
   double rr, scale, target;
+  int dgks, pad1;      // second Gram-Schmidt passes run
 };
 cudaError_t launch_outer_control(SolveCtl* c, const double* rn2, cudaGraphConditionalHandle h_outer,
                                  cudaGraphConditionalHandle h_cycle, cudaGraphConditionalHandle h_inner,

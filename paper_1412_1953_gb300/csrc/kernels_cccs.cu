@@ -171,82 +171,117 @@ __global__ void __launch_bounds__(256) k_cc_split(int nb, int mx, int my, const 
 // root Y = P X; backward, Y_j = P_j X_j - Q_j Y_{j-s} - R_j Y_{j+s} on the rows each
 // level eliminated.  Each system is solved by one thread-block cluster of CR_CLUSTER
 // CTAs (cluster 0: channel A along y, cluster 1: channel B along x); every level is one
-// pass over (row, component) pairs split across the cluster, separated by cluster
-// barriers (release/acquire at cluster scope orders the global-memory traffic).
+// pass over (row, component) pairs split across the cluster.  Levels are separated by
+// split cluster barriers: every thread arrives (release) after its stores, loads the
+// read-only factor rows of its first item of the next level, and only then waits
+// (acquire), so the factor loads overlap the barrier.  Arrive and wait sit outside all
+// data-dependent branches, so each warp executes them convergently.  The sums of each update are formed as
+// independent length-nb dot products, which keeps the dependent FP64 chain short.
 constexpr int CR_CLUSTER = 8;
 constexpr int CR_THREADS = 256;
 
-__device__ __forceinline__ void cluster_barrier() {
+__device__ __forceinline__ void cluster_arrive() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
   asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
+template <int NB>
+__device__ __forceinline__ void load_row(cplx (&d)[NB], const cplx* __restrict__ src) {
+#pragma unroll
+  for (int p = 0; p < NB; ++p) d[p] = __ldg(src + p);
+}
+
+template <int NB>
+__device__ __forceinline__ cplx dot_row(const cplx (&a)[NB], const cplx* x) {
+  cplx s = cmul(a[0], x[0]);
+#pragma unroll
+  for (int p = 1; p < NB; ++p) s = cfma(a[p], x[p], s);
+  return s;
+}
+
+template <int NB>
 __global__ void __cluster_dims__(CR_CLUSTER, 1, 1) __launch_bounds__(CR_THREADS)
 k_channel_solve(CRSystem SA, CRSystem SB) {
   const int sys = blockIdx.x / CR_CLUSTER;
   const int rank = blockIdx.x % CR_CLUSTER;
-  const CRSystem& S = sys == 0 ? SA : SB;
-  const int nb = S.nb, nb2 = nb * nb, M = S.M, q = S.q, m = S.m;
+  const CRSystem S = sys == 0 ? SA : SB;
+  constexpr int nb2 = NB * NB;
+  const int M = S.M, q = S.q, m = S.m;
   const int t0 = rank * CR_THREADS + threadIdx.x, nt = CR_CLUSTER * CR_THREADS;
-  for (int idx = t0; idx < (M + 2) * nb; idx += nt) {
-    const int row = idx / nb, comp = idx % nb;
+  for (int idx = t0; idx < (M + 2) * NB; idx += nt) {
+    const int row = idx / NB, comp = idx % NB;
     S.X[idx] = (row >= 1 && row <= m) ? S.r[comp * m + row - 1] : cmk(0.0, 0.0);
     S.Y[idx] = cmk(0.0, 0.0);
   }
-  cluster_barrier();
+  cluster_arrive();
+  cplx fa[NB], fb[NB], fc[NB];
   for (int l = 1; l < q; ++l) {
     const int s = 1 << (l - 1);
     const int nk = (1 << (q - l)) - 1;
     const int off = cr_fwd_offset(q, l);
-    for (int w = t0; w < nk * nb; w += nt) {
-      const int t = w / nb + 1, comp = w % nb, i = 2 * s * t;
-      const cplx* al = S.alpha + (size_t)(off + t - 1) * nb2 + comp * nb;
-      const cplx* ga = S.gamma + (size_t)(off + t - 1) * nb2 + comp * nb;
-      cplx acc = S.X[i * nb + comp];
-      for (int p = 0; p < nb; ++p) {
-        acc = cfms(al[p], S.X[(i - s) * nb + p], acc);
-        acc = cfms(ga[p], S.X[(i + s) * nb + p], acc);
-      }
-      S.X[i * nb + comp] = acc;
+    const int total = nk * NB;
+    // factor rows of this thread's first item, loaded while the barrier completes
+    if (t0 < total) {
+      const size_t fo = (size_t)(off + t0 / NB) * nb2 + (t0 % NB) * NB;
+      load_row<NB>(fa, S.alpha + fo);
+      load_row<NB>(fb, S.gamma + fo);
     }
-    cluster_barrier();
+    cluster_wait();                           // previous level complete
+    for (int w = t0; w < total; w += nt) {
+      const int t = w / NB + 1, comp = w % NB, i = 2 * s * t;
+      if (w != t0) {
+        const size_t fo = (size_t)(off + t - 1) * nb2 + comp * NB;
+        load_row<NB>(fa, S.alpha + fo);
+        load_row<NB>(fb, S.gamma + fo);
+      }
+      const cplx a = dot_row<NB>(fa, S.X + (size_t)(i - s) * NB);
+      const cplx g = dot_row<NB>(fb, S.X + (size_t)(i + s) * NB);
+      S.X[i * NB + comp] = csub(S.X[i * NB + comp], cadd(a, g));
+    }
+    cluster_arrive();
   }
   const int root = 1 << (q - 1);
-  if (t0 < nb) {
-    const cplx* Pr = S.P + (size_t)root * nb2 + t0 * nb;
-    cplx acc = cmk(0.0, 0.0);
-    for (int p = 0; p < nb; ++p) acc = cfma(Pr[p], S.X[root * nb + p], acc);
-    S.Y[root * nb + t0] = acc;
-  }
-  cluster_barrier();
+  if (t0 < NB) load_row<NB>(fa, S.P + (size_t)root * nb2 + t0 * NB);
+  cluster_wait();
+  if (t0 < NB) S.Y[root * NB + t0] = dot_row<NB>(fa, S.X + (size_t)root * NB);
+  cluster_arrive();
   for (int l = q - 1; l >= 1; --l) {
     const int s = 1 << (l - 1);
     const int ne = 1 << (q - l);           // odd multiples of s in 1..M
-    for (int w = t0; w < ne * nb; w += nt) {
-      const int j = s * (2 * (w / nb) + 1), comp = w % nb;
-      const cplx* Pj = S.P + (size_t)j * nb2 + comp * nb;
-      const cplx* Qj = S.Q + (size_t)j * nb2 + comp * nb;
-      const cplx* Rj = S.R + (size_t)j * nb2 + comp * nb;
-      cplx acc = cmk(0.0, 0.0);
-      for (int p = 0; p < nb; ++p) {
-        acc = cfma(Pj[p], S.X[j * nb + p], acc);
-        acc = cfms(Qj[p], S.Y[(j - s) * nb + p], acc);
-        acc = cfms(Rj[p], S.Y[(j + s) * nb + p], acc);
-      }
-      S.Y[j * nb + comp] = acc;
+    const int total = ne * NB;
+    if (t0 < total) {
+      const size_t fo = (size_t)(s * (2 * (t0 / NB) + 1)) * nb2 + (t0 % NB) * NB;
+      load_row<NB>(fa, S.P + fo);
+      load_row<NB>(fb, S.Q + fo);
+      load_row<NB>(fc, S.R + fo);
     }
-    cluster_barrier();
+    cluster_wait();
+    for (int w = t0; w < total; w += nt) {
+      const int j = s * (2 * (w / NB) + 1), comp = w % NB;
+      if (w != t0) {
+        const size_t fo = (size_t)j * nb2 + comp * NB;
+        load_row<NB>(fa, S.P + fo);
+        load_row<NB>(fb, S.Q + fo);
+        load_row<NB>(fc, S.R + fo);
+      }
+      const cplx px = dot_row<NB>(fa, S.X + (size_t)j * NB);
+      const cplx qy = dot_row<NB>(fb, S.Y + (size_t)(j - s) * NB);
+      const cplx ry = dot_row<NB>(fc, S.Y + (size_t)(j + s) * NB);
+      S.Y[j * NB + comp] = csub(px, cadd(qy, ry));
+    }
+    cluster_arrive();
   }
-  for (int idx = t0; idx < m * nb; idx += nt) {
+  cluster_wait();
+  for (int idx = t0; idx < m * NB; idx += nt) {
     const int comp = idx / m, k = idx % m;
-    const cplx v = S.Y[(k + 1) * nb + comp];
+    const cplx v = S.Y[(k + 1) * NB + comp];
     S.e[idx] = v;
     if (S.e32) S.e32[idx] = make_float2((float)v.x, (float)v.y);
   }
 }
 
-// u += sum_m phi_m(x) e^A_m(y) + sum_l e^B_l(x) vphi_l(y) in the element precision
-// (the channel solutions arrive already rounded to it).
 template <int NB, class C>
 __global__ void __launch_bounds__(256) k_cccs_correct(int mx, int my, const C* __restrict__ phi,
                                                       const C* __restrict__ vphi, const C* __restrict__ eA,
@@ -319,7 +354,17 @@ int cr_levels(int m) {
 }
 
 cudaError_t launch_channel_solve(const CRSystem& A, const CRSystem& B, cudaStream_t st) {
-  k_channel_solve<<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B);
+  switch (A.nb) {
+    case 1: k_channel_solve<1><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
+    case 2: k_channel_solve<2><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
+    case 3: k_channel_solve<3><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
+    case 4: k_channel_solve<4><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
+    case 5: k_channel_solve<5><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
+    case 6: k_channel_solve<6><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
+    case 7: k_channel_solve<7><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
+    case 8: k_channel_solve<8><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

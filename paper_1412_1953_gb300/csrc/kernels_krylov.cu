@@ -126,32 +126,44 @@ __global__ void __launch_bounds__(NT) k_scale_by_norm(long long n, const C* __re
 // [conj(c) conj(s); -s c] with c = a/rho, s = b/rho, rho = sqrt(|a|^2 + |b|^2).
 __global__ void k_givens(int j, int m, cplx* __restrict__ H, cplx* __restrict__ cs, cplx* __restrict__ sn,
                          cplx* __restrict__ g, double* __restrict__ est) {
-  if (threadIdx.x != 0) return;
-  cplx* col = H + (size_t)j * (m + 1);
-  for (int i = 0; i < j; ++i) {
-    cplx x = col[i], y = col[i + 1];
-    cplx c = cs[i], s = sn[i];
-    col[i] = cadd(cmul(cmk(c.x, -c.y), x), cmul(cmk(s.x, -s.y), y));
-    col[i + 1] = csub(cmul(c, y), cmul(s, x));
+  // the column and the earlier rotations are staged in shared memory by the warp, so the
+  // sequential chain of thread 0 waits on no global load
+  __shared__ cplx col[MGC_MAX_RESTART + 1], rc[MGC_MAX_RESTART], rs[MGC_MAX_RESTART];
+  cplx* colg = H + (size_t)j * (m + 1);
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) col[i] = colg[i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    rc[i] = cs[i];
+    rs[i] = sn[i];
   }
-  cplx a = col[j], b = col[j + 1];
-  double rho = sqrt(cabs2(a) + cabs2(b));
-  cplx c, s;
-  if (rho == 0.0) {
-    c = cmk(1.0, 0.0);
-    s = cmk(0.0, 0.0);
-  } else {
-    c = cscal(1.0 / rho, a);
-    s = cscal(1.0 / rho, b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < j; ++i) {
+      cplx x = col[i], y = col[i + 1];
+      cplx c = rc[i], s = rs[i];
+      col[i] = cadd(cmul(cmk(c.x, -c.y), x), cmul(cmk(s.x, -s.y), y));
+      col[i + 1] = csub(cmul(c, y), cmul(s, x));
+    }
+    cplx a = col[j], b = col[j + 1];
+    double rho = sqrt(cabs2(a) + cabs2(b));
+    cplx c, s;
+    if (rho == 0.0) {
+      c = cmk(1.0, 0.0);
+      s = cmk(0.0, 0.0);
+    } else {
+      c = cscal(1.0 / rho, a);
+      s = cscal(1.0 / rho, b);
+    }
+    cs[j] = c;
+    sn[j] = s;
+    col[j] = cmk(rho, 0.0);
+    col[j + 1] = cmk(0.0, 0.0);
+    cplx gj = g[j];
+    g[j + 1] = cneg(cmul(s, gj));
+    g[j] = cmul(cmk(c.x, -c.y), gj);
+    *est = cmod(g[j + 1]);
   }
-  cs[j] = c;
-  sn[j] = s;
-  col[j] = cmk(rho, 0.0);
-  col[j + 1] = cmk(0.0, 0.0);
-  cplx gj = g[j];
-  g[j + 1] = cneg(cmul(s, gj));
-  g[j] = cmul(cmk(c.x, -c.y), gj);
-  *est = cmod(g[j + 1]);
+  __syncthreads();
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) colg[i] = col[i];
 }
 
 // Back substitution R y = g[0..k-1] with the rotated (upper-triangular) H.
@@ -171,8 +183,17 @@ __global__ void k_hess_solve(int k, int m, const cplx* __restrict__ H, const cpl
 // pass never loses more than about 1e3 ulps of orthogonality.  (The classic threshold
 // 1/sqrt(2) fires on almost every step here: with a good preconditioner A M^{-1} v_j is
 // close to v_j and a first pass routinely removes half of |w|^2, harmlessly.)
-__global__ void k_dgks(const double* __restrict__ before, const double* __restrict__ after, int* __restrict__ gate) {
-  if (threadIdx.x == 0) *gate = (*after < 1e-6 * *before) ? 1 : 0;
+// In a device-driven solve graph the decision also steers the conditional node that
+// holds the second pass (use_cond), and fired passes are counted.
+__global__ void k_dgks(const double* __restrict__ before, const double* __restrict__ after, int* __restrict__ gate,
+                       cudaGraphConditionalHandle hd, int use_cond, int* __restrict__ fired) {
+  if (threadIdx.x != 0) return;
+  const int second = (*after < 1e-6 * *before) ? 1 : 0;
+  *gate = second;
+  if (use_cond) {
+    cudaGraphSetConditional(hd, (unsigned)second);
+    if (second) *fired += 1;
+  }
 }
 
 // ---- device-driven GMRES: stop tests that steer the conditional nodes of a solve graph.
@@ -305,8 +326,9 @@ cudaError_t launch_hess_solve(int k, int m, const cplx* H, const cplx* g, cplx* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_dgks(const double* before, const double* after, int* gate, cudaStream_t st) {
-  k_dgks<<<1, 32, 0, st>>>(before, after, gate);
+cudaError_t launch_dgks(const double* before, const double* after, int* gate, cudaStream_t st,
+                        cudaGraphConditionalHandle hd, int* fired) {
+  k_dgks<<<1, 32, 0, st>>>(before, after, gate, hd, fired ? 1 : 0, fired);
   return cudaGetLastError();
 }
 

@@ -260,54 +260,93 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int nc, const cplx* __rest
 // residual, restriction, ..., the dense coarsest solve, prolongation, post-smoothing)
 // with __syncthreads() between steps instead of kernel boundaries, so a V-cycle's
 // coarse tail costs one launch instead of six per level.  The result is left in lv[0].u.
+// Stages of the fused kernel: one pass over a level's nodes by the whole CTA.  The
+// restrict-qualified pointers and the unrolled loop let each thread keep the loads of
+// several nodes in flight (one node per thread would leave the SM waiting on L2).
+template <class C>
+__device__ __forceinline__ void tail_jacobi(const StencilViewT<C>& s, const C* __restrict__ u, C* __restrict__ o,
+                                            const C* __restrict__ f, bool zero) {
+  const int mx = s.mx, np = s.mx * s.my;
+  if (zero) {
+#pragma unroll 4
+    for (int p = threadIdx.x; p < np; p += TAIL_THREADS) o[p] = cmul(__ldg(s.Dinv + p), ldm<false>(f + p));
+  } else {
+#pragma unroll 4
+    for (int p = threadIdx.x; p < np; p += TAIL_THREADS) o[p] = jacobi_pt<false>(s, u, f, p % mx, p / mx);
+  }
+}
+
+template <class C>
+__device__ __forceinline__ void tail_residual(const StencilViewT<C>& s, const C* __restrict__ u,
+                                              const C* __restrict__ f, C* __restrict__ r) {
+  const int mx = s.mx, np = s.mx * s.my;
+#pragma unroll 4
+  for (int p = threadIdx.x; p < np; p += TAIL_THREADS) r[p] = residual_pt<false>(s, u, f, p % mx, p / mx);
+}
+
+template <class C>
+__device__ __forceinline__ void tail_restrict(int mx, int mcx, int mcy, const C* __restrict__ r, C* __restrict__ fc) {
+  const int ncp = mcx * mcy;
+#pragma unroll 4
+  for (int q = threadIdx.x; q < ncp; q += TAIL_THREADS) fc[q] = restrict_pt<false>(mx, r, q % mcx, q / mcx);
+}
+
+template <class C>
+__device__ __forceinline__ void tail_prolong(int mx, int my, int mcx, int mcy, const C* __restrict__ ec,
+                                             C* __restrict__ u) {
+  const int np = mx * my;
+#pragma unroll 4
+  for (int p = threadIdx.x; p < np; p += TAIL_THREADS) u[p] = cadd(u[p], prolong_pt<false>(mcx, mcy, ec, p % mx, p / mx));
+}
+
+// ---- fused coarse levels: the V-cycle below a size threshold in one CTA ----------
+// Levels 0..n-1 of `a` are consecutive multigrid levels ending at the coarsest.  The
+// kernel runs the same steps as the one-step kernels in the same order (pre-smoothing,
+// residual, restriction, ..., the dense coarsest solve, prolongation, post-smoothing)
+// with __syncthreads() between steps instead of kernel boundaries, so a V-cycle's
+// coarse tail costs one launch instead of six per level.  The result is left in lv[0].u.
 template <class C>
 __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_constant__ TailArgs<C> a) {
-  const int tid = threadIdx.x, nth = blockDim.x;
+  const int tid = threadIdx.x;
   C* cur[MGC_MAX_LEVELS];
   C* oth[MGC_MAX_LEVELS];
   for (int l = 0; l < a.n - 1; ++l) {
     const TailLevel<C>& L = a.lv[l];
-    const int mx = L.sv.mx, np = L.sv.mx * L.sv.my;
     C* c = L.u;
     C* o = L.t;
     bool zero = l == 0 ? a.zero_init != 0 : true;
     for (int sw = 0; sw < a.nu1; ++sw) {
-      for (int p = tid; p < np; p += nth)
-        o[p] = zero ? cmul(__ldg(L.sv.Dinv + p), ldm<false>(L.f + p))
-                    : jacobi_pt<false>(L.sv, c, L.f, p % mx, p / mx);
+      tail_jacobi(L.sv, c, o, L.f, zero);
       zero = false;
       C* x = c; c = o; o = x;
       __syncthreads();
     }
     if (zero) {
-      for (int p = tid; p < np; p += nth) c[p] = CT<C>::make(0.0, 0.0);
+      for (int p = tid; p < L.sv.mx * L.sv.my; p += TAIL_THREADS) c[p] = CT<C>::make(0.0, 0.0);
       __syncthreads();
     }
-    for (int p = tid; p < np; p += nth) L.r[p] = residual_pt<false>(L.sv, c, L.f, p % mx, p / mx);
+    tail_residual(L.sv, c, L.f, L.r);
     __syncthreads();
-    const TailLevel<C>& Lc = a.lv[l + 1];
-    const int mcx = Lc.sv.mx, ncp = Lc.sv.mx * Lc.sv.my;
-    for (int q = tid; q < ncp; q += nth) Lc.f[q] = restrict_pt<false>(mx, L.r, q % mcx, q / mcx);
+    tail_restrict(L.sv.mx, a.lv[l + 1].sv.mx, a.lv[l + 1].sv.my, L.r, a.lv[l + 1].f);
     __syncthreads();
     cur[l] = c;
     oth[l] = o;
   }
   {
     const TailLevel<C>& Lc = a.lv[a.n - 1];
-    for (int row = tid >> 5; row < a.nc; row += nth >> 5) coarse_row<false>(a.nc, a.Ainv, Lc.f, Lc.u, row, tid & 31);
+    for (int row = tid >> 5; row < a.nc; row += TAIL_THREADS >> 5)
+      coarse_row<false>(a.nc, a.Ainv, Lc.f, Lc.u, row, tid & 31);
     __syncthreads();
   }
   const C* ec = a.lv[a.n - 1].u;
   for (int l = a.n - 2; l >= 0; --l) {
     const TailLevel<C>& L = a.lv[l];
-    const int mx = L.sv.mx, np = L.sv.mx * L.sv.my;
-    const int mcx = a.lv[l + 1].sv.mx, mcy = a.lv[l + 1].sv.my;
     C* c = cur[l];
     C* o = oth[l];
-    for (int p = tid; p < np; p += nth) c[p] = cadd(c[p], prolong_pt<false>(mcx, mcy, ec, p % mx, p / mx));
+    tail_prolong(L.sv.mx, L.sv.my, a.lv[l + 1].sv.mx, a.lv[l + 1].sv.my, ec, c);
     __syncthreads();
     for (int sw = 0; sw < a.nu2; ++sw) {
-      for (int p = tid; p < np; p += nth) o[p] = jacobi_pt<false>(L.sv, c, L.f, p % mx, p / mx);
+      tail_jacobi(L.sv, c, o, L.f, false);
       C* x = c; c = o; o = x;
       __syncthreads();
     }
@@ -316,7 +355,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_const
   }
   if (cur[0] != a.lv[0].u) {
     const int np = a.lv[0].sv.mx * a.lv[0].sv.my;
-    for (int p = tid; p < np; p += nth) a.lv[0].u[p] = cur[0][p];
+    for (int p = tid; p < np; p += TAIL_THREADS) a.lv[0].u[p] = cur[0][p];
   }
 }
 

@@ -80,7 +80,8 @@ struct mgcccs_handle {
   cudaGraphExec_t solve_exec[4];             // device-driven solve graphs by (u, f) pointers
   const void *solve_u[4], *solve_f[4];
   int solve_next;
-  long long sg_pro, sg_outer, sg_cycle, sg_step;
+  long long sg_pro, sg_outer, sg_cycle, sg_step, sg_dgks;
+  cudaGraphConditionalHandle dgks_cond[MGC_MAX_RESTART];
   long long launches;
 };
 
@@ -572,6 +573,53 @@ int read_double(mgcccs_handle* h, const double* dev, double* out) {
   return MGCCCS_OK;
 }
 
+// ---- stream-capture helpers for graphs with conditional nodes
+
+struct CaptureGuard {          // ends a capture on error so that the stream stays usable
+  cudaStream_t s;
+  bool open;
+  ~CaptureGuard() {
+    if (open) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(s, &g);
+    }
+  }
+};
+
+int capture_into(CaptureGuard& cg, cudaGraph_t g) {
+  MGC_CUDA(cudaStreamBeginCaptureToGraph(cg.s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cg.open = true;
+  return MGCCCS_OK;
+}
+
+int capture_end(CaptureGuard& cg) {
+  cudaGraph_t g = nullptr;
+  cg.open = false;
+  MGC_CUDA(cudaStreamEndCapture(cg.s, &g));
+  return MGCCCS_OK;
+}
+
+// Appends a conditional node after the capture's current tail; returns its body graphs.
+int add_conditional(cudaStream_t s, cudaGraphConditionalHandle hd, cudaGraphConditionalNodeType type,
+                    unsigned size, cudaGraph_t** bodies) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  MGC_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive) return MGCCCS_ECUDA;
+  cudaGraphNodeParams prm{};
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = hd;
+  prm.conditional.type = type;
+  prm.conditional.size = size;
+  cudaGraphNode_t node;
+  MGC_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, nd, &prm));
+  *bodies = prm.conditional.phGraph_out;
+  MGC_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return MGCCCS_OK;
+}
+
 // z = M^{-1} r: one V-cycle from zero, then the CCCS.
 template <class C>
 int precond(mgcccs_handle* h, C* z, const C* r) {
@@ -626,11 +674,34 @@ int issue_arnoldi_step(mgcccs_handle* h, int j) {
   MGC_LAUNCH(launch_sum_partials(h->norm_part, nb, h->norm_out + 1, st));
   // second pass only when the first one cancelled |w| by more than 1e3;
   // the corrections are added into H(0:j, j)
-  MGC_LAUNCH(launch_dgks(h->norm_out + 3, h->norm_out + 1, h->gate, st));
-  MGC_LAUNCH(launch_multidot(N, j + 1, (const C*)V, N, (const C*)w, h->dotpart, nbd, (const int*)h->gate, st));
-  MGC_LAUNCH(launch_reduce_dots(nbd, j + 1, h->dotpart, h->hc, col, st));
-  MGC_LAUNCH(launch_multiaxpy(N, j + 1, (const C*)V, N, h->hc, -1.0, w, h->norm_part, nb, (const int*)h->gate, st));
-  MGC_LAUNCH(launch_sum_partials(h->norm_part, nb, h->norm_out + 1, st, h->gate));
+  if (h->device_loop) {
+    // device-driven graph: the pass is the body of a conditional node, so it costs no
+    // launch when it does not run
+    MGC_LAUNCH(launch_dgks(h->norm_out + 3, h->norm_out + 1, h->gate, st, h->dgks_cond[j], &h->ctl->dgks));
+    cudaGraph_t* body = nullptr;
+    int rc2 = add_conditional(st, h->dgks_cond[j], cudaGraphCondTypeIf, 1, &body);
+    if (rc2) return rc2;
+    CaptureGuard cg{h->gst[0], false};
+    rc2 = capture_into(cg, body[0]);
+    if (rc2) return rc2;
+    cudaStream_t bs = h->gst[0];
+    const long long b0 = h->launches;
+    MGC_LAUNCH(launch_multidot(N, j + 1, (const C*)V, N, (const C*)w, h->dotpart, nbd, (const int*)nullptr, bs));
+    MGC_LAUNCH(launch_reduce_dots(nbd, j + 1, h->dotpart, h->hc, col, bs));
+    MGC_LAUNCH(launch_multiaxpy(N, j + 1, (const C*)V, N, h->hc, -1.0, w, h->norm_part, nb, (const int*)nullptr, bs));
+    MGC_LAUNCH(launch_sum_partials(h->norm_part, nb, h->norm_out + 1, bs));
+    h->sg_dgks = h->launches - b0;
+    h->launches = b0;
+    rc2 = capture_end(cg);
+    if (rc2) return rc2;
+  } else {
+    MGC_LAUNCH(launch_dgks(h->norm_out + 3, h->norm_out + 1, h->gate, st));
+    MGC_LAUNCH(launch_multidot(N, j + 1, (const C*)V, N, (const C*)w, h->dotpart, nbd, (const int*)h->gate, st));
+    MGC_LAUNCH(launch_reduce_dots(nbd, j + 1, h->dotpart, h->hc, col, st));
+    MGC_LAUNCH(launch_multiaxpy(N, j + 1, (const C*)V, N, h->hc, -1.0, w, h->norm_part, nb, (const int*)h->gate,
+                                st));
+    MGC_LAUNCH(launch_sum_partials(h->norm_part, nb, h->norm_out + 1, st, h->gate));
+  }
   MGC_LAUNCH(launch_scale_by_norm(N, (const C*)w, w, h->norm_out + 1, col + j + 1, nb, st));
   MGC_LAUNCH(launch_givens(j, m, h->Hh, h->cs, h->sn, h->g, h->norm_out + 2, st));
   if (!h->device_loop)
@@ -966,51 +1037,6 @@ int batch_solve_impl(std::vector<BatchItem>& items, double rtol, int max_iter) {
 //
 // Several problems are independent root branches of one graph (batched solves).
 
-struct CaptureGuard {          // ends a capture on error so that the stream stays usable
-  cudaStream_t s;
-  bool open;
-  ~CaptureGuard() {
-    if (open) {
-      cudaGraph_t g = nullptr;
-      cudaStreamEndCapture(s, &g);
-    }
-  }
-};
-
-int capture_into(CaptureGuard& cg, cudaGraph_t g) {
-  MGC_CUDA(cudaStreamBeginCaptureToGraph(cg.s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  cg.open = true;
-  return MGCCCS_OK;
-}
-
-int capture_end(CaptureGuard& cg) {
-  cudaGraph_t g = nullptr;
-  cg.open = false;
-  MGC_CUDA(cudaStreamEndCapture(cg.s, &g));
-  return MGCCCS_OK;
-}
-
-// Appends a conditional node after the capture's current tail; returns its body graphs.
-int add_conditional(cudaStream_t s, cudaGraphConditionalHandle hd, cudaGraphConditionalNodeType type,
-                    unsigned size, cudaGraph_t** bodies) {
-  cudaStreamCaptureStatus cs;
-  cudaGraph_t g = nullptr;
-  const cudaGraphNode_t* deps = nullptr;
-  size_t nd = 0;
-  MGC_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
-  if (cs != cudaStreamCaptureStatusActive) return MGCCCS_ECUDA;
-  cudaGraphNodeParams prm{};
-  prm.type = cudaGraphNodeTypeConditional;
-  prm.conditional.handle = hd;
-  prm.conditional.type = type;
-  prm.conditional.size = size;
-  cudaGraphNode_t node;
-  MGC_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, nd, &prm));
-  *bodies = prm.conditional.phGraph_out;
-  MGC_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-  return MGCCCS_OK;
-}
-
 template <class C>
 int append_steps(mgcccs_handle* h, cudaGraph_t* bodies, cudaStream_t s) {
   cudaStream_t orig = h->st;
@@ -1114,6 +1140,7 @@ int append_solve(mgcccs_handle* h, cplx* u, const cplx* f, cudaGraph_t G) {
     rc = capture_end(cg);
     if (rc) return rc;
   }
+  for (int j = 0; j < m; ++j) MGC_CUDA(cudaGraphConditionalHandleCreate(&h->dgks_cond[j], G, 0, 0));
   int rc = h->mixed ? append_steps<float2>(h, b4, h->gst[1]) : append_steps<cplx>(h, b4, h->gst[1]);
   if (rc) return rc;
   h->sg_step += 1;                     // + k_step_control
@@ -1157,7 +1184,7 @@ int fetch_ctl(mgcccs_handle* h, cudaStream_t st) {
 int finish_ctl(mgcccs_handle* h, cplx* u, int* iters, double* relres) {
   const SolveCtl& c = *h->ctl_host;
   h->launches += h->sg_pro + (long long)c.outer * h->sg_outer + (long long)c.cycles * h->sg_cycle +
-                 (long long)c.steps * h->sg_step;
+                 (long long)c.steps * h->sg_step + (long long)c.dgks * h->sg_dgks;
   if (iters) *iters = c.steps;
   if (relres) *relres = c.rr;
   switch (c.status) {
