@@ -162,6 +162,21 @@ int mgcccs_solve(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f, double rtol,
 int mgcccs_solve_host(mgcccs_t h, mgcccs_c128* u_host, const mgcccs_c128* f_host,
                       double rtol, int max_iter, int* iters, double* relres);
 
+/* All eigenvalues of the fine-grid 1D Hamiltonian H1 = -1/2 d^2/dz^2 + V of one axis
+ * (axis 0: x with V1, axis 1: y with V2) on the ECS grid, the matrix whose n_b
+ * smallest-real-part eigenpairs are the bound states (Eq. (9), Sec. 4.1).
+ * method 0: Ehrlich-Aberth simultaneous iteration with divide-and-conquer starting
+ * values (what setup uses); method 1: the one-thread FP64 root-free QR (setup's
+ * fallback; its rotations are complex-orthogonal, not unitary, and on this
+ * non-Hermitian matrix part of its large-modulus spectrum is inaccurate, while the
+ * smallest-real-part eigenvalues that setup takes from it are right).  lam_host: host
+ * array of (n-1) entries, unordered.  Synchronous.
+ * EBREAKDOWN if the chosen method did not converge. */
+int mgcccs_axis_spectrum(mgcccs_t h, int axis, int method, mgcccs_c128* lam_host);
+/* Number of axes whose bound-state eigenvalues needed the QR fallback in the last
+ * setup of h (0 normally), or -1 for a NULL handle. */
+int mgcccs_eig_fallbacks(mgcccs_t h);
+
 /* Solve drivers for mgcccs_set_solve_driver. */
 enum { MGCCCS_DRIVER_GRAPH = 0, MGCCCS_DRIVER_HOST = 1 };
 int mgcccs_set_solve_driver(mgcccs_t h, int driver);

@@ -291,10 +291,18 @@ cudaError_t launch_setup_diag(int mx, int my, int stride, int fine_mx, const cpl
                               cplx* D, cplx* Dinv, int* status, cudaStream_t st);
 size_t coarse_inverse_scratch(int nc);                       // complex entries of aug
 cudaError_t launch_coarse_inverse(const StencilView& s, cplx* aug, cplx* Ainv, int* status, cudaStream_t st);
+// eig: all m eigenvalues when already computed (eig_aberth), else null (FP64 QR inside)
 cudaError_t launch_bound_states(int m, const cplx* west, const cplx* east, const cplx* diag, const cplx* v,
                                 const cplx* w, int nb, cplx* lam, cplx* phi, cplx* scratch, int* status,
-                                cudaStream_t st);
+                                cudaStream_t st, const cplx* eig = nullptr);
 size_t bound_states_scratch(int m, int nb);
+// kernels_eig.cu: all eigenvalues of diag + v with squared off-diagonals east_k west_{k+1}
+// into out[m]; *ok false when the iteration did not converge (the caller falls back to QR).
+size_t eig_scratch_entries(int m);
+cudaError_t eig_aberth(int m, const cplx* west, const cplx* east, const cplx* diag, const cplx* v, cplx* scratch,
+                       cplx* out, bool* ok, cudaStream_t st);
+cudaError_t launch_qr_spectrum(int m, const cplx* west, const cplx* east, const cplx* diag, const cplx* v,
+                               cplx* scratch, cplx* out, int* status, cudaStream_t st);
 cudaError_t launch_weight_states(int m, int nb, const cplx* w, const cplx* phi, cplx* wphi, cudaStream_t st);
 cudaError_t launch_channel_potentials(int mx, int my, int nb, const cplx* wphi, const cplx* phi,
                                       const cplx* wvphi, const cplx* vphi, const cplx* v12,

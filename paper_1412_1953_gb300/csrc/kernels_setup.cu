@@ -343,7 +343,8 @@ __global__ void __launch_bounds__(32) k_bound_states(int m, const cplx* __restri
                                                      const cplx* __restrict__ east, const cplx* __restrict__ diag,
                                                      const cplx* __restrict__ v, const cplx* __restrict__ w, int nb,
                                                      cplx* __restrict__ lam, cplx* __restrict__ phi,
-                                                     cplx* __restrict__ scratch, int* status) {
+                                                     cplx* __restrict__ scratch, int* status,
+                                                     const cplx* __restrict__ eig) {
   __shared__ cplx sel[MGC_MAX_NB];
   __shared__ cplx fin_l[MGC_MAX_NB];
   __shared__ int ok;
@@ -351,12 +352,21 @@ __global__ void __launch_bounds__(32) k_bound_states(int m, const cplx* __restri
   cplx* d = scratch;            // m
   cplx* e2 = scratch + m;       // m
   if (q == 0) {
-    // squared off-diagonals of the symmetric form: e_k^2 = east_k * west_{k+1}
-    for (int k = 0; k < m; ++k) {
-      d[k] = cadd(diag[k], v[k]);
-      e2[k] = (k + 1 < m) ? cmul(east[k], west[k + 1]) : cmk(0.0, 0.0);
+    if (eig) {
+      // all eigenvalues given (the Ehrlich-Aberth iteration of kernels_eig.cu)
+      for (int k = 0; k < m; ++k) {
+        d[k] = eig[k];
+        e2[k] = cmk(0.0, 0.0);
+      }
+      ok = 1;
+    } else {
+      // squared off-diagonals of the symmetric form: e_k^2 = east_k * west_{k+1}
+      for (int k = 0; k < m; ++k) {
+        d[k] = cadd(diag[k], v[k]);
+        e2[k] = (k + 1 < m) ? cmul(east[k], west[k + 1]) : cmk(0.0, 0.0);
+      }
+      ok = qr_rootfree_eigenvalues(m, d, e2) ? 1 : 0;
     }
-    ok = qr_rootfree_eigenvalues(m, d, e2) ? 1 : 0;
     if (ok) {
       // the nb eigenvalues with the smallest real part, ascending (ties: lower index)
       for (int s = 0; s < nb; ++s) {
@@ -424,6 +434,24 @@ __global__ void __launch_bounds__(32) k_bound_states(int m, const cplx* __restri
       for (int b = a + 1; b < nb; ++b)
         if (cabs1(csub(fin_l[a], fin_l[b])) <= 1e-10 * fmax(1.0, cabs1(fin_l[a]))) atomicOr(status, MGC_ST_EIG);
   }
+}
+
+// All eigenvalues by the FP64 root-free QR (one thread), for the spectrum entry point.
+__global__ void k_qr_spectrum(int m, const cplx* __restrict__ west, const cplx* __restrict__ east,
+                              const cplx* __restrict__ diag, const cplx* __restrict__ v, cplx* __restrict__ scratch,
+                              cplx* __restrict__ out, int* status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  cplx* d = scratch;
+  cplx* e2 = scratch + m;
+  for (int k = 0; k < m; ++k) {
+    d[k] = cadd(diag[k], v[k]);
+    e2[k] = (k + 1 < m) ? cmul(east[k], west[k + 1]) : cmk(0.0, 0.0);
+  }
+  if (!qr_rootfree_eigenvalues(m, d, e2)) {
+    atomicOr(status, MGC_ST_EIG);
+    return;
+  }
+  for (int k = 0; k < m; ++k) out[k] = d[k];
 }
 
 __global__ void k_weight_states(int m, int nb, const cplx* __restrict__ w, const cplx* __restrict__ phi,
@@ -643,8 +671,14 @@ size_t bound_states_scratch(int m, int nb) {
 
 cudaError_t launch_bound_states(int m, const cplx* west, const cplx* east, const cplx* diag, const cplx* v,
                                 const cplx* w, int nb, cplx* lam, cplx* phi, cplx* scratch, int* status,
-                                cudaStream_t st) {
-  k_bound_states<<<1, 32, 0, st>>>(m, west, east, diag, v, w, nb, lam, phi, scratch, status);
+                                cudaStream_t st, const cplx* eig) {
+  k_bound_states<<<1, 32, 0, st>>>(m, west, east, diag, v, w, nb, lam, phi, scratch, status, eig);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qr_spectrum(int m, const cplx* west, const cplx* east, const cplx* diag, const cplx* v,
+                               cplx* scratch, cplx* out, int* status, cudaStream_t st) {
+  k_qr_spectrum<<<1, 32, 0, st>>>(m, west, east, diag, v, scratch, out, status);
   return cudaGetLastError();
 }
 

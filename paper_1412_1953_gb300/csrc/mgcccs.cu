@@ -44,6 +44,9 @@ struct mgcccs_handle {
   CRSystem crA, crB;       // channel A (along y, x bound states), channel B (along x)
   cplx* cr_scratch;
   cplx* eig_scratch;
+  cplx *eig_ab, *eig_vals;  // Ehrlich-Aberth scratch and its eigenvalues (one axis at a time)
+  cplx *v1c, *v2c;          // copies of V1, V2 (the spectrum entry point reads them)
+  int eig_fallbacks;        // axes whose eigenvalues needed the QR fallback
   CCView cc;
   double* norm_part;
   int norm_nparts;
@@ -172,6 +175,13 @@ void layout(mgcccs_handle* h, Carver& cv) {
   }
   h->Ainv = cv.take<cplx>((size_t)h->nc * h->nc);
   h->aug = cv.take<cplx>(coarse_inverse_scratch(h->nc));
+  {
+    const int mm = h->lv[0].mx > h->lv[0].my ? h->lv[0].mx : h->lv[0].my;
+    h->v1c = cv.take<cplx>(h->lv[0].mx);
+    h->v2c = cv.take<cplx>(h->lv[0].my);
+    h->eig_ab = cv.take<cplx>(eig_scratch_entries(mm));
+    h->eig_vals = cv.take<cplx>(mm);
+  }
   const int nb = p.n_b, mx = h->lv[0].mx, my = h->lv[0].my;
   h->nb = nb;
   if (nb > 0) {
@@ -309,11 +319,28 @@ int read_status(mgcccs_handle* h) {
   return MGCCCS_OK;
 }
 
+// Bound states of one axis (Eq. (9)): all eigenvalues by the Ehrlich-Aberth iteration
+// (parallel; the one-thread FP64 QR when it does not converge), then selection and
+// refinement in k_bound_states.
+int axis_states(mgcccs_handle* h, int m, const cplx* west, const cplx* east, const cplx* diag, const cplx* v,
+                const cplx* w, cplx* lam, cplx* phi) {
+  bool ok = false;
+  MGC_CUDA(eig_aberth(m, west, east, diag, v, h->eig_ab, h->eig_vals, &ok, h->st));
+  h->launches += 4;
+  if (!ok) h->eig_fallbacks += 1;
+  MGC_LAUNCH(launch_bound_states(m, west, east, diag, v, w, h->nb, lam, phi, h->eig_scratch, h->status, h->st,
+                                 ok ? h->eig_vals : nullptr));
+  return MGCCCS_OK;
+}
+
 int do_setup(mgcccs_handle* h, const cplx* v1, const cplx* v2, const cplx* v12, const cplx* lam_in = nullptr,
              const cplx* phi_in = nullptr, const cplx* mu_in = nullptr, const cplx* vphi_in = nullptr) {
   const mgcccs_params& p = h->p;
   cudaStream_t st = h->st;
   MGC_CUDA(cudaMemsetAsync(h->status, 0, 4 * sizeof(int), st));
+  MGC_CUDA(cudaMemcpyAsync(h->v1c, v1, sizeof(cplx) * h->lv[0].mx, cudaMemcpyDeviceToDevice, st));
+  MGC_CUDA(cudaMemcpyAsync(h->v2c, v2, sizeof(cplx) * h->lv[0].my, cudaMemcpyDeviceToDevice, st));
+  h->eig_fallbacks = 0;
   const int fine_mx = h->lv[0].mx;
   for (int l = 0; l < h->L; ++l) {
     LevelBufs& b = h->lv[l];
@@ -366,8 +393,8 @@ int do_setup(mgcccs_handle* h, const cplx* v1, const cplx* v2, const cplx* v12, 
       MGC_CUDA(cudaMemcpyAsync(h->phi, phi_in, sizeof(cplx) * nb * b.mx, cudaMemcpyDeviceToDevice, st));
       MGC_CUDA(cudaMemcpyAsync(h->vphi, vphi_in, sizeof(cplx) * nb * b.my, cudaMemcpyDeviceToDevice, st));
     } else {
-      MGC_LAUNCH(launch_bound_states(b.mx, b.west_x, b.east_x, b.diag_x, v1, b.w_x, nb, h->lam, h->phi,
-                                     h->eig_scratch, h->status, st));
+      int rc = axis_states(h, b.mx, b.west_x, b.east_x, b.diag_x, v1, b.w_x, h->lam, h->phi);
+      if (rc) return rc;
       // the y eigenproblem is the x one when both axes and potentials coincide (square TP grids)
       bool same = p.nx == p.ny && p.Lx == p.Ly && p.R0x == p.R0y;
       if (same) {
@@ -382,8 +409,8 @@ int do_setup(mgcccs_handle* h, const cplx* v1, const cplx* v2, const cplx* v12, 
         MGC_CUDA(cudaMemcpyAsync(h->mu, h->lam, sizeof(cplx) * nb, cudaMemcpyDeviceToDevice, st));
         MGC_CUDA(cudaMemcpyAsync(h->vphi, h->phi, sizeof(cplx) * nb * b.mx, cudaMemcpyDeviceToDevice, st));
       } else {
-        MGC_LAUNCH(launch_bound_states(b.my, b.west_y, b.east_y, b.diag_y, v2, b.w_y, nb, h->mu, h->vphi,
-                                       h->eig_scratch, h->status, st));
+        rc = axis_states(h, b.my, b.west_y, b.east_y, b.diag_y, v2, b.w_y, h->mu, h->vphi);
+        if (rc) return rc;
       }
     }
     MGC_LAUNCH(launch_weight_states(b.mx, nb, b.w_x, h->phi, h->wphi, st));
@@ -1523,6 +1550,33 @@ int mgcccs_batch_solve(mgcccs_t* handles, int count, mgcccs_c128* const* u, cons
   }
   return worst;
 }
+
+int mgcccs_axis_spectrum(mgcccs_t h, int axis, int method, mgcccs_c128* lam_host) {
+  if (!h || !lam_host || (axis != 0 && axis != 1) || (method != 0 && method != 1)) return MGCCCS_EINVAL;
+  const LevelBufs& b = h->lv[0];
+  const int m = axis == 0 ? b.mx : b.my;
+  const cplx* west = axis == 0 ? b.west_x : b.west_y;
+  const cplx* east = axis == 0 ? b.east_x : b.east_y;
+  const cplx* diag = axis == 0 ? b.diag_x : b.diag_y;
+  const cplx* v = axis == 0 ? h->v1c : h->v2c;
+  if (method == 0) {
+    bool ok = false;
+    MGC_CUDA(eig_aberth(m, west, east, diag, v, h->eig_ab, h->eig_vals, &ok, h->st));
+    if (!ok) return MGCCCS_EBREAKDOWN;
+  } else {
+    MGC_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), h->st));
+    MGC_LAUNCH(launch_qr_spectrum(m, west, east, diag, v, h->eig_ab, h->eig_vals, h->status, h->st));
+    int st = 0;
+    MGC_CUDA(cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    MGC_CUDA(cudaStreamSynchronize(h->st));
+    if (st) return MGCCCS_EBREAKDOWN;
+  }
+  MGC_CUDA(cudaMemcpyAsync(lam_host, h->eig_vals, sizeof(cplx) * m, cudaMemcpyDeviceToHost, h->st));
+  MGC_CUDA(cudaStreamSynchronize(h->st));
+  return MGCCCS_OK;
+}
+
+int mgcccs_eig_fallbacks(mgcccs_t h) { return h ? h->eig_fallbacks : -1; }
 
 int mgcccs_set_solve_driver(mgcccs_t h, int driver) {
   if (!h || (driver != MGCCCS_DRIVER_GRAPH && driver != MGCCCS_DRIVER_HOST)) return MGCCCS_EINVAL;

@@ -62,6 +62,8 @@ _SIGS = {
     "mgcccs_solve_host": (_i, [_vp, _vp, _vp, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
     "mgcccs_precond_apply": (_i, [_vp, _vp, _vp]),
     "mgcccs_set_solve_driver": (_i, [_vp, _i]),
+    "mgcccs_axis_spectrum": (_i, [_vp, _i, _i, _vp]),
+    "mgcccs_eig_fallbacks": (_i, [_vp]),
     "mgcccs_batch_create": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp),
                                  ctypes.POINTER(_vp), _vp]),
     "mgcccs_batch_run": (_i, [_vp, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d), ctypes.POINTER(_i)]),
@@ -323,6 +325,17 @@ class Solver:
         _check(lib().mgcccs_get_bound_states(self.h, lam.ctypes.data, phi.data_ptr(), mu.ctypes.data,
                                              vphi.data_ptr()), "mgcccs_get_bound_states")
         return lam, phi, mu, vphi
+
+    def axis_spectrum(self, axis: int = 0, method: int = 0) -> np.ndarray:
+        """All eigenvalues of the fine-grid H1 of one axis (0: x, 1: y); method 0 is the
+        Ehrlich-Aberth iteration setup uses, 1 the FP64 QR."""
+        n = self.mx if axis == 0 else self.my
+        out = np.zeros(n, dtype=np.complex128)
+        _check(lib().mgcccs_axis_spectrum(self.h, int(axis), int(method), out.ctypes.data), "mgcccs_axis_spectrum")
+        return out
+
+    def eig_fallbacks(self) -> int:
+        return int(lib().mgcccs_eig_fallbacks(self.h))
 
     def launch_count(self) -> int:
         return int(lib().mgcccs_launch_count(self.h))
