@@ -207,9 +207,17 @@ def measured_peaks():
 
 
 def kernel_source_sha():
+    """Hash of the source text that defines the fine-level complex128 k_jacobi launch: the
+    per-node helpers it calls and the kernel itself (edits elsewhere in the file do not
+    change the kernel, so they keep its committed ncu counters valid)."""
+    src = open(os.path.join(ROOT, "paper_1412_1953_gb300", "csrc", "kernels_mg.cu")).read()
+    a = src.index("__device__ __forceinline__ T ldm(")
+    b = src.index("template <bool NC, class C>\n__device__ __forceinline__ C residual_pt(")
+    k = src.index("__launch_bounds__(BX * BY) k_jacobi(")
+    e = src.index("\n}\n", k)
     h = hashlib.sha256()
-    for f in ("kernels_mg.cu",):
-        h.update(open(os.path.join(ROOT, "paper_1412_1953_gb300", "csrc", f), "rb").read())
+    h.update(src[a:b].encode())
+    h.update(src[k:e].encode())
     return h.hexdigest()[:16]
 
 
