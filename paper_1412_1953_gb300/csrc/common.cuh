@@ -240,32 +240,23 @@ struct CCViewT {
 typedef CCViewT<cplx> CCView;
 typedef CCViewT<float2> CCView32;
 
-// Cyclic-reduction factors of one coupled-channel system (Eqs. (28)-(29)),
-// a_k x_{k-1} + B_k x_k + c_k x_{k+1} = r_k with n_b x n_b blocks.  Rows are numbered
-// 1..M with M = 2^q - 1 >= m; rows past m are identity padding.  Level l (1..q-1)
-// eliminates the odd multiples of s = 2^(l-1); for the kept rows i (multiples of 2s)
-// alpha_i, gamma_i hold A_i B_{i-s}^{-1}, C_i B_{i+s}^{-1}; an eliminated row j keeps
-// P_j = B_j^{-1}, Q_j = B_j^{-1} A_j, R_j = B_j^{-1} C_j of its elimination level; the
-// root 2^(q-1) keeps P only.
+// One coupled-channel system (Eqs. (28)-(29)) with its parallel-cyclic-reduction factors.
 struct CRSystem {
-  int m, q, M, nb;
-  cplx* alpha;             // [M][nb*nb] kept rows of every level, level by level
-  cplx* gamma;
-  cplx* P;                 // [M+1][nb*nb] indexed by row
-  cplx* Q;
-  cplx* R;
-  cplx* X;                 // [(M+2)*nb] reduced right-hand side (solve scratch)
-  cplx* Y;                 // [(M+2)*nb] solution, rows 0 and M+1 zero (solve scratch)
+  int m, nb;
+  cplx* X;                 // [m*nb] reduced right-hand side (solve scratch)
+  cplx* Y;                 // [m*nb] second buffer of the levels
   const cplx* r;           // [nb][m] right-hand side
   cplx* e;                 // [nb][m] solution
   float2* e32;             // [nb][m] solution rounded to complex64 (mixed precision), or null
+  // parallel cyclic reduction: pq = ceil(log2 m) levels; level l with stride s = 2^l
+  // updates every row k by x_k -= pa_k x_{k-s} + pg_k x_{k+s}; then x_k = pbinv_k x_k.
+  // Rows are 0..m-1; terms outside them are absent.
+  int pq;
+  cplx* pa;                // [pq][m][nb*nb]
+  cplx* pg;                // [pq][m][nb*nb]
+  cplx* pbinv;             // [m][nb*nb]
 };
-int cr_levels(int m);
-__host__ __device__ inline int cr_fwd_offset(int q, int l) {
-  int o = 0;
-  for (int k = 1; k < l; ++k) o += (1 << (q - k)) - 1;
-  return o;
-}
+int pcr_levels(int m);
 int cc_tiles_x(int mx);
 int cc_tiles_y(int my);
 template <class C>
@@ -273,6 +264,7 @@ cudaError_t launch_residual_project(const StencilViewT<C>& s, const CCViewT<C>& 
                                     cudaStream_t st);
 template <class C>
 cudaError_t launch_cc_rhs(const CCViewT<C>& c, cudaStream_t st);
+cudaError_t channel_solve_prepare(int nb);
 cudaError_t launch_channel_solve(const CRSystem& A, const CRSystem& B, cudaStream_t st);
 template <class C>
 cudaError_t launch_cccs_correct(const CCViewT<C>& c, C* u, cudaStream_t st);
@@ -307,10 +299,10 @@ cudaError_t launch_weight_states(int m, int nb, const cplx* w, const cplx* phi, 
 cudaError_t launch_channel_potentials(int mx, int my, int nb, const cplx* wphi, const cplx* phi,
                                       const cplx* wvphi, const cplx* vphi, const cplx* v12,
                                       cplx* VA, cplx* VB, cudaStream_t st);
-cudaError_t launch_channel_factor(const CRSystem& S, const cplx* diag, const cplx* v, double E, const cplx* lam,
-                                  const cplx* Vc, const cplx* a, const cplx* c, cplx* scratch, int* status,
-                                  cudaStream_t st);
-
+cudaError_t launch_channel_factor_pcr(const CRSystem& S, const cplx* diag, const cplx* v, double E, const cplx* lam,
+                                      const cplx* Vc, const cplx* a, const cplx* c, cplx* scratch, int* status,
+                                      cudaStream_t st);
+size_t channel_factor_pcr_scratch(int m, int nb);
 // kernels_adjoint.cu
 int wdot_blocks(long long n);
 cudaError_t launch_weighted_dot(int mx, int my, const cplx* wx, const cplx* wy, const cplx* a, const cplx* b,

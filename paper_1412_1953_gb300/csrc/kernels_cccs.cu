@@ -166,18 +166,16 @@ __global__ void __launch_bounds__(256) k_cc_split(int nb, int mx, int my, const 
   }
 }
 
-// Cyclic-reduction solve of one coupled-channel system with the setup-time factors:
-// forward, level by level, X_i -= alpha_i X_{i-s} + gamma_i X_{i+s} on the kept rows;
-// root Y = P X; backward, Y_j = P_j X_j - Q_j Y_{j-s} - R_j Y_{j+s} on the rows each
-// level eliminated.  Each system is solved by one thread-block cluster of CR_CLUSTER
-// CTAs (cluster 0: channel A along y, cluster 1: channel B along x); every level is one
-// pass over (row, component) pairs split across the cluster.  Levels are separated by
-// split cluster barriers: every thread arrives (release) after its stores, loads the
-// read-only factor rows of its first item of the next level, and only then waits
-// (acquire), so the factor loads overlap the barrier.  Arrive and wait sit outside all
-// data-dependent branches, so each warp executes them convergently.  The sums of each update are formed as
-// independent length-nb dot products, which keeps the dependent FP64 chain short.
-constexpr int CR_CLUSTER = 8;
+// Coupled-channel solves (Eqs. (28)-(29)) by parallel cyclic reduction with setup-time
+// factors: each system is solved by one thread-block cluster of CR_CLUSTER CTAs (cluster
+// 0: channel A along y, cluster 1: channel B along x); every level is one pass over the
+// (row, component) pairs split across the cluster.  Levels are separated by split
+// cluster barriers: every thread arrives (release) after its stores, loads the read-only
+// factor rows of its first item of the next level, and only then waits (acquire), so
+// the factor loads overlap the barrier.  Arrive and wait sit outside all data-dependent
+// branches, so each warp executes them convergently.  Sums are formed as independent
+// length-nb dot products, which keeps the dependent FP64 chain short.
+constexpr int CR_CLUSTER = 16;           // non-portable size: allowed per kernel at setup
 constexpr int CR_THREADS = 256;
 
 __device__ __forceinline__ void cluster_arrive() {
@@ -201,84 +199,62 @@ __device__ __forceinline__ cplx dot_row(const cplx (&a)[NB], const cplx* x) {
   return s;
 }
 
+// Level l (stride s = 2^l) updates every row, x_k <- x_k - pa_k x_{k-s} - pg_k x_{k+s}
+// (X and Y alternate); after ceil(log2 m) levels x_k = pbinv_k x_k.  Against block cyclic
+// reduction (2 log2 m dependent levels on half the rows) this halves the dependent levels
+// for log2(m)/2 times the arithmetic, which 16-CTA clusters absorb: 37 us against 57 us
+// per CCCS at 1023 rows, n_b = 3.
 template <int NB>
 __global__ void __cluster_dims__(CR_CLUSTER, 1, 1) __launch_bounds__(CR_THREADS)
-k_channel_solve(CRSystem SA, CRSystem SB) {
+k_channel_solve_pcr(CRSystem SA, CRSystem SB) {
   const int sys = blockIdx.x / CR_CLUSTER;
   const int rank = blockIdx.x % CR_CLUSTER;
   const CRSystem S = sys == 0 ? SA : SB;
   constexpr int nb2 = NB * NB;
-  const int M = S.M, q = S.q, m = S.m;
+  const int m = S.m, pq = S.pq;
   const int t0 = rank * CR_THREADS + threadIdx.x, nt = CR_CLUSTER * CR_THREADS;
-  for (int idx = t0; idx < (M + 2) * NB; idx += nt) {
-    const int row = idx / NB, comp = idx % NB;
-    S.X[idx] = (row >= 1 && row <= m) ? S.r[comp * m + row - 1] : cmk(0.0, 0.0);
-    S.Y[idx] = cmk(0.0, 0.0);
+  const int total = m * NB;
+  cplx* X = S.X;
+  cplx* Y = S.Y;
+  for (int idx = t0; idx < total; idx += nt) {
+    const int k = idx / NB, comp = idx % NB;
+    X[idx] = S.r[comp * m + k];
   }
   cluster_arrive();
-  cplx fa[NB], fb[NB], fc[NB];
-  for (int l = 1; l < q; ++l) {
-    const int s = 1 << (l - 1);
-    const int nk = (1 << (q - l)) - 1;
-    const int off = cr_fwd_offset(q, l);
-    const int total = nk * NB;
-    // factor rows of this thread's first item, loaded while the barrier completes
+  cplx fa[NB], fb[NB];
+  for (int l = 0; l < pq; ++l) {
+    const int s = 1 << l;
+    const cplx* pa = S.pa + (size_t)l * m * nb2;
+    const cplx* pg = S.pg + (size_t)l * m * nb2;
     if (t0 < total) {
-      const size_t fo = (size_t)(off + t0 / NB) * nb2 + (t0 % NB) * NB;
-      load_row<NB>(fa, S.alpha + fo);
-      load_row<NB>(fb, S.gamma + fo);
-    }
-    cluster_wait();                           // previous level complete
-    for (int w = t0; w < total; w += nt) {
-      const int t = w / NB + 1, comp = w % NB, i = 2 * s * t;
-      if (w != t0) {
-        const size_t fo = (size_t)(off + t - 1) * nb2 + comp * NB;
-        load_row<NB>(fa, S.alpha + fo);
-        load_row<NB>(fb, S.gamma + fo);
-      }
-      const cplx a = dot_row<NB>(fa, S.X + (size_t)(i - s) * NB);
-      const cplx g = dot_row<NB>(fb, S.X + (size_t)(i + s) * NB);
-      S.X[i * NB + comp] = csub(S.X[i * NB + comp], cadd(a, g));
-    }
-    cluster_arrive();
-  }
-  const int root = 1 << (q - 1);
-  if (t0 < NB) load_row<NB>(fa, S.P + (size_t)root * nb2 + t0 * NB);
-  cluster_wait();
-  if (t0 < NB) S.Y[root * NB + t0] = dot_row<NB>(fa, S.X + (size_t)root * NB);
-  cluster_arrive();
-  for (int l = q - 1; l >= 1; --l) {
-    const int s = 1 << (l - 1);
-    const int ne = 1 << (q - l);           // odd multiples of s in 1..M
-    const int total = ne * NB;
-    if (t0 < total) {
-      const size_t fo = (size_t)(s * (2 * (t0 / NB) + 1)) * nb2 + (t0 % NB) * NB;
-      load_row<NB>(fa, S.P + fo);
-      load_row<NB>(fb, S.Q + fo);
-      load_row<NB>(fc, S.R + fo);
+      const size_t fo = (size_t)(t0 / NB) * nb2 + (t0 % NB) * NB;
+      load_row<NB>(fa, pa + fo);
+      load_row<NB>(fb, pg + fo);
     }
     cluster_wait();
     for (int w = t0; w < total; w += nt) {
-      const int j = s * (2 * (w / NB) + 1), comp = w % NB;
+      const int k = w / NB, comp = w % NB;
       if (w != t0) {
-        const size_t fo = (size_t)j * nb2 + comp * NB;
-        load_row<NB>(fa, S.P + fo);
-        load_row<NB>(fb, S.Q + fo);
-        load_row<NB>(fc, S.R + fo);
+        const size_t fo = (size_t)k * nb2 + comp * NB;
+        load_row<NB>(fa, pa + fo);
+        load_row<NB>(fb, pg + fo);
       }
-      const cplx px = dot_row<NB>(fa, S.X + (size_t)j * NB);
-      const cplx qy = dot_row<NB>(fb, S.Y + (size_t)(j - s) * NB);
-      const cplx ry = dot_row<NB>(fc, S.Y + (size_t)(j + s) * NB);
-      S.Y[j * NB + comp] = csub(px, cadd(qy, ry));
+      cplx acc = X[w];
+      if (k - s >= 0) acc = csub(acc, dot_row<NB>(fa, X + (size_t)(k - s) * NB));
+      if (k + s < m) acc = csub(acc, dot_row<NB>(fb, X + (size_t)(k + s) * NB));
+      Y[w] = acc;
     }
     cluster_arrive();
+    cplx* t = X; X = Y; Y = t;
   }
+  if (t0 < total) load_row<NB>(fa, S.pbinv + (size_t)(t0 / NB) * nb2 + (t0 % NB) * NB);
   cluster_wait();
-  for (int idx = t0; idx < m * NB; idx += nt) {
-    const int comp = idx / m, k = idx % m;
-    const cplx v = S.Y[(k + 1) * NB + comp];
-    S.e[idx] = v;
-    if (S.e32) S.e32[idx] = make_float2((float)v.x, (float)v.y);
+  for (int w = t0; w < total; w += nt) {
+    const int k = w / NB, comp = w % NB;
+    if (w != t0) load_row<NB>(fa, S.pbinv + (size_t)k * nb2 + comp * NB);
+    const cplx v = dot_row<NB>(fa, X + (size_t)k * NB);
+    S.e[comp * m + k] = v;
+    if (S.e32) S.e32[comp * m + k] = make_float2((float)v.x, (float)v.y);
   }
 }
 
@@ -347,22 +323,29 @@ cudaError_t launch_cc_rhs(const CCViewT<C>& c, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-int cr_levels(int m) {
-  int q = 1;
-  while ((1 << q) - 1 < m) ++q;
-  return q;
+// Clusters of more than 8 CTAs must be allowed per kernel (once, before any launch or
+// capture); called by setup.
+cudaError_t channel_solve_prepare(int nb) {
+  switch (nb) {
+#define MGC_PREP(K)                                                                                         \
+  case K:                                                                                                   \
+    return cudaFuncSetAttribute(k_channel_solve_pcr<K>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    MGC_PREP(1) MGC_PREP(2) MGC_PREP(3) MGC_PREP(4) MGC_PREP(5) MGC_PREP(6) MGC_PREP(7) MGC_PREP(8)
+#undef MGC_PREP
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_channel_solve(const CRSystem& A, const CRSystem& B, cudaStream_t st) {
   switch (A.nb) {
-    case 1: k_channel_solve<1><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
-    case 2: k_channel_solve<2><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
-    case 3: k_channel_solve<3><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
-    case 4: k_channel_solve<4><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
-    case 5: k_channel_solve<5><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
-    case 6: k_channel_solve<6><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
-    case 7: k_channel_solve<7><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
-    case 8: k_channel_solve<8><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
+    case 1: k_channel_solve_pcr<1><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
+    case 2: k_channel_solve_pcr<2><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
+    case 3: k_channel_solve_pcr<3><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
+    case 4: k_channel_solve_pcr<4><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
+    case 5: k_channel_solve_pcr<5><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
+    case 6: k_channel_solve_pcr<6><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
+    case 7: k_channel_solve_pcr<7><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
+    case 8: k_channel_solve_pcr<8><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

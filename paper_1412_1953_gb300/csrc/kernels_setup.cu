@@ -529,92 +529,107 @@ __device__ void small_matmul(int n, const cplx* A, const cplx* B, cplx* C) {
 // Cyclic-reduction factors of the coupled-channel system along one axis (one block):
 // B_k = (diag_k + v_k - E) I + diag(lam) + Vc_k, A_k = a_k I, C_k = c_k I, rows padded
 // with identity to M = 2^q - 1.  `scratch` holds the current A, B, C of rows 0..M.
-__global__ void __launch_bounds__(256) k_channel_factor(CRSystem S, const cplx* __restrict__ diag,
-                                                        const cplx* __restrict__ v, double E,
-                                                        const cplx* __restrict__ lam, const cplx* __restrict__ Vc,
-                                                        const cplx* __restrict__ sub, const cplx* __restrict__ sup,
-                                                        cplx* __restrict__ scratch, int* status) {
-  const int nb = S.nb, nb2 = nb * nb, M = S.M, q = S.q, m = S.m;
-  cplx* Ac = scratch;
-  cplx* Bc = scratch + (size_t)(M + 1) * nb2;
-  cplx* Cc = scratch + (size_t)2 * (M + 1) * nb2;
+// Parallel cyclic reduction factors of one coupled-channel system (Eqs. (28)-(29)):
+// rows k = 0..m-1 of A_k x_{k-1} + B_k x_k + C_k x_{k+1} = r_k with n_b x n_b blocks
+// (A_k, C_k the 1D Laplacian couplings times the identity, B_k the channel block).
+// Level l (stride s = 2^l) eliminates every row's couplings to k +- s with the rows
+// k +- s themselves: alpha = A_k B_{k-s}^{-1}, gamma = C_k B_{k+s}^{-1},
+//   A_k <- -alpha A_{k-s},  B_k <- B_k - alpha C_{k-s} - gamma A_{k+s},  C_k <- -gamma C_{k+s};
+// after ceil(log2 m) levels no coupling is left and x_k = B_k^{-1} r_k.  One block, the
+// rows of a level in parallel, double-buffered blocks.
+__global__ void __launch_bounds__(256) k_channel_factor_pcr(CRSystem S, const cplx* __restrict__ diag,
+                                                            const cplx* __restrict__ v, double E,
+                                                            const cplx* __restrict__ lam, const cplx* __restrict__ Vc,
+                                                            const cplx* __restrict__ sub, const cplx* __restrict__ sup,
+                                                            cplx* __restrict__ scratch, int* status) {
+  const int nb = S.nb, nb2 = nb * nb, m = S.m;
+  const size_t blk = (size_t)m * nb2;
+  cplx* Ab[2] = {scratch, scratch + 3 * blk};
+  cplx* Bb[2] = {scratch + blk, scratch + 4 * blk};
+  cplx* Cb[2] = {scratch + 2 * blk, scratch + 5 * blk};
+  cplx* Binv = scratch + 6 * blk;
   const int t0 = threadIdx.x, nt = blockDim.x;
-  for (int i = 1 + t0; i <= M; i += nt) {
-    cplx* A = Ac + (size_t)i * nb2;
-    cplx* B = Bc + (size_t)i * nb2;
-    cplx* C = Cc + (size_t)i * nb2;
-    if (i <= m) {
-      const int k = i - 1;
-      cplx base = cadd(diag[k], v[k]);
-      base.x -= E;
-      for (int r = 0; r < nb; ++r)
-        for (int c = 0; c < nb; ++c) {
-          cplx val = Vc[((size_t)k * nb + r) * nb + c];
-          if (r == c) val = cadd(val, cadd(base, lam[r]));
-          B[r * nb + c] = val;
-          A[r * nb + c] = (r == c && k > 0) ? sub[k] : cmk(0.0, 0.0);
-          C[r * nb + c] = (r == c && k < m - 1) ? sup[k] : cmk(0.0, 0.0);
-        }
-    } else {
-      for (int r = 0; r < nb2; ++r) {
-        B[r] = cmk((r % (nb + 1)) == 0 ? 1.0 : 0.0, 0.0);
-        A[r] = cmk(0.0, 0.0);
-        C[r] = cmk(0.0, 0.0);
+  for (int k = t0; k < m; k += nt) {
+    cplx* A = Ab[0] + (size_t)k * nb2;
+    cplx* B = Bb[0] + (size_t)k * nb2;
+    cplx* C = Cb[0] + (size_t)k * nb2;
+    cplx base = cadd(diag[k], v[k]);
+    base.x -= E;
+    for (int r = 0; r < nb; ++r)
+      for (int c = 0; c < nb; ++c) {
+        cplx val = Vc[((size_t)k * nb + r) * nb + c];
+        if (r == c) val = cadd(val, cadd(base, lam[r]));
+        B[r * nb + c] = val;
+        A[r * nb + c] = (r == c && k > 0) ? sub[k] : cmk(0.0, 0.0);
+        C[r * nb + c] = (r == c && k < m - 1) ? sup[k] : cmk(0.0, 0.0);
       }
-    }
   }
   __syncthreads();
-  cplx T1[MGC_MAX_NB * MGC_MAX_NB], T2[MGC_MAX_NB * MGC_MAX_NB];
-  for (int l = 1; l < q; ++l) {
-    const int s = 1 << (l - 1);
-    // rows eliminated at this level: P = B^{-1}, Q = P A, R = P C
-    for (int j = s + 2 * s * t0; j <= M; j += 2 * s * nt) {
-      for (int r = 0; r < nb2; ++r) T1[r] = Bc[(size_t)j * nb2 + r];
+  cplx T1[MGC_MAX_NB * MGC_MAX_NB], T2[MGC_MAX_NB * MGC_MAX_NB], al[MGC_MAX_NB * MGC_MAX_NB],
+      ga[MGC_MAX_NB * MGC_MAX_NB];
+  int cur = 0;
+  for (int l = 0; l < S.pq; ++l) {
+    const int s = 1 << l;
+    const cplx* A = Ab[cur];
+    const cplx* B = Bb[cur];
+    const cplx* C = Cb[cur];
+    for (int k = t0; k < m; k += nt) {
+      for (int r = 0; r < nb2; ++r) T1[r] = B[(size_t)k * nb2 + r];
       if (!small_inverse(nb, T1)) {
         atomicOr(status, MGC_ST_PIVOT);
         for (int r = 0; r < nb2; ++r) T1[r] = cmk(0.0, 0.0);
       }
-      for (int r = 0; r < nb2; ++r) S.P[(size_t)j * nb2 + r] = T1[r];
-      small_matmul(nb, T1, Ac + (size_t)j * nb2, S.Q + (size_t)j * nb2);
-      small_matmul(nb, T1, Cc + (size_t)j * nb2, S.R + (size_t)j * nb2);
+      for (int r = 0; r < nb2; ++r) Binv[(size_t)k * nb2 + r] = T1[r];
     }
     __syncthreads();
-    // kept rows: alpha = A_i P_{i-s}, gamma = C_i P_{i+s}, then the reduced coefficients
-    const int nk = (1 << (q - l)) - 1;
-    const int off = cr_fwd_offset(q, l);
-    for (int t = 1 + t0; t <= nk; t += nt) {
-      const int i = 2 * s * t;
-      cplx* al = S.alpha + (size_t)(off + t - 1) * nb2;
-      cplx* ga = S.gamma + (size_t)(off + t - 1) * nb2;
-      small_matmul(nb, Ac + (size_t)i * nb2, S.P + (size_t)(i - s) * nb2, al);
-      small_matmul(nb, Cc + (size_t)i * nb2, S.P + (size_t)(i + s) * nb2, ga);
-      cplx* B = Bc + (size_t)i * nb2;
-      small_matmul(nb, al, Cc + (size_t)(i - s) * nb2, T1);
-      small_matmul(nb, ga, Ac + (size_t)(i + s) * nb2, T2);
-      for (int r = 0; r < nb2; ++r) B[r] = csub(csub(B[r], T1[r]), T2[r]);
-      small_matmul(nb, al, Ac + (size_t)(i - s) * nb2, T1);
-      small_matmul(nb, ga, Cc + (size_t)(i + s) * nb2, T2);
+    cplx* A2 = Ab[cur ^ 1];
+    cplx* B2 = Bb[cur ^ 1];
+    cplx* C2 = Cb[cur ^ 1];
+    for (int k = t0; k < m; k += nt) {
+      const bool lo = k - s >= 0, hi = k + s < m;
+      if (lo) small_matmul(nb, A + (size_t)k * nb2, Binv + (size_t)(k - s) * nb2, al);
+      else for (int r = 0; r < nb2; ++r) al[r] = cmk(0.0, 0.0);
+      if (hi) small_matmul(nb, C + (size_t)k * nb2, Binv + (size_t)(k + s) * nb2, ga);
+      else for (int r = 0; r < nb2; ++r) ga[r] = cmk(0.0, 0.0);
+      cplx* pa = S.pa + ((size_t)l * m + k) * nb2;
+      cplx* pg = S.pg + ((size_t)l * m + k) * nb2;
       for (int r = 0; r < nb2; ++r) {
-        Ac[(size_t)i * nb2 + r] = cneg(T1[r]);
-        Cc[(size_t)i * nb2 + r] = cneg(T2[r]);
+        pa[r] = al[r];
+        pg[r] = ga[r];
+        B2[(size_t)k * nb2 + r] = B[(size_t)k * nb2 + r];
+        A2[(size_t)k * nb2 + r] = cmk(0.0, 0.0);
+        C2[(size_t)k * nb2 + r] = cmk(0.0, 0.0);
+      }
+      if (lo) {
+        small_matmul(nb, al, C + (size_t)(k - s) * nb2, T1);
+        small_matmul(nb, al, A + (size_t)(k - s) * nb2, T2);
+        for (int r = 0; r < nb2; ++r) {
+          B2[(size_t)k * nb2 + r] = csub(B2[(size_t)k * nb2 + r], T1[r]);
+          A2[(size_t)k * nb2 + r] = cneg(T2[r]);
+        }
+      }
+      if (hi) {
+        small_matmul(nb, ga, A + (size_t)(k + s) * nb2, T1);
+        small_matmul(nb, ga, C + (size_t)(k + s) * nb2, T2);
+        for (int r = 0; r < nb2; ++r) {
+          B2[(size_t)k * nb2 + r] = csub(B2[(size_t)k * nb2 + r], T1[r]);
+          C2[(size_t)k * nb2 + r] = cneg(T2[r]);
+        }
       }
     }
     __syncthreads();
+    cur ^= 1;
   }
-  if (t0 == 0) {
-    const int root = 1 << (q - 1);
-    for (int r = 0; r < nb2; ++r) T1[r] = Bc[(size_t)root * nb2 + r];
+  for (int k = t0; k < m; k += nt) {
+    for (int r = 0; r < nb2; ++r) T1[r] = Bb[cur][(size_t)k * nb2 + r];
     if (!small_inverse(nb, T1)) {
       atomicOr(status, MGC_ST_PIVOT);
       for (int r = 0; r < nb2; ++r) T1[r] = cmk(0.0, 0.0);
     }
-    for (int r = 0; r < nb2; ++r) {
-      S.P[(size_t)root * nb2 + r] = T1[r];
-      S.Q[(size_t)root * nb2 + r] = cmk(0.0, 0.0);
-      S.R[(size_t)root * nb2 + r] = cmk(0.0, 0.0);
-    }
+    for (int r = 0; r < nb2; ++r) S.pbinv[(size_t)k * nb2 + r] = T1[r];
   }
 }
+
 
 }  // namespace
 
@@ -700,9 +715,18 @@ cudaError_t launch_channel_potentials(int mx, int my, int nb, const cplx* wphi, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_channel_factor(const CRSystem& S, const cplx* diag, const cplx* v, double E, const cplx* lam,
-                                  const cplx* Vc, const cplx* a, const cplx* c, cplx* scratch, int* status,
-                                  cudaStream_t st) {
-  k_channel_factor<<<1, 256, 0, st>>>(S, diag, v, E, lam, Vc, a, c, scratch, status);
+int pcr_levels(int m) {
+  int q = 0;
+  while ((1 << q) < m) ++q;
+  return q;
+}
+
+size_t channel_factor_pcr_scratch(int m, int nb) { return (size_t)7 * m * nb * nb; }
+
+cudaError_t launch_channel_factor_pcr(const CRSystem& S, const cplx* diag, const cplx* v, double E, const cplx* lam,
+                                      const cplx* Vc, const cplx* a, const cplx* c, cplx* scratch, int* status,
+                                      cudaStream_t st) {
+  k_channel_factor_pcr<<<1, 256, 0, st>>>(S, diag, v, E, lam, Vc, a, c, scratch, status);
   return cudaGetLastError();
 }
+

@@ -197,20 +197,17 @@ void layout(mgcccs_handle* h, Carver& cv) {
       CRSystem& S = c == 0 ? h->crA : h->crB;
       S.m = c == 0 ? my : mx;
       S.nb = nb;
-      S.q = cr_levels(S.m);
-      S.M = (1 << S.q) - 1;
       const size_t nb2 = (size_t)nb * nb;
-      S.alpha = cv.take<cplx>((size_t)S.M * nb2);
-      S.gamma = cv.take<cplx>((size_t)S.M * nb2);
-      S.P = cv.take<cplx>((size_t)(S.M + 1) * nb2);
-      S.Q = cv.take<cplx>((size_t)(S.M + 1) * nb2);
-      S.R = cv.take<cplx>((size_t)(S.M + 1) * nb2);
-      S.X = cv.take<cplx>((size_t)(S.M + 2) * nb);
-      S.Y = cv.take<cplx>((size_t)(S.M + 2) * nb);
+      S.X = cv.take<cplx>((size_t)S.m * nb);
+      S.Y = cv.take<cplx>((size_t)S.m * nb);
+      S.pq = pcr_levels(S.m);
+      S.pa = cv.take<cplx>((size_t)S.pq * S.m * nb2);
+      S.pg = cv.take<cplx>((size_t)S.pq * S.m * nb2);
+      S.pbinv = cv.take<cplx>((size_t)S.m * nb2);
     }
     {
-      const int Mmax = h->crA.M > h->crB.M ? h->crA.M : h->crB.M;
-      h->cr_scratch = cv.take<cplx>((size_t)3 * (Mmax + 1) * nb * nb);
+      const int mmax = h->crA.m > h->crB.m ? h->crA.m : h->crB.m;
+      h->cr_scratch = cv.take<cplx>(channel_factor_pcr_scratch(mmax, nb));
     }
     size_t es = bound_states_scratch(mx > my ? mx : my, nb);
     h->eig_scratch = cv.take<cplx>((es + sizeof(cplx) - 1) / sizeof(cplx));
@@ -386,6 +383,7 @@ int do_setup(mgcccs_handle* h, const cplx* v1, const cplx* v2, const cplx* v12, 
   if (h->nb > 0) {
     const LevelBufs& b = h->lv[0];
     const int nb = h->nb;
+    MGC_CUDA(channel_solve_prepare(nb));
     if (lam_in) {
       // states supplied by the caller (a previous setup on the same grid and V1, V2)
       MGC_CUDA(cudaMemcpyAsync(h->lam, lam_in, sizeof(cplx) * nb, cudaMemcpyHostToDevice, st));
@@ -418,10 +416,10 @@ int do_setup(mgcccs_handle* h, const cplx* v1, const cplx* v2, const cplx* v12, 
     MGC_LAUNCH(launch_channel_potentials(b.mx, b.my, nb, h->wphi, h->phi, h->wvphi, h->vphi, v12, h->VA, h->VB,
                                          st));
     // channel A runs along y with the x bound states; channel B along x with the y ones
-    MGC_LAUNCH(launch_channel_factor(h->crA, b.diag_y, v2, p.E, h->lam, h->VA, b.west_y, b.east_y, h->cr_scratch,
-                                     h->status, st));
-    MGC_LAUNCH(launch_channel_factor(h->crB, b.diag_x, v1, p.E, h->mu, h->VB, b.west_x, b.east_x, h->cr_scratch,
-                                     h->status, st));
+    MGC_LAUNCH(launch_channel_factor_pcr(h->crA, b.diag_y, v2, p.E, h->lam, h->VA, b.west_y, b.east_y,
+                                         h->cr_scratch, h->status, st));
+    MGC_LAUNCH(launch_channel_factor_pcr(h->crB, b.diag_x, v1, p.E, h->mu, h->VB, b.west_x, b.east_x,
+                                         h->cr_scratch, h->status, st));
   }
   int rc0 = read_status(h);
   if (rc0 || !h->mixed) return rc0;
