@@ -1,0 +1,63 @@
+"""The larger workloads in the launch configurations the benchmark modes time, checked by
+properties that hold at any size: the precision form at 2048^2 on [0,60]^2 (n_b = 6,
+complex64 cycles in FP64 refinement) meets 1e-10 under the oracle's FP64 operator and
+agrees with the FP64 solve; the 64-energy batch graph converges every problem, and the
+oracle's operator confirms the residuals of a sample of them."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mgcccs_oracle as O
+from paper_1412_1953_gb300 import batch as BT
+from paper_1412_1953_gb300 import build, inputs
+from paper_1412_1953_gb300 import mgcccs as M
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+
+
+def _oracle_relres(prob, u):
+    lev = O.build_levels(O.params_from_problem(prob, levels=1, n_b=0), prob.v1, prob.v2, prob.v12)[0]
+    return float(np.linalg.norm(O.residual(lev, u, prob.f)) / np.linalg.norm(prob.f))
+
+
+def test_precision_form_2048_meets_tolerance_and_matches_fp64():
+    prob = inputs.temkin_poet(2048, L=60.0, R0=40.0, theta=math.pi / 6, E=0.5, seed=0)
+    f = torch.as_tensor(prob.f).to("cuda")
+    sols = {}
+    for prec in (0, 1):
+        sv = M.Solver(M.params_for(prob, levels=9, n_b=6, krylov_restart=20, precision=prec), prob.v1, prob.v2,
+                      prob.v12)
+        u = torch.zeros_like(f)
+        its, rr = sv.solve(u, f, rtol=1e-10, max_iter=1000)
+        assert rr <= 1e-10
+        sols[prec] = u.cpu().numpy()
+        sv.close()
+    assert _oracle_relres(prob, sols[1]) <= 1.001e-10
+    assert _oracle_relres(prob, sols[0]) <= 1.001e-10
+    diff = np.linalg.norm(sols[1] - sols[0]) / np.linalg.norm(sols[0])
+    assert diff <= 1e-8
+
+
+def test_batch_of_64_energies_converges_everywhere():
+    problems = inputs.batching_problems(count=64)
+    sched = {n: BT.default_schedule(n) for n in sorted({p.nx for p in problems})}
+    bs = BT.BatchSolver(problems, sched, n_b=3, precision=1)
+    g = bs.graph()
+    for u in bs.u:
+        u.zero_()
+    its, rr, st = g.run(rtol=1e-10, max_iter=2000)
+    torch.cuda.synchronize()
+    assert st == [M.OK] * 64
+    assert max(rr) <= 1e-10 and min(its) > 0
+    for k in range(0, 64, 9):
+        assert _oracle_relres(problems[k], bs.u[k].cpu().numpy()) <= 1.001e-10
+    g.close()
+    bs.close()
