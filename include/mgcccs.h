@@ -51,7 +51,9 @@ enum {
   MGCCCS_EBREAKDOWN = -4,  /* zero pivot in the coarsest or channel factorisation,
                               or the bound-state eigen-solve did not converge */
   MGCCCS_ENONFINITE = -5,  /* residual became NaN/Inf during a solve */
-  MGCCCS_ENOTCONV = -6     /* max_iter reached without meeting rtol (u, relres valid) */
+  MGCCCS_ENOTCONV = -6,    /* max_iter reached without meeting rtol (u, relres valid) */
+  MGCCCS_EDIVERGED = -7    /* the relative residual rose above 1e6 times its smallest value
+                              so far: the iteration diverges (u, relres valid) */
 };
 
 /* Problem and solver parameters (Sec. 2.5, Sec. 3.2, Sec. 4, Sec. 6). */
@@ -145,7 +147,8 @@ int mgcccs_cccs(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f);
  * doubles receiving the relative residual (GMRES: its least-squares estimate)
  * after each iteration, may be NULL.  Synchronous.  Returns ENOTCONV when
  * max_iter is reached (u, relres valid), ENONFINITE if the residual is not
- * finite.
+ * finite, EDIVERGED when the true relative residual (after each stand-alone
+ * iteration, at each GMRES restart) exceeds 1e6 times its smallest value so far.
  * GMRES solves without history run device-driven by default: the whole solve is
  * one CUDA graph whose conditional nodes (while / if / switch) carry the restart
  * loop, the Arnoldi loop and the stop tests, so the host launches it once and
@@ -194,7 +197,7 @@ int mgcccs_batch_create(mgcccs_batch_t* out, mgcccs_t* handles, int count, mgccc
                         const mgcccs_c128* const* f, void* stream);
 /* One launch of the batch graph: every problem from its current u until
  * ||f - (H-E)u|| / ||f|| <= rtol or max_iter Arnoldi steps.  iters, relres, status:
- * host arrays of count entries, may be NULL (status[k]: OK, ENOTCONV or ENONFINITE).
+ * host arrays of count entries, may be NULL (status[k]: OK, ENOTCONV, ENONFINITE or EDIVERGED).
  * Synchronous.  Returns the worst status. */
 int mgcccs_batch_run(mgcccs_batch_t b, double rtol, int max_iter, int* iters, double* relres, int* status);
 void mgcccs_batch_destroy(mgcccs_batch_t b);
@@ -208,7 +211,7 @@ void mgcccs_batch_destroy(mgcccs_batch_t b);
  * met its target.  A problem leaves the batch when ||f - (H-E)u|| / ||f|| <= rtol or
  * after max_iter used steps.  u[k], f[k]: device arrays of problem k (u in/out).
  * iters, relres, status: host arrays of count entries, may be NULL (status[k] is
- * MGCCCS_OK, ENOTCONV or ENONFINITE).  Synchronous.  Returns the worst status, or
+ * MGCCCS_OK, ENOTCONV, ENONFINITE or EDIVERGED).  Synchronous.  Returns the worst status, or
  * EINVAL (a handle listed twice, a handle without GMRES, NULL pointers). */
 int mgcccs_batch_solve(mgcccs_t* handles, int count, mgcccs_c128* const* u, const mgcccs_c128* const* f,
                        double rtol, int max_iter, int* iters, double* relres, int* status);

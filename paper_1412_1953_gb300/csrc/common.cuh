@@ -195,7 +195,9 @@ cudaError_t launch_hess_solve(int k, int m, const cplx* H, const cplx* g, cplx* 
 // The host writes the inputs before each launch of the solve graph; the control kernels
 // keep the counters and the outcome.
 enum { SOLVECTL_RUNNING = 0, SOLVECTL_CONVERGED = 1, SOLVECTL_MAXITER = 2, SOLVECTL_NONFINITE = 3,
-       SOLVECTL_ZERO_RHS = 4 };
+       SOLVECTL_ZERO_RHS = 4, SOLVECTL_DIVERGED = 5 };
+// divergence test on the true relative residual: rr above 1e6 times its minimum so far
+constexpr double MGC_DIVERGENCE_FACTOR = 1e6;
 struct SolveCtl {
   double fn2;          // |f|^2, written inside the graph
   double rtol, inner_rtol;
@@ -203,6 +205,7 @@ struct SolveCtl {
   int steps, k, j, cycles, outer, status;
   double rr, scale, target;
   int dgks, pad1;      // second Gram-Schmidt passes run
+  double rr_min;       // smallest true relative residual so far (host sets +inf)
 };
 cudaError_t launch_outer_control(SolveCtl* c, const double* rn2, cudaGraphConditionalHandle h_outer,
                                  cudaGraphConditionalHandle h_cycle, cudaGraphConditionalHandle h_inner,

@@ -215,8 +215,11 @@ __global__ void k_outer_control(SolveCtl* __restrict__ c, const double* __restri
   } else {
     const double rr = sqrt(rn2) / fn;
     c->rr = rr;
+    if (rr < c->rr_min) c->rr_min = rr;
     if (!isfinite(rr)) {
       c->status = SOLVECTL_NONFINITE;
+    } else if (rr > MGC_DIVERGENCE_FACTOR * c->rr_min) {
+      c->status = SOLVECTL_DIVERGED;
     } else if (rr <= c->rtol) {
       c->status = SOLVECTL_CONVERGED;
     } else if (c->steps >= c->max_iter) {

@@ -811,7 +811,7 @@ int gmres_impl(mgcccs_handle* h, cplx* u, const cplx* f, double fn, double rtol,
   const long long N = (long long)s0.mx * s0.my;
   const int nb = h->kr_nblk;
   int steps = 0;
-  double rr = INFINITY;
+  double rr = INFINITY, rr_min = INFINITY;
   for (;;) {
     // true residual r = f - A u into V_0
     MGC_LAUNCH(launch_residual(s0, (const cplx*)u, f, h->V, h->norm_part, st));
@@ -825,6 +825,12 @@ int gmres_impl(mgcccs_handle* h, cplx* u, const cplx* f, double fn, double rtol,
       if (relres) *relres = rr;
       return MGCCCS_ENONFINITE;
     }
+    if (rr > MGC_DIVERGENCE_FACTOR * rr_min) {
+      if (iters) *iters = steps;
+      if (relres) *relres = rr;
+      return MGCCCS_EDIVERGED;
+    }
+    rr_min = std::min(rr_min, rr);
     if (rr <= rtol || steps >= max_iter) break;
     MGC_LAUNCH(launch_zero_c(m + 1, h->g, st));
     MGC_LAUNCH(launch_scale_by_norm(N, (const cplx*)h->V, h->V, h->norm_out, h->g, nb, st));
@@ -860,7 +866,7 @@ int gmres_ir_impl(mgcccs_handle* h, cplx* u, const cplx* f, double fn, double rt
   const long long N = (long long)s0.mx * s0.my;
   const int nb = h->kr_nblk;
   int steps = 0;
-  double rr = INFINITY;
+  double rr = INFINITY, rr_min = INFINITY;
   for (;;) {
     MGC_LAUNCH(launch_residual(s0, (const cplx*)u, f, h->r64, h->norm_part, st));
     MGC_LAUNCH(launch_sum_partials(h->norm_part, residual_norm_blocks(s0), h->norm_out, st));
@@ -873,6 +879,12 @@ int gmres_ir_impl(mgcccs_handle* h, cplx* u, const cplx* f, double fn, double rt
       if (relres) *relres = rr;
       return MGCCCS_ENONFINITE;
     }
+    if (rr > MGC_DIVERGENCE_FACTOR * rr_min) {
+      if (iters) *iters = steps;
+      if (relres) *relres = rr;
+      return MGCCCS_EDIVERGED;
+    }
+    rr_min = std::min(rr_min, rr);
     if (rr <= rtol || steps >= max_iter) break;
     // v_0 = r/|r| in complex64, renormalised in the rounded precision; g = (|v_0|, 0, ...)
     MGC_LAUNCH(launch_demote(N, h->r64, h->norm_out, h->V32, st));
@@ -916,7 +928,7 @@ struct BatchItem {
   mgcccs_handle* h;
   cplx* u;
   const cplx* f;
-  double fn, rr, scale, target;
+  double fn, rr, scale, target, rr_min;
   int steps, k;
   bool active, in_cycle;
   int status;
@@ -947,6 +959,12 @@ int batch_cycle_begin(BatchItem& it, double rtol, int max_iter) {
     it.status = MGCCCS_ENONFINITE;
     return MGCCCS_OK;
   }
+  if (it.rr > MGC_DIVERGENCE_FACTOR * it.rr_min) {
+    it.active = false;
+    it.status = MGCCCS_EDIVERGED;
+    return MGCCCS_OK;
+  }
+  it.rr_min = std::min(it.rr_min, it.rr);
   if (it.rr <= rtol || it.steps >= max_iter) {
     it.active = false;
     it.status = it.rr <= rtol ? MGCCCS_OK : MGCCCS_ENOTCONV;
@@ -1195,6 +1213,7 @@ int stage_ctl(mgcccs_handle* h, double rtol, int max_iter, cudaStream_t st) {
   c.max_iter = max_iter;
   c.mixed = h->mixed;
   c.m = h->km;
+  c.rr_min = INFINITY;
   *h->ctl_host = c;
   MGC_CUDA(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(SolveCtl), cudaMemcpyHostToDevice, st));
   return MGCCCS_OK;
@@ -1220,6 +1239,7 @@ int finish_ctl(mgcccs_handle* h, cplx* u, int* iters, double* relres) {
       return MGCCCS_OK;
     case SOLVECTL_MAXITER: return MGCCCS_ENOTCONV;
     case SOLVECTL_NONFINITE: return MGCCCS_ENONFINITE;
+    case SOLVECTL_DIVERGED: return MGCCCS_EDIVERGED;
     default: return MGCCCS_ECUDA;
   }
 }
@@ -1276,7 +1296,7 @@ int solve_impl(mgcccs_handle* h, cplx* u, const cplx* f, double rtol, int max_it
   }
   if (h->km > 0 && h->mixed) return gmres_ir_impl(h, u, f, std::sqrt(fn2), rtol, max_iter, iters, relres, history);
   if (h->km > 0) return gmres_impl(h, u, f, std::sqrt(fn2), rtol, max_iter, iters, relres, history);
-  double rr = INFINITY;
+  double rr = INFINITY, rr_min = INFINITY;
   int it = 0;
   for (it = 1; it <= max_iter; ++it) {
     rc = vcycle_fine(h, u, f, false);
@@ -1295,6 +1315,12 @@ int solve_impl(mgcccs_handle* h, cplx* u, const cplx* f, double rtol, int max_it
       if (relres) *relres = rr;
       return MGCCCS_ENONFINITE;
     }
+    if (rr > MGC_DIVERGENCE_FACTOR * rr_min) {
+      if (iters) *iters = it;
+      if (relres) *relres = rr;
+      return MGCCCS_EDIVERGED;
+    }
+    rr_min = std::min(rr_min, rr);
     if (rr <= rtol) break;
   }
   if (it > max_iter) it = max_iter;
@@ -1517,7 +1543,7 @@ int mgcccs_batch_solve(mgcccs_t* handles, int count, mgcccs_c128* const* u, cons
     for (int q = 0; q < k; ++q)
       if (handles[q] == h) return MGCCCS_EINVAL;   // a handle's buffers serve one problem
     items[k] = BatchItem{h, reinterpret_cast<cplx*>(u[k]), reinterpret_cast<const cplx*>(f[k]), 0.0, INFINITY,
-                         1.0, rtol, 0, 0, true, false, MGCCCS_OK};
+                         1.0, rtol, INFINITY, 0, 0, true, false, MGCCCS_OK};
   }
   for (auto& it : items) {
     double fn2 = 0.0;
@@ -1543,7 +1569,7 @@ int mgcccs_batch_solve(mgcccs_t* handles, int count, mgcccs_c128* const* u, cons
     if (iters) iters[k] = items[k].steps;
     if (relres) relres[k] = items[k].rr;
     if (status) status[k] = items[k].status;
-    if (items[k].status == MGCCCS_ENONFINITE) worst = MGCCCS_ENONFINITE;
+    if (items[k].status == MGCCCS_ENONFINITE || items[k].status == MGCCCS_EDIVERGED) worst = items[k].status;
     else if (items[k].status == MGCCCS_ENOTCONV && worst == MGCCCS_OK) worst = MGCCCS_ENOTCONV;
   }
   return worst;
@@ -1636,7 +1662,7 @@ int mgcccs_batch_run(mgcccs_batch_t b, double rtol, int max_iter, int* iters, do
     int s = finish_ctl(b->hs[k], b->u[k], iters ? iters + k : nullptr, relres ? relres + k : nullptr);
     if (s == MGCCCS_ECUDA) return s;
     if (status) status[k] = s;
-    if (s == MGCCCS_ENONFINITE) worst = MGCCCS_ENONFINITE;
+    if (s == MGCCCS_ENONFINITE || s == MGCCCS_EDIVERGED) worst = s;
     else if (s == MGCCCS_ENOTCONV && worst == MGCCCS_OK) worst = MGCCCS_ENOTCONV;
   }
   return worst;
@@ -1659,6 +1685,7 @@ const char* mgcccs_strerror(int code) {
     case MGCCCS_EBREAKDOWN: return "zero pivot or eigen-solve breakdown during setup";
     case MGCCCS_ENONFINITE: return "residual is not finite";
     case MGCCCS_ENOTCONV: return "max_iter reached before rtol";
+    case MGCCCS_EDIVERGED: return "the residual grew above 1e6 times its minimum: the iteration diverges";
   }
   return "unknown error code";
 }

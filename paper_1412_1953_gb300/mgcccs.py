@@ -20,7 +20,7 @@ from . import build as _build
 
 HEADER = os.path.join(_build.ROOT, "include", "mgcccs.h")
 
-OK, EINVAL, ECUDA, ENOSPACE, EBREAKDOWN, ENONFINITE, ENOTCONV = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ECUDA, ENOSPACE, EBREAKDOWN, ENONFINITE, ENOTCONV, EDIVERGED = 0, -1, -2, -3, -4, -5, -6, -7
 
 
 class MGCCCSError(RuntimeError):
@@ -352,7 +352,7 @@ def mgcccs_batch_solve(solvers, us, fs, rtol=1e-10, max_iter=1000):
     rr = (_d * K)()
     st = (_i * K)()
     code = lib().mgcccs_batch_solve(hs, K, up, fp, float(rtol), int(max_iter), its, rr, st)
-    if code not in (OK, ENOTCONV, ENONFINITE):
+    if code not in (OK, ENOTCONV, ENONFINITE, EDIVERGED):
         raise MGCCCSError(code, "mgcccs_batch_solve")
     return list(its), list(rr), list(st)
 
@@ -385,7 +385,7 @@ class Batch:
         K = len(self.solvers)
         its, rr, st = (_i * K)(), (_d * K)(), (_i * K)()
         code = lib().mgcccs_batch_run(self.b, float(rtol), int(max_iter), its, rr, st)
-        if code not in (OK, ENOTCONV, ENONFINITE):
+        if code not in (OK, ENOTCONV, ENONFINITE, EDIVERGED):
             raise MGCCCSError(code, "mgcccs_batch_run")
         return list(its), list(rr), list(st)
 
