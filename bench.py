@@ -657,6 +657,9 @@ def run_reference(args):
                   f"the {args.n}^2 workload, {t_it:.3f} s each, scaled to the {n_steps} steps the oracle needs on "
                   f"the 256^2 instance of the same problem (size-independent count); setup {setup_s:.1f} s excluded")
     cfg["iterations"] = n_steps
+    if args.krylov:
+        cfg["outer"] = (f"GMRES({args.krylov}) right-preconditioned by one MG-CCCS iteration; CPU oracle "
+                        f"(modified Gram-Schmidt, host loop)")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_it * per_step * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (FP64)",
