@@ -254,49 +254,46 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int nc, const cplx* __rest
   coarse_row<true>(nc, Ainv, f, u, row, threadIdx.x & 31);
 }
 
-// ---- fused coarse levels: the V-cycle below a size threshold in one CTA ----------
-// Levels 0..n-1 of `a` are consecutive multigrid levels ending at the coarsest.  The
-// kernel runs the same steps as the one-step kernels in the same order (pre-smoothing,
-// residual, restriction, ..., the dense coarsest solve, prolongation, post-smoothing)
-// with __syncthreads() between steps instead of kernel boundaries, so a V-cycle's
-// coarse tail costs one launch instead of six per level.  The result is left in lv[0].u.
-// Stages of the fused kernel: one pass over a level's nodes by the whole CTA.  The
-// restrict-qualified pointers and the unrolled loop let each thread keep the loads of
-// several nodes in flight (one node per thread would leave the SM waiting on L2).
+// Stages of the fused kernel: one pass over a level's nodes by the whole CTA, lane x of
+// warp y taking the nodes (x + 32a, y + 32b) (no index division, rows read by whole
+// warps).  The restrict-qualified pointers let the loads of a thread's nodes overlap.
+constexpr int TAIL_WARPS = TAIL_THREADS / 32;
+
 template <class C>
 __device__ __forceinline__ void tail_jacobi(const StencilViewT<C>& s, const C* __restrict__ u, C* __restrict__ o,
                                             const C* __restrict__ f, bool zero) {
-  const int mx = s.mx, np = s.mx * s.my;
-  if (zero) {
-#pragma unroll 4
-    for (int p = threadIdx.x; p < np; p += TAIL_THREADS) o[p] = cmul(__ldg(s.Dinv + p), ldm<false>(f + p));
-  } else {
-#pragma unroll 4
-    for (int p = threadIdx.x; p < np; p += TAIL_THREADS) o[p] = jacobi_pt<false>(s, u, f, p % mx, p / mx);
-  }
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int j = ty; j < s.my; j += TAIL_WARPS)
+    for (int i = tx; i < s.mx; i += 32) {
+      const int p = j * s.mx + i;
+      o[p] = zero ? cmul(__ldg(s.Dinv + p), ldm<false>(f + p)) : jacobi_pt<false>(s, u, f, i, j);
+    }
 }
 
 template <class C>
 __device__ __forceinline__ void tail_residual(const StencilViewT<C>& s, const C* __restrict__ u,
                                               const C* __restrict__ f, C* __restrict__ r) {
-  const int mx = s.mx, np = s.mx * s.my;
-#pragma unroll 4
-  for (int p = threadIdx.x; p < np; p += TAIL_THREADS) r[p] = residual_pt<false>(s, u, f, p % mx, p / mx);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int j = ty; j < s.my; j += TAIL_WARPS)
+    for (int i = tx; i < s.mx; i += 32) r[j * s.mx + i] = residual_pt<false>(s, u, f, i, j);
 }
 
 template <class C>
 __device__ __forceinline__ void tail_restrict(int mx, int mcx, int mcy, const C* __restrict__ r, C* __restrict__ fc) {
-  const int ncp = mcx * mcy;
-#pragma unroll 4
-  for (int q = threadIdx.x; q < ncp; q += TAIL_THREADS) fc[q] = restrict_pt<false>(mx, r, q % mcx, q / mcx);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int J = ty; J < mcy; J += TAIL_WARPS)
+    for (int I = tx; I < mcx; I += 32) fc[J * mcx + I] = restrict_pt<false>(mx, r, I, J);
 }
 
 template <class C>
 __device__ __forceinline__ void tail_prolong(int mx, int my, int mcx, int mcy, const C* __restrict__ ec,
                                              C* __restrict__ u) {
-  const int np = mx * my;
-#pragma unroll 4
-  for (int p = threadIdx.x; p < np; p += TAIL_THREADS) u[p] = cadd(u[p], prolong_pt<false>(mcx, mcy, ec, p % mx, p / mx));
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int j = ty; j < my; j += TAIL_WARPS)
+    for (int i = tx; i < mx; i += 32) {
+      const int p = j * mx + i;
+      u[p] = cadd(u[p], prolong_pt<false>(mcx, mcy, ec, i, j));
+    }
 }
 
 // ---- fused coarse levels: the V-cycle below a size threshold in one CTA ----------
