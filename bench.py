@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--R0", type=float, default=20.0, help="ECS start")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default=None,
                     help="default: fp64 (mixed for --mode batch)")
-    ap.add_argument("--mode", choices=["bench", "solve-only", "kernel", "adjoint", "sweep", "precision", "batch"],
+    ap.add_argument("--mode", choices=["bench", "solve-only", "kernel", "adjoint", "sweep", "precision", "batch",
+                                       "oracle"],
                     default="bench",
                     help="solve-only: setup + warm-up + timed solves, nothing else (for launch lists); "
                          "kernel: setup + 6 launches of one kernel (for ncu captures)")
@@ -490,6 +491,49 @@ def run_batch(args):
     bs.close()
 
 
+def cpu_description():
+    """Core count and CPU model of this host (for the oracle's timing rows)."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "model": model, "threads_used": 1}
+
+
+def run_oracle_timing(args):
+    """The CPU oracle on the parity and benchmark configurations, one core: a complete
+    GMRES(20)+MG-CCCS solve to 1e-10 at 128^2; at 512^2, 1024^2 (both on [0,30]^2) and 2048^2
+    (on [0,60]^2, n_b = 6) a median over sampled Arnoldi steps times the step count the
+    same solve takes (the GPU's, equal to the oracle's within 2 by the parity tests).
+    Setup is timed separately."""
+    from oracle import mgcccs_oracle as O
+    from paper_1412_1953_gb300 import inputs
+    rows = []
+    t0 = time.perf_counter()
+    prob = inputs.temkin_poet(128)
+    so = O.Solver(O.params_from_problem(prob, levels=5, n_b=3), prob.v1, prob.v2, prob.v12)
+    setup = time.perf_counter() - t0
+    t = time.perf_counter()
+    _, hist, rr = O.gmres(so, prob.f, m=20, rtol=1e-10, max_iter=1000)
+    el = time.perf_counter() - t
+    rows.append({"workload": "tp_ecs_128", "steps": len(hist), "relres": float(rr), "seconds": el,
+                 "setup_seconds": setup, "unknowns_per_s": prob.n_unknowns / el, "kind": "full solve"})
+    for n, L, R0, lv, nb, steps in ((512, 30.0, 20.0, 7, 3, 97), (1024, 30.0, 20.0, 8, 3, 99),
+                                     (2048, 60.0, 40.0, 9, 6, 163)):
+        prob = inputs.temkin_poet(n, L=L, R0=R0, theta=math.pi / 6, E=0.5, seed=0)
+        sub = argparse.Namespace(levels=lv, nb=nb, krylov=20)
+        per, sampled, setup = oracle_step_time(prob, sub, seconds=args.cpu_seconds)
+        rows.append({"workload": f"tp_ecs_{n}" + ("" if L == 30.0 else f"_L{L:g}"), "steps": steps,
+                     "seconds_per_step": per, "sampled_steps": sampled, "setup_seconds": setup,
+                     "unknowns_per_s": prob.n_unknowns / (per * steps), "kind": "sampled Arnoldi steps"})
+    print(json.dumps({"mode": "oracle", "cpu": cpu_description(), "rows": rows}), flush=True)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -683,6 +727,8 @@ def main():
         run_precision(args)
     elif args.mode == "batch":
         run_batch(args)
+    elif args.mode == "oracle":
+        run_oracle_timing(args)
     else:
         run_ours(args)
 
