@@ -61,3 +61,18 @@ def test_batch_of_64_energies_converges_everywhere():
         assert _oracle_relres(problems[k], bs.u[k].cpu().numpy()) <= 1.001e-10
     g.close()
     bs.close()
+
+
+def test_largest_grid_4096_solves_to_tolerance():
+    """16.7 M unknowns (4096^2 cells on [0,30]^2, 10 levels): setup (Ehrlich-Aberth bound
+    states at 4095 rows, parallel-cyclic-reduction factors) and the FP64 GMRES(20) solve
+    reach 1e-10 under the oracle's operator."""
+    prob = inputs.temkin_poet(4096)
+    sv = M.Solver(M.params_for(prob, levels=10, n_b=3, krylov_restart=20), prob.v1, prob.v2, prob.v12)
+    assert sv.eig_fallbacks() == 0
+    f = torch.as_tensor(prob.f).to("cuda")
+    u = torch.zeros_like(f)
+    its, rr = sv.solve(u, f, rtol=1e-10, max_iter=600)
+    assert rr <= 1e-10
+    assert _oracle_relres(prob, u.cpu().numpy()) <= 1.001e-10
+    sv.close()
