@@ -182,12 +182,15 @@ template <class C>
 cudaError_t launch_multiaxpy(long long n, int k, const C* V, long long ld, const cplx* coef, double sgn,
                              C* w, double* norm_part, int nblk, const int* gate, cudaStream_t st,
                              const int* dk = nullptr);
-cudaError_t launch_dgks(const double* before, const double* after, int* gate, cudaStream_t st,
-                        cudaGraphConditionalHandle hd = 0, int* fired = nullptr);
 template <class C>
 cudaError_t launch_scale_by_norm(long long n, const C* w, C* out, const double* norm2, cplx* store,
                                  int nblk, cudaStream_t st);
-cudaError_t launch_givens(int j, int m, cplx* H, cplx* cs, cplx* sn, cplx* g, double* est, cudaStream_t st);
+cudaError_t launch_givens(int j, int m, cplx* H, cplx* cs, cplx* sn, cplx* g, double* est, const double* hnorm2,
+                          cudaStream_t st);
+// |w|^2 from partials into *out plus the second-pass decision (*gate; in a device-driven
+// graph also the conditional node hd and the counter *fired)
+cudaError_t launch_sum_dgks(const double* part, int n, double* out, const double* before, int* gate,
+                           cudaStream_t st, cudaGraphConditionalHandle hd = 0, int* fired = nullptr);
 cudaError_t launch_hess_solve(int k, int m, const cplx* H, const cplx* g, cplx* y, cudaStream_t st,
                               const int* dk = nullptr);
 

@@ -121,16 +121,20 @@ __global__ void __launch_bounds__(NT) k_scale_by_norm(long long n, const C* __re
   for (long long p = p0; p < n; p += (long long)gridDim.x * NT) out[p] = cscal((typename CT<C>::R)s, w[p]);
 }
 
-// Apply rotations 0..j-1 to column j of H, build rotation j, update g; est = |g[j+1]|.
+// Apply rotations 0..j-1 to column j of H (h_{j+1,j} = sqrt(*hnorm2)), build rotation j,
+// update g; est = |g[j+1]|.
 // H is column-major with leading dimension m+1.  Rotation j maps rows (j, j+1) by
 // [conj(c) conj(s); -s c] with c = a/rho, s = b/rho, rho = sqrt(|a|^2 + |b|^2).
 __global__ void k_givens(int j, int m, cplx* __restrict__ H, cplx* __restrict__ cs, cplx* __restrict__ sn,
-                         cplx* __restrict__ g, double* __restrict__ est) {
+                         cplx* __restrict__ g, double* __restrict__ est, const double* __restrict__ hnorm2) {
   // the column and the earlier rotations are staged in shared memory by the warp, so the
   // sequential chain of thread 0 waits on no global load
   __shared__ cplx col[MGC_MAX_RESTART + 1], rc[MGC_MAX_RESTART], rs[MGC_MAX_RESTART];
   cplx* colg = H + (size_t)j * (m + 1);
-  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) col[i] = colg[i];
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) col[i] = colg[i];
+  // h_{j+1,j} = |w| from its square (the value the normalisation of v_{j+1} uses), so the
+  // rotation need not wait for that kernel
+  if (threadIdx.x == 0) col[j + 1] = cmk(sqrt(*hnorm2), 0.0);
   for (int i = threadIdx.x; i < j; i += blockDim.x) {
     rc[i] = cs[i];
     rs[i] = sn[i];
@@ -175,24 +179,6 @@ __global__ void k_hess_solve(int k, int m, const cplx* __restrict__ H, const cpl
     cplx t = g[i];
     for (int q = i + 1; q < k; ++q) t = cfms(H[(size_t)q * (m + 1) + i], y[q], t);
     y[i] = cdiv(t, H[(size_t)i * (m + 1) + i]);
-  }
-}
-
-// Reorthogonalisation test: a second Gram-Schmidt pass runs only when the first pass
-// cancelled |w| by more than a factor 1e3 (|w_after|^2 < 1e-6 |w_before|^2), so one
-// pass never loses more than about 1e3 ulps of orthogonality.  (The classic threshold
-// 1/sqrt(2) fires on almost every step here: with a good preconditioner A M^{-1} v_j is
-// close to v_j and a first pass routinely removes half of |w|^2, harmlessly.)
-// In a device-driven solve graph the decision also steers the conditional node that
-// holds the second pass (use_cond), and fired passes are counted.
-__global__ void k_dgks(const double* __restrict__ before, const double* __restrict__ after, int* __restrict__ gate,
-                       cudaGraphConditionalHandle hd, int use_cond, int* __restrict__ fired) {
-  if (threadIdx.x != 0) return;
-  const int second = (*after < 1e-6 * *before) ? 1 : 0;
-  *gate = second;
-  if (use_cond) {
-    cudaGraphSetConditional(hd, (unsigned)second);
-    if (second) *fired += 1;
   }
 }
 
@@ -259,6 +245,39 @@ __global__ void k_step_control(SolveCtl* __restrict__ c, const double* __restric
   cudaGraphSetConditional(h_inner, cont ? 1u : 0u);
 }
 
+// Reorthogonalisation test: a second Gram-Schmidt pass runs only when the first pass
+// cancelled |w| by more than a factor 1e3 (|w_after|^2 < 1e-6 |w_before|^2), so one
+// pass never loses more than about 1e3 ulps of orthogonality.  (The classic threshold
+// 1/sqrt(2) fires on almost every step here: with a good preconditioner A M^{-1} v_j is
+// close to v_j and a first pass routinely removes half of |w|^2, harmlessly.)
+// |w|^2 after the first pass comes from the block partials in the fixed summation order
+// of k_sum_partials, and the decision is taken in the same kernel; in a device-driven
+// solve graph it also sets the conditional node that holds the second pass (use_cond)
+// and counts the passes that run.
+__global__ void __launch_bounds__(256) k_sum_dgks(const double* __restrict__ part, int n, double* __restrict__ out,
+                                                  const double* __restrict__ before, int* __restrict__ gate,
+                                                  cudaGraphConditionalHandle hd, int use_cond,
+                                                  int* __restrict__ fired) {
+  __shared__ double sh[8];
+  double v = 0.0;
+  for (int k = threadIdx.x; k < n; k += 256) v += part[k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double tot = 0.0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) tot += sh[w];
+  *out = tot;
+  const int second = (tot < 1e-6 * *before) ? 1 : 0;
+  *gate = second;
+  if (use_cond) {
+    cudaGraphSetConditional(hd, (unsigned)second);
+    if (second) *fired += 1;
+  }
+}
+
 __global__ void k_zero_c(int n, cplx* __restrict__ a) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) a[t] = cmk(0.0, 0.0);
@@ -318,8 +337,9 @@ MGC_INSTANTIATE(double2)
 MGC_INSTANTIATE(float2)
 #undef MGC_INSTANTIATE
 
-cudaError_t launch_givens(int j, int m, cplx* H, cplx* cs, cplx* sn, cplx* g, double* est, cudaStream_t st) {
-  k_givens<<<1, 32, 0, st>>>(j, m, H, cs, sn, g, est);
+cudaError_t launch_givens(int j, int m, cplx* H, cplx* cs, cplx* sn, cplx* g, double* est, const double* hnorm2,
+                          cudaStream_t st) {
+  k_givens<<<1, 32, 0, st>>>(j, m, H, cs, sn, g, est, hnorm2);
   return cudaGetLastError();
 }
 
@@ -329,11 +349,6 @@ cudaError_t launch_hess_solve(int k, int m, const cplx* H, const cplx* g, cplx* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_dgks(const double* before, const double* after, int* gate, cudaStream_t st,
-                        cudaGraphConditionalHandle hd, int* fired) {
-  k_dgks<<<1, 32, 0, st>>>(before, after, gate, hd, fired ? 1 : 0, fired);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_outer_control(SolveCtl* c, const double* rn2, cudaGraphConditionalHandle h_outer,
                                  cudaGraphConditionalHandle h_cycle, cudaGraphConditionalHandle h_inner,
@@ -345,6 +360,12 @@ cudaError_t launch_outer_control(SolveCtl* c, const double* rn2, cudaGraphCondit
 cudaError_t launch_step_control(SolveCtl* c, const double* est, cudaGraphConditionalHandle h_inner,
                                 cudaGraphConditionalHandle h_switch, cudaStream_t st) {
   k_step_control<<<1, 32, 0, st>>>(c, est, h_inner, h_switch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_dgks(const double* part, int n, double* out, const double* before, int* gate,
+                           cudaStream_t st, cudaGraphConditionalHandle hd, int* fired) {
+  k_sum_dgks<<<1, 256, 0, st>>>(part, n, out, before, gate, hd, fired ? 1 : 0, fired);
   return cudaGetLastError();
 }
 

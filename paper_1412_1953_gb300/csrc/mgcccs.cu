@@ -78,6 +78,8 @@ struct mgcccs_handle {
   SolveCtl* ctl;
   SolveCtl* ctl_host;
   cudaStream_t gst[2];
+  cudaStream_t fork_st;                      // side branch of the Arnoldi step graphs
+  cudaEvent_t fev[4];                        // fork/join events of the side branch
   bool device_loop;
   int driver;                                // MGCCCS_DRIVER_GRAPH or MGCCCS_DRIVER_HOST
   cudaGraphExec_t solve_exec[4];             // device-driven solve graphs by (u, f) pointers
@@ -688,21 +690,27 @@ int issue_arnoldi_step(mgcccs_handle* h, int j) {
   cplx* col = h->Hh + (size_t)j * (m + 1);
   int rc = precond<C>(h, zj, vj);
   if (rc) return rc;
-  // w = A z_j, with |w|^2 for the reorthogonalisation test
+  // w = A z_j, with |w|^2 for the reorthogonalisation test; the sum of its partials runs
+  // on a side branch beside the first multi-dot (the step is always captured as a graph,
+  // so the fork and join become graph edges)
   MGC_LAUNCH(launch_apply(s0, (const C*)zj, w, st, h->norm_part));
-  MGC_LAUNCH(launch_sum_partials(h->norm_part, residual_norm_blocks(s0), h->norm_out + 3, st));
+  MGC_CUDA(cudaEventRecord(h->fev[0], st));
+  MGC_CUDA(cudaStreamWaitEvent(h->fork_st, h->fev[0], 0));
+  MGC_LAUNCH(launch_sum_partials(h->norm_part, residual_norm_blocks(s0), h->norm_out + 3, h->fork_st));
+  MGC_CUDA(cudaEventRecord(h->fev[1], h->fork_st));
   // Gram-Schmidt, first pass: H(0:j, j) = V^H w ; w -= V H(0:j, j)
   const int nbd = multidot_blocks(N, j + 1);
   MGC_LAUNCH(launch_multidot(N, j + 1, (const C*)V, N, (const C*)w, h->dotpart, nbd, (const int*)nullptr, st));
   MGC_LAUNCH(launch_reduce_dots(nbd, j + 1, h->dotpart, col, nullptr, st));
+  MGC_CUDA(cudaStreamWaitEvent(st, h->fev[1], 0));     // norm_part is reused by the multi-axpy
   MGC_LAUNCH(launch_multiaxpy(N, j + 1, (const C*)V, N, col, -1.0, w, h->norm_part, nb, (const int*)nullptr, st));
-  MGC_LAUNCH(launch_sum_partials(h->norm_part, nb, h->norm_out + 1, st));
   // second pass only when the first one cancelled |w| by more than 1e3;
   // the corrections are added into H(0:j, j)
   if (h->device_loop) {
     // device-driven graph: the pass is the body of a conditional node, so it costs no
     // launch when it does not run
-    MGC_LAUNCH(launch_dgks(h->norm_out + 3, h->norm_out + 1, h->gate, st, h->dgks_cond[j], &h->ctl->dgks));
+    MGC_LAUNCH(launch_sum_dgks(h->norm_part, nb, h->norm_out + 1, h->norm_out + 3, h->gate, st, h->dgks_cond[j],
+                               &h->ctl->dgks));
     cudaGraph_t* body = nullptr;
     int rc2 = add_conditional(st, h->dgks_cond[j], cudaGraphCondTypeIf, 1, &body);
     if (rc2) return rc2;
@@ -720,17 +728,23 @@ int issue_arnoldi_step(mgcccs_handle* h, int j) {
     rc2 = capture_end(cg);
     if (rc2) return rc2;
   } else {
-    MGC_LAUNCH(launch_dgks(h->norm_out + 3, h->norm_out + 1, h->gate, st));
+    MGC_LAUNCH(launch_sum_dgks(h->norm_part, nb, h->norm_out + 1, h->norm_out + 3, h->gate, st));
     MGC_LAUNCH(launch_multidot(N, j + 1, (const C*)V, N, (const C*)w, h->dotpart, nbd, (const int*)h->gate, st));
     MGC_LAUNCH(launch_reduce_dots(nbd, j + 1, h->dotpart, h->hc, col, st));
     MGC_LAUNCH(launch_multiaxpy(N, j + 1, (const C*)V, N, h->hc, -1.0, w, h->norm_part, nb, (const int*)h->gate,
                                 st));
     MGC_LAUNCH(launch_sum_partials(h->norm_part, nb, h->norm_out + 1, st, h->gate));
   }
-  MGC_LAUNCH(launch_scale_by_norm(N, (const C*)w, w, h->norm_out + 1, col + j + 1, nb, st));
-  MGC_LAUNCH(launch_givens(j, m, h->Hh, h->cs, h->sn, h->g, h->norm_out + 2, st));
+  // v_{j+1} = w/|w| and the Givens rotation (which takes h_{j+1,j} = |w| from the same
+  // squared norm) on two branches
+  MGC_CUDA(cudaEventRecord(h->fev[2], st));
+  MGC_CUDA(cudaStreamWaitEvent(h->fork_st, h->fev[2], 0));
+  MGC_LAUNCH(launch_givens(j, m, h->Hh, h->cs, h->sn, h->g, h->norm_out + 2, h->norm_out + 1, h->fork_st));
   if (!h->device_loop)
-    MGC_CUDA(cudaMemcpyAsync(h->est_host + j, h->norm_out + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    MGC_CUDA(cudaMemcpyAsync(h->est_host + j, h->norm_out + 2, sizeof(double), cudaMemcpyDeviceToHost, h->fork_st));
+  MGC_CUDA(cudaEventRecord(h->fev[3], h->fork_st));
+  MGC_LAUNCH(launch_scale_by_norm(N, (const C*)w, w, h->norm_out + 1, (cplx*)nullptr, nb, st));
+  MGC_CUDA(cudaStreamWaitEvent(st, h->fev[3], 0));
   return MGCCCS_OK;
 }
 
@@ -1276,6 +1290,8 @@ int create_krylov_objects(mgcccs_handle* h) {
   MGC_CUDA(cudaMallocHost(reinterpret_cast<void**>(&h->est_host), sizeof(double) * (MGC_MAX_RESTART + 1)));
   MGC_CUDA(cudaMallocHost(reinterpret_cast<void**>(&h->ctl_host), sizeof(SolveCtl)));
   for (int q = 0; q < 2; ++q) MGC_CUDA(cudaStreamCreateWithFlags(&h->gst[q], cudaStreamNonBlocking));
+  MGC_CUDA(cudaStreamCreateWithFlags(&h->fork_st, cudaStreamNonBlocking));
+  for (int q = 0; q < 4; ++q) MGC_CUDA(cudaEventCreateWithFlags(&h->fev[q], cudaEventDisableTiming));
   return MGCCCS_OK;
 }
 
@@ -1703,6 +1719,9 @@ void mgcccs_destroy(mgcccs_t h) {
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
   for (int q = 0; q < 2; ++q)
     if (h->gst[q]) cudaStreamDestroy(h->gst[q]);
+  if (h->fork_st) cudaStreamDestroy(h->fork_st);
+  for (int q = 0; q < 4; ++q)
+    if (h->fev[q]) cudaEventDestroy(h->fev[q]);
   if (h->est_host) cudaFreeHost(h->est_host);
   if (h->ctl_host) cudaFreeHost(h->ctl_host);
   delete h;
