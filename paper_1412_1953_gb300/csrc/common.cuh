@@ -146,6 +146,10 @@ template <class C>
 cudaError_t launch_jacobi(const StencilViewT<C>& s, const C* u_in, C* u_out, const C* f, cudaStream_t st);
 template <class C>
 cudaError_t launch_jacobi_zero(const StencilViewT<C>& s, C* u_out, const C* f, cudaStream_t st);
+// w <- w / sqrt(*norm2) in place, and u_out = omega D^{-1} w (zero-start sweep)
+template <class C>
+cudaError_t launch_scale_jacobi_zero(const StencilViewT<C>& s, C* w, const double* norm2, C* u_out,
+                                     cudaStream_t st);
 template <class C>
 cudaError_t launch_residual(const StencilViewT<C>& s, const C* u, const C* f, C* r, double* norm_part,
                             cudaStream_t st);

@@ -171,6 +171,27 @@ __global__ void __launch_bounds__(256) k_jacobi_zero(long long n, const C* __res
   if (p < n) u_out[p] = cmul(__ldg(Dinv + p), __ldg(f + p));
 }
 
+// First sweep from a zero initial guess on the Krylov vector w, fused with its
+// normalisation: v = w / sqrt(*norm2) (zeros if the norm vanishes) is written back in
+// place and u = omega D^{-1} v; the same arithmetic as k_scale_by_norm then k_jacobi_zero.
+template <class C>
+__global__ void __launch_bounds__(256) k_scale_jacobi_zero(long long n, C* w, const double* __restrict__ norm2,
+                                                          const C* __restrict__ Dinv, C* __restrict__ u_out) {
+  __shared__ double sb;
+  if (threadIdx.x == 0) {
+    const double b = sqrt(*norm2);
+    sb = b > 0.0 ? 1.0 / b : 0.0;
+  }
+  __syncthreads();
+  const typename CT<C>::R sc = (typename CT<C>::R)sb;
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p < n) {
+    const C v = cscal(sc, w[p]);
+    w[p] = v;
+    u_out[p] = cmul(__ldg(Dinv + p), v);
+  }
+}
+
 // Deterministic block reduction (fixed tree order): warp sums in the value's own
 // precision R, the per-warp totals summed in FP64 by thread 0.  For complex64 data this
 // keeps the FP64 pipe (1/64 of the FP32 rate here) out of the per-element work.
@@ -459,6 +480,14 @@ cudaError_t launch_jacobi_zero(const StencilViewT<C>& s, C* u_out, const C* f, c
 }
 
 template <class C>
+cudaError_t launch_scale_jacobi_zero(const StencilViewT<C>& s, C* w, const double* norm2, C* u_out,
+                                     cudaStream_t st) {
+  long long n = (long long)s.mx * s.my;
+  k_scale_jacobi_zero<C><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, w, norm2, s.Dinv, u_out);
+  return cudaGetLastError();
+}
+
+template <class C>
 int residual_norm_blocks(const StencilViewT<C>& s) {
   dim3 g = grid2(s.mx, s.my);
   return (int)(g.x * g.y);
@@ -512,6 +541,8 @@ cudaError_t launch_norm2(const C* v, long long n, double* part, int nblocks, cud
 #define MGC_INSTANTIATE(C)                                                                                  \
   template cudaError_t launch_jacobi<C>(const StencilViewT<C>&, const C*, C*, const C*, cudaStream_t);     \
   template cudaError_t launch_jacobi_zero<C>(const StencilViewT<C>&, C*, const C*, cudaStream_t);          \
+  template cudaError_t launch_scale_jacobi_zero<C>(const StencilViewT<C>&, C*, const double*, C*,          \
+                                                   cudaStream_t);                                         \
   template int residual_norm_blocks<C>(const StencilViewT<C>&);                                           \
   template cudaError_t launch_residual<C>(const StencilViewT<C>&, const C*, const C*, C*, double*,        \
                                           cudaStream_t);                                                  \

@@ -79,8 +79,9 @@ struct mgcccs_handle {
   SolveCtl* ctl_host;
   cudaStream_t gst[2];
   cudaStream_t fork_st;                      // side branch of the Arnoldi step graphs
-  cudaEvent_t fev[4];                        // fork/join events of the side branch
+  cudaEvent_t fev[2];                        // fork/join events of the side branch
   bool device_loop;
+  const double* pend_norm2;                  // set: the next fine zero-start sweep first normalises f
   int driver;                                // MGCCCS_DRIVER_GRAPH or MGCCCS_DRIVER_HOST
   cudaGraphExec_t solve_exec[4];             // device-driven solve graphs by (u, f) pointers
   const void *solve_u[4], *solve_f[4];
@@ -523,8 +524,15 @@ int vcycle_rec(mgcccs_handle* h, int l, C* u, const C* f, bool zero_init, C** ou
   C* oth = b.t;
   bool zero = zero_init;
   for (int s = 0; s < h->p.nu1; ++s) {
-    if (zero) MGC_LAUNCH(launch_jacobi_zero(*b.sv, oth, f, st));
-    else MGC_LAUNCH(launch_jacobi(*b.sv, (const C*)cur, oth, f, st));
+    if (zero && l == 0 && h->pend_norm2) {
+      // the Krylov vector f = w is normalised by the same pass (see issue_arnoldi_step)
+      MGC_LAUNCH(launch_scale_jacobi_zero(*b.sv, const_cast<C*>(f), h->pend_norm2, oth, st));
+      h->pend_norm2 = nullptr;
+    } else if (zero) {
+      MGC_LAUNCH(launch_jacobi_zero(*b.sv, oth, f, st));
+    } else {
+      MGC_LAUNCH(launch_jacobi(*b.sv, (const C*)cur, oth, f, st));
+    }
     zero = false;
     C* tmp = cur; cur = oth; oth = tmp;
   }
@@ -688,7 +696,18 @@ int issue_arnoldi_step(mgcccs_handle* h, int j) {
   C* w = V + (size_t)(j + 1) * N;
   C* zj = kv_Z<C>(h) + (size_t)j * N;
   cplx* col = h->Hh + (size_t)j * (m + 1);
+  // v_j = w_j / |w_j| (|w_j|^2 left in norm_out[1] by step j-1; v_0 is normalised by the
+  // cycle start): fused into the first pre-smoothing sweep of the preconditioner when
+  // the fine level starts one, else a launch of its own
+  if (j > 0) {
+    if (h->p.nu1 >= 1 && h->L > 1 && tail_level<C>(h) > 0) {
+      h->pend_norm2 = h->norm_out + 1;
+    } else {
+      MGC_LAUNCH(launch_scale_by_norm(N, (const C*)vj, vj, h->norm_out + 1, (cplx*)nullptr, nb, st));
+    }
+  }
   int rc = precond<C>(h, zj, vj);
+  h->pend_norm2 = nullptr;
   if (rc) return rc;
   // w = A z_j, with |w|^2 for the reorthogonalisation test; the sum of its partials runs
   // on a side branch beside the first multi-dot (the step is always captured as a graph,
@@ -735,16 +754,11 @@ int issue_arnoldi_step(mgcccs_handle* h, int j) {
                                 st));
     MGC_LAUNCH(launch_sum_partials(h->norm_part, nb, h->norm_out + 1, st, h->gate));
   }
-  // v_{j+1} = w/|w| and the Givens rotation (which takes h_{j+1,j} = |w| from the same
-  // squared norm) on two branches
-  MGC_CUDA(cudaEventRecord(h->fev[2], st));
-  MGC_CUDA(cudaStreamWaitEvent(h->fork_st, h->fev[2], 0));
-  MGC_LAUNCH(launch_givens(j, m, h->Hh, h->cs, h->sn, h->g, h->norm_out + 2, h->norm_out + 1, h->fork_st));
+  // Givens rotation j, taking h_{j+1,j} = |w| from its square; w is normalised at the
+  // start of step j+1 (a cycle that stops here never uses it)
+  MGC_LAUNCH(launch_givens(j, m, h->Hh, h->cs, h->sn, h->g, h->norm_out + 2, h->norm_out + 1, st));
   if (!h->device_loop)
-    MGC_CUDA(cudaMemcpyAsync(h->est_host + j, h->norm_out + 2, sizeof(double), cudaMemcpyDeviceToHost, h->fork_st));
-  MGC_CUDA(cudaEventRecord(h->fev[3], h->fork_st));
-  MGC_LAUNCH(launch_scale_by_norm(N, (const C*)w, w, h->norm_out + 1, (cplx*)nullptr, nb, st));
-  MGC_CUDA(cudaStreamWaitEvent(st, h->fev[3], 0));
+    MGC_CUDA(cudaMemcpyAsync(h->est_host + j, h->norm_out + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
   return MGCCCS_OK;
 }
 
@@ -1291,7 +1305,7 @@ int create_krylov_objects(mgcccs_handle* h) {
   MGC_CUDA(cudaMallocHost(reinterpret_cast<void**>(&h->ctl_host), sizeof(SolveCtl)));
   for (int q = 0; q < 2; ++q) MGC_CUDA(cudaStreamCreateWithFlags(&h->gst[q], cudaStreamNonBlocking));
   MGC_CUDA(cudaStreamCreateWithFlags(&h->fork_st, cudaStreamNonBlocking));
-  for (int q = 0; q < 4; ++q) MGC_CUDA(cudaEventCreateWithFlags(&h->fev[q], cudaEventDisableTiming));
+  for (int q = 0; q < 2; ++q) MGC_CUDA(cudaEventCreateWithFlags(&h->fev[q], cudaEventDisableTiming));
   return MGCCCS_OK;
 }
 
@@ -1720,7 +1734,7 @@ void mgcccs_destroy(mgcccs_t h) {
   for (int q = 0; q < 2; ++q)
     if (h->gst[q]) cudaStreamDestroy(h->gst[q]);
   if (h->fork_st) cudaStreamDestroy(h->fork_st);
-  for (int q = 0; q < 4; ++q)
+  for (int q = 0; q < 2; ++q)
     if (h->fev[q]) cudaEventDestroy(h->fev[q]);
   if (h->est_host) cudaFreeHost(h->est_host);
   if (h->ctl_host) cudaFreeHost(h->ctl_host);
