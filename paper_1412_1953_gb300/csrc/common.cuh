@@ -96,15 +96,25 @@ __host__ __device__ __forceinline__ double2 to_c128(float2 a) { return make_doub
 
 // ---------------------------------------------------------------- level descriptors
 
+// Neighbour coefficients of one axis of one level (Eq. (11)).  Interior indices i < u have
+// both neighbours at the inner grid spacing h e^{i gamma}, so west = east = cin, the closed
+// form -1/(2 h^2) e^{-2 i gamma}.  Indices i >= u (the kink at R0 and the complex-scaled
+// part) read west/east from the per-node arrays, which the setup forms from the node
+// coordinates as Eq. (11) does; u = 0 sends every index there.
+template <class C>
+struct AxisCoefT {
+  int u;
+  int in_real;             // 1: cin has zero imaginary part (a level on the unrotated contour)
+  C cin;
+};
+
 // 5-point operator of one level, (H - E)u = D u + west_x u_W + east_x u_E + west_y u_S + east_y u_N.
-// In the box i < ux, j < uy all four neighbour coefficients equal `cu` (uniform spacing on
-// an unbent part of the contour), which the kernels use to skip the per-node coefficients.
 template <class C>
 struct StencilViewT {
   int mx, my;              // interior nodes per axis (row pitch = mx)
-  int ux, uy;              // uniform box
-  int rbox;                // 1: cu and D are real inside the box (unrotated level, real potential)
-  C cu;                    // uniform neighbour coefficient in the box
+  AxisCoefT<C> cx, cy;     // per-axis uniform regions and their coefficients
+  int rbox;                // 1: both cin real and D real for i < cx.u, j < cy.u (real potential)
+  typename CT<C>::R keep;  // 1 - omega: the share of u an omega-Jacobi update keeps
   const C* west_x;         // [mx]
   const C* east_x;         // [mx]
   const C* west_y;         // [my]
@@ -114,6 +124,160 @@ struct StencilViewT {
 };
 typedef StencilViewT<cplx> StencilView;
 typedef StencilViewT<float2> StencilView32;
+
+// How the nodes of one block take the neighbour coefficients of an axis: all inside the
+// inner region (AX_IN, the closed-form coefficient), all beyond it (AX_ARR, per-node
+// arrays) or straddling it (AX_GEN, a test per node); and how they take D and omega/D:
+// complex (DG_CPLX), real (DG_REAL, the block lies in the real box) or by a test per node
+// (DG_GEN).  The stencil kernels select one instantiation per block, so the per-node code
+// of nearly every block is free of data-dependent branches: the compiler turns such short
+// branches into predicated code, and a warp then issues the FP64 instructions of both
+// sides.  Every instantiation gives the same result at a node: the real forms are the
+// complex ones with zero imaginary parts dropped.
+enum { AX_GEN = 0, AX_IN = 1, AX_ARR = 2 };
+enum { DG_CPLX = 0, DG_REAL = 1, DG_GEN = 2 };
+template <int V>
+struct IntC {
+  static constexpr int value = V;
+};
+
+// acc - (west_i u_m + east_i u_p) along one axis (SUB) or acc + (...) (!SUB), where u_m, u_p
+// are the neighbour values (zero outside the interior).  In the inner region one
+// coefficient multiplies u_m + u_p: 4 FP64 operations per complex value with a real
+// coefficient (IR = 1), 6 with a complex one, against 8 with two per-node coefficients.
+template <int K, int IR, bool SUB, class C>
+__device__ __forceinline__ C axis_acc(const AxisCoefT<C>& a, const C* __restrict__ west, const C* __restrict__ east,
+                                      int i, C um, C up, C acc) {
+  typedef typename CT<C>::R R;
+  if constexpr (K == AX_GEN) {
+    if (i < a.u) return axis_acc<AX_IN, IR, SUB>(a, west, east, i, um, up, acc);
+    return axis_acc<AX_ARR, IR, SUB>(a, west, east, i, um, up, acc);
+  } else if constexpr (K == AX_IN) {
+    const C sm = cadd(um, up);
+    if constexpr (IR) {
+      const R c = SUB ? -a.cin.x : a.cin.x;
+      acc.x = fma(c, sm.x, acc.x);
+      acc.y = fma(c, sm.y, acc.y);
+      return acc;
+    } else {
+      return SUB ? cfms(a.cin, sm, acc) : cfma(a.cin, sm, acc);
+    }
+  } else {
+    const C w = __ldg(west + i), e = __ldg(east + i);
+    return SUB ? cfms(e, up, cfms(w, um, acc)) : cfma(e, up, cfma(w, um, acc));
+  }
+}
+
+// Whether node (i, j) lies in the region where D and omega/D are real.
+template <class C>
+__device__ __forceinline__ bool in_rbox(const StencilViewT<C>& s, int i, int j) {
+  return s.rbox && i < s.cx.u && j < s.cy.u;
+}
+
+template <int DG, class C>
+__device__ __forceinline__ bool diag_real(const StencilViewT<C>& s, int i, int j) {
+  if constexpr (DG == DG_GEN) return in_rbox(s, i, j);
+  else return DG == DG_REAL;
+}
+
+// Real part of a complex array element (only the real word is loaded).
+template <class C>
+__device__ __forceinline__ typename CT<C>::R ldre(const C* __restrict__ a, int p) {
+  return __ldg(reinterpret_cast<const typename CT<C>::R*>(a) + 2 * p);
+}
+
+// f - (H - E)u at node p = (i, j) from the centre value uc, the neighbour values (west,
+// east, south, north) and f_p.
+template <int KX, int KY, int IR, int DG, class C>
+__device__ __forceinline__ C residual_vals(const StencilViewT<C>& s, int i, int j, int p, C uc, C uw, C ue, C us,
+                                           C un, C fp) {
+  typedef typename CT<C>::R R;
+  C t = axis_acc<KX, IR, true>(s.cx, s.west_x, s.east_x, i, uw, ue, fp);
+  t = axis_acc<KY, IR, true>(s.cy, s.west_y, s.east_y, j, us, un, t);
+  if (diag_real<DG>(s, i, j)) {
+    const R d = ldre(s.D, p);
+    t.x = fma(-d, uc.x, t.x);
+    t.y = fma(-d, uc.y, t.y);
+    return t;
+  }
+  return cfms(__ldg(s.D + p), uc, t);
+}
+
+// (H - E)u at node p = (i, j) from the centre and neighbour values.
+template <int KX, int KY, int IR, int DG, class C>
+__device__ __forceinline__ C apply_vals(const StencilViewT<C>& s, int i, int j, int p, C uc, C uw, C ue, C us,
+                                        C un) {
+  typedef typename CT<C>::R R;
+  C a;
+  if (diag_real<DG>(s, i, j)) {
+    const R d = ldre(s.D, p);
+    a.x = d * uc.x;
+    a.y = d * uc.y;
+  } else {
+    a = cmul(__ldg(s.D + p), uc);
+  }
+  a = axis_acc<KX, IR, false>(s.cx, s.west_x, s.east_x, i, uw, ue, a);
+  return axis_acc<KY, IR, false>(s.cy, s.west_y, s.east_y, j, us, un, a);
+}
+
+// One omega-Jacobi update u + (omega/D)(f - (H - E)u) at node p = (i, j), evaluated as
+// (1 - omega) u + (omega/D)(f - N u) with N the off-diagonal part of H - E: the diagonal
+// term (omega/D) D u is omega u, so D is not read.  FP64 operations per node: 12 where
+// the coefficients and omega/D are real, 18 with one complex-scaled axis, 22 with two.
+template <int KX, int KY, int IR, int DG, class C>
+__device__ __forceinline__ C jacobi_vals(const StencilViewT<C>& s, int i, int j, int p, C uc, C uw, C ue, C us,
+                                         C un, C fp) {
+  typedef typename CT<C>::R R;
+  C t = axis_acc<KX, IR, true>(s.cx, s.west_x, s.east_x, i, uw, ue, fp);
+  t = axis_acc<KY, IR, true>(s.cy, s.west_y, s.east_y, j, us, un, t);
+  C o = cscal(s.keep, uc);
+  if (diag_real<DG>(s, i, j)) {
+    const R di = ldre(s.Dinv, p);
+    o.x = fma(di, t.x, o.x);
+    o.y = fma(di, t.y, o.y);
+    return o;
+  }
+  return cfma(__ldg(s.Dinv + p), t, o);
+}
+
+// Kind of an axis for the index range [lo, hi) of a block.
+template <class C>
+__device__ __forceinline__ int axis_kind(const AxisCoefT<C>& a, int lo, int hi) {
+  return hi <= a.u ? AX_IN : (lo >= a.u ? AX_ARR : AX_GEN);
+}
+
+template <int KX, int KY, class F>
+__device__ __forceinline__ void dispatch_ir_dg(bool ir, bool rb, F& f) {
+  if constexpr (KX == AX_ARR || KY == AX_ARR) {
+    if (ir) f(IntC<KX>(), IntC<KY>(), IntC<1>(), IntC<DG_CPLX>());
+    else f(IntC<KX>(), IntC<KY>(), IntC<0>(), IntC<DG_CPLX>());
+  } else {
+    constexpr int DGR = (KX == AX_IN && KY == AX_IN) ? DG_REAL : DG_GEN;
+    if (rb) f(IntC<KX>(), IntC<KY>(), IntC<1>(), IntC<DGR>());   // a real box needs real inner coefficients
+    else if (ir) f(IntC<KX>(), IntC<KY>(), IntC<1>(), IntC<DG_CPLX>());
+    else f(IntC<KX>(), IntC<KY>(), IntC<0>(), IntC<DG_CPLX>());
+  }
+}
+
+// Calls f(IntC<KX>, IntC<KY>, IntC<IR>, IntC<DG>) with the kinds of the block covering
+// interior indices [i0, i1) x [j0, j1) (clipped to the interior by the caller).
+template <class C, class F>
+__device__ __forceinline__ void dispatch_kinds(const StencilViewT<C>& s, int i0, int i1, int j0, int j1, F&& f) {
+  const int kx = axis_kind(s.cx, i0, i1), ky = axis_kind(s.cy, j0, j1);
+  const bool ir = s.cx.in_real && s.cy.in_real;
+  const bool rb = s.rbox && ir;
+  switch (kx * 3 + ky) {
+    case AX_GEN * 3 + AX_GEN: dispatch_ir_dg<AX_GEN, AX_GEN>(ir, rb, f); break;
+    case AX_GEN * 3 + AX_IN: dispatch_ir_dg<AX_GEN, AX_IN>(ir, rb, f); break;
+    case AX_GEN * 3 + AX_ARR: dispatch_ir_dg<AX_GEN, AX_ARR>(ir, rb, f); break;
+    case AX_IN * 3 + AX_GEN: dispatch_ir_dg<AX_IN, AX_GEN>(ir, rb, f); break;
+    case AX_IN * 3 + AX_IN: dispatch_ir_dg<AX_IN, AX_IN>(ir, rb, f); break;
+    case AX_IN * 3 + AX_ARR: dispatch_ir_dg<AX_IN, AX_ARR>(ir, rb, f); break;
+    case AX_ARR * 3 + AX_GEN: dispatch_ir_dg<AX_ARR, AX_GEN>(ir, rb, f); break;
+    case AX_ARR * 3 + AX_IN: dispatch_ir_dg<AX_ARR, AX_IN>(ir, rb, f); break;
+    default: dispatch_ir_dg<AX_ARR, AX_ARR>(ir, rb, f); break;
+  }
+}
 
 // One level of the fused coarse-level V-cycle (k_vcycle_tail): stencil, iterate,
 // right-hand side, smoother scratch and residual.

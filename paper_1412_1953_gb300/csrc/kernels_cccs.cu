@@ -25,34 +25,12 @@ __device__ __forceinline__ C ldz(const C* __restrict__ a, int p, bool ok) {
   return ok ? __ldg(a + p) : CT<C>::make(0.0, 0.0);
 }
 
-template <class C>
+template <int KX, int KY, int IR, int DG, class C>
 __device__ __forceinline__ C residual_at(const StencilViewT<C>& s, const C* __restrict__ u, const C* __restrict__ f,
                                          int i, int j) {
-  typedef typename CT<C>::R R;
   const int p = j * s.mx + i;
-  C uc = __ldg(u + p);
-  C uw = ldz(u, p - 1, i > 0);
-  C ue = ldz(u, p + 1, i + 1 < s.mx);
-  C us = ldz(u, p - s.mx, j > 0);
-  C un = ldz(u, p + s.mx, j + 1 < s.my);
-  C a;
-  if (s.rbox && i < s.ux && j < s.uy) {
-    C sum = cadd(cadd(uw, ue), cadd(us, un));
-    const R d = __ldg(reinterpret_cast<const R*>(s.D) + 2 * p);
-    a.x = fma(s.cu.x, sum.x, d * uc.x);
-    a.y = fma(s.cu.x, sum.y, d * uc.y);
-    return csub(__ldg(f + p), a);
-  }
-  a = cmul(__ldg(s.D + p), uc);
-  if (i < s.ux && j < s.uy) {
-    a = cfma(s.cu, cadd(cadd(uw, ue), cadd(us, un)), a);
-  } else {
-    a = cfma(__ldg(s.west_x + i), uw, a);
-    a = cfma(__ldg(s.east_x + i), ue, a);
-    a = cfma(__ldg(s.west_y + j), us, a);
-    a = cfma(__ldg(s.east_y + j), un, a);
-  }
-  return csub(__ldg(f + p), a);
+  return residual_vals<KX, KY, IR, DG>(s, i, j, p, __ldg(u + p), ldz(u, p - 1, i > 0), ldz(u, p + 1, i + 1 < s.mx),
+                                       ldz(u, p - s.mx, j > 0), ldz(u, p + s.mx, j + 1 < s.my), __ldg(f + p));
 }
 
 // One 32 x 32 tile per block: each thread computes the residual at four nodes into a
@@ -68,11 +46,16 @@ __global__ void __launch_bounds__(TX * WY) k_residual_project(StencilViewT<C> s,
   const int wy = threadIdx.y;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int i = i0 + lane;
-  for (int q = 0; q < SY; ++q) {
-    const int row = q * WY + wy;
-    const int j = j0 + row;
-    R[row][lane] = (i < s.mx && j < s.my) ? residual_at(s, u, f, i, j) : CT<C>::make(0.0, 0.0);
-  }
+  dispatch_kinds(s, i0, min(i0 + TX, s.mx), j0, min(j0 + TY, s.my), [&](auto kx, auto ky, auto ir, auto dg) {
+    for (int q = 0; q < SY; ++q) {
+      const int row = q * WY + wy;
+      const int j = j0 + row;
+      R[row][lane] = (i < s.mx && j < s.my)
+                         ? residual_at<decltype(kx)::value, decltype(ky)::value, decltype(ir)::value,
+                                       decltype(dg)::value>(s, u, f, i, j)
+                         : CT<C>::make(0.0, 0.0);
+    }
+  });
   __syncthreads();
   const int t = wy * TX + lane;
   for (int w = t; w < 2 * TX * NB; w += TX * WY) {

@@ -7,7 +7,7 @@
 // over the element type C: double2 (complex128, the plain path, bound by the FP64
 // pipe on this GPU) or float2 (complex64, the mixed-precision smoother and transfers,
 // bound by HBM).  Each output is computed exactly once (no overlapped halo
-// recomputation) and the uniform-spacing box uses a single neighbour coefficient.
+// recomputation) and the uniform parts of each axis use a single neighbour coefficient.
 #include "common.cuh"
 
 namespace {
@@ -28,76 +28,52 @@ __device__ __forceinline__ C ldz(const C* __restrict__ a, int p, bool ok) {
   return ok ? ldm<NC>(a + p) : CT<C>::make(0.0, 0.0);
 }
 
+// The four neighbour values of interior node p = (i, j) (zero outside the interior).
+#define MGC_NEIGHBOURS(NC, s, u, p, i, j)                                                             \
+  ldz<NC>(u, (p) - 1, (i) > 0), ldz<NC>(u, (p) + 1, (i) + 1 < (s).mx), ldz<NC>(u, (p) - (s).mx, (j) > 0), \
+      ldz<NC>(u, (p) + (s).mx, (j) + 1 < (s).my)
+
+// Template arguments of the per-node helpers from the IntC arguments of dispatch_kinds.
+#define MGC_KINDS(kx, ky, ir, dg) decltype(kx)::value, decltype(ky)::value, decltype(ir)::value, decltype(dg)::value
+
 // (H - E) u at interior node (i, j), given the centre value uc.
-template <bool NC, class C>
-__device__ __forceinline__ C apply_op(const StencilViewT<C>& s, const C* __restrict__ u, int i, int j, C uc) {
+template <int KX, int KY, int IR, int DG, bool NC, class C>
+__device__ __forceinline__ C apply_pt(const StencilViewT<C>& s, const C* __restrict__ u, int i, int j, C uc) {
   const int p = j * s.mx + i;
-  C uw = ldz<NC>(u, p - 1, i > 0);
-  C ue = ldz<NC>(u, p + 1, i + 1 < s.mx);
-  C us = ldz<NC>(u, p - s.mx, j > 0);
-  C un = ldz<NC>(u, p + s.mx, j + 1 < s.my);
-  C a = cmul(__ldg(s.D + p), uc);
-  if (i < s.ux && j < s.uy) {
-    C sum = cadd(cadd(uw, ue), cadd(us, un));
-    a = cfma(s.cu, sum, a);
-  } else {
-    a = cfma(__ldg(s.west_x + i), uw, a);
-    a = cfma(__ldg(s.east_x + i), ue, a);
-    a = cfma(__ldg(s.west_y + j), us, a);
-    a = cfma(__ldg(s.east_y + j), un, a);
-  }
-  return a;
-}
-
-// Real part of a complex array element (only the real word is loaded).
-template <class C>
-__device__ __forceinline__ typename CT<C>::R ldre(const C* __restrict__ a, int p) {
-  return __ldg(reinterpret_cast<const typename CT<C>::R*>(a) + 2 * p);
-}
-
-// (H - E) u in the real box: real coefficient cu.x and real diagonal.
-template <bool NC, class C>
-__device__ __forceinline__ C apply_op_rbox(const StencilViewT<C>& s, const C* __restrict__ u, int i, int j, C uc) {
-  const int p = j * s.mx + i;
-  C sum = cadd(cadd(ldz<NC>(u, p - 1, i > 0), ldz<NC>(u, p + 1, i + 1 < s.mx)),
-               cadd(ldz<NC>(u, p - s.mx, j > 0), ldz<NC>(u, p + s.mx, j + 1 < s.my)));
-  const typename CT<C>::R d = ldre(s.D, p);
-  C a;
-  a.x = fma(s.cu.x, sum.x, d * uc.x);
-  a.y = fma(s.cu.x, sum.y, d * uc.y);
-  return a;
-}
-
-template <bool NC, class C>
-__device__ __forceinline__ C apply_any(const StencilViewT<C>& s, const C* __restrict__ u, int i, int j, C uc) {
-  return (s.rbox && i < s.ux && j < s.uy) ? apply_op_rbox<NC>(s, u, i, j, uc) : apply_op<NC>(s, u, i, j, uc);
+  return apply_vals<KX, KY, IR, DG>(s, i, j, p, uc, MGC_NEIGHBOURS(NC, s, u, p, i, j));
 }
 
 // ---- per-node arithmetic shared by the one-step kernels and the fused coarse-level kernel
 
 // One omega-Jacobi update at (i, j): u + (omega/D)(f - (H-E)u).
-template <bool NC, class C>
+template <int KX, int KY, int IR, int DG, bool NC, class C>
 __device__ __forceinline__ C jacobi_pt(const StencilViewT<C>& s, const C* __restrict__ u_in,
                                        const C* __restrict__ f, int i, int j) {
   const int p = j * s.mx + i;
-  C uc = ldm<NC>(u_in + p);
-  if (s.rbox && i < s.ux && j < s.uy) {
-    C r = csub(ldm<NC>(f + p), apply_op_rbox<NC>(s, u_in, i, j, uc));
-    const typename CT<C>::R di = ldre(s.Dinv, p);
-    C o;
-    o.x = fma(di, r.x, uc.x);
-    o.y = fma(di, r.y, uc.y);
-    return o;
-  }
-  C r = csub(ldm<NC>(f + p), apply_op<NC>(s, u_in, i, j, uc));
-  return cfma(__ldg(s.Dinv + p), r, uc);
+  return jacobi_vals<KX, KY, IR, DG>(s, i, j, p, ldm<NC>(u_in + p), MGC_NEIGHBOURS(NC, s, u_in, p, i, j),
+                                     ldm<NC>(f + p));
 }
 
-template <bool NC, class C>
+template <int KX, int KY, int IR, int DG, bool NC, class C>
 __device__ __forceinline__ C residual_pt(const StencilViewT<C>& s, const C* __restrict__ u, const C* __restrict__ f,
                                          int i, int j) {
   const int p = j * s.mx + i;
-  return csub(ldm<NC>(f + p), apply_any<NC>(s, u, i, j, ldm<NC>(u + p)));
+  return residual_vals<KX, KY, IR, DG>(s, i, j, p, ldm<NC>(u + p), MGC_NEIGHBOURS(NC, s, u, p, i, j),
+                                       ldm<NC>(f + p));
+}
+
+// dispatch_kinds for the BX x BY block of this thread.
+template <class C, class F>
+__device__ __forceinline__ void block_kinds(const StencilViewT<C>& s, F&& f) {
+  const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
+  dispatch_kinds(s, i0, min(i0 + BX, s.mx), j0, min(j0 + BY, s.my), f);
+}
+
+// Whole-level kinds (the fused coarse-level kernel): a test per node.
+template <class C, class F>
+__device__ __forceinline__ void level_kinds(const StencilViewT<C>& s, F&& f) {
+  const bool ir = s.cx.in_real && s.cy.in_real;
+  dispatch_ir_dg<AX_GEN, AX_GEN>(ir, s.rbox && ir, f);
 }
 
 // Full weighting 1/16 [1 2 1; 2 4 2; 1 2 1] onto coarse interior node (I, J), which sits
@@ -160,7 +136,9 @@ __global__ void __launch_bounds__(BX * BY) k_jacobi(StencilViewT<C> s, const C* 
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   if (i >= s.mx || j >= s.my) return;
-  u_out[j * s.mx + i] = jacobi_pt<true>(s, u_in, f, i, j);
+  block_kinds(s, [&](auto kx, auto ky, auto ir, auto dg) {
+    u_out[j * s.mx + i] = jacobi_pt<MGC_KINDS(kx, ky, ir, dg), true>(s, u_in, f, i, j);
+  });
 }
 
 // First sweep from a zero initial guess: u = omega D^{-1} f.
@@ -235,9 +213,11 @@ __global__ void __launch_bounds__(BX * BY) k_residual(StencilViewT<C> s, const C
   typename CT<C>::R n2 = 0;
   if (i < s.mx && j < s.my) {
     const int p = j * s.mx + i;
-    C rv = residual_pt<true>(s, u, f, i, j);
-    if (r) r[p] = rv;
-    n2 = cabs2(rv);
+    block_kinds(s, [&](auto kx, auto ky, auto ir, auto dg) {
+      C rv = residual_pt<MGC_KINDS(kx, ky, ir, dg), true>(s, u, f, i, j);
+      if (r) r[p] = rv;
+      n2 = cabs2(rv);
+    });
   }
   if (norm_part) {
     double tot = block_sum_r<BX * BY>(n2, sh);
@@ -284,19 +264,24 @@ template <class C>
 __device__ __forceinline__ void tail_jacobi(const StencilViewT<C>& s, const C* __restrict__ u, C* __restrict__ o,
                                             const C* __restrict__ f, bool zero) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int j = ty; j < s.my; j += TAIL_WARPS)
-    for (int i = tx; i < s.mx; i += 32) {
-      const int p = j * s.mx + i;
-      o[p] = zero ? cmul(__ldg(s.Dinv + p), ldm<false>(f + p)) : jacobi_pt<false>(s, u, f, i, j);
-    }
+  level_kinds(s, [&](auto kx, auto ky, auto ir, auto dg) {
+    for (int j = ty; j < s.my; j += TAIL_WARPS)
+      for (int i = tx; i < s.mx; i += 32) {
+        const int p = j * s.mx + i;
+        o[p] = zero ? cmul(__ldg(s.Dinv + p), ldm<false>(f + p))
+                    : jacobi_pt<MGC_KINDS(kx, ky, ir, dg), false>(s, u, f, i, j);
+      }
+  });
 }
 
 template <class C>
 __device__ __forceinline__ void tail_residual(const StencilViewT<C>& s, const C* __restrict__ u,
                                               const C* __restrict__ f, C* __restrict__ r) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int j = ty; j < s.my; j += TAIL_WARPS)
-    for (int i = tx; i < s.mx; i += 32) r[j * s.mx + i] = residual_pt<false>(s, u, f, i, j);
+  level_kinds(s, [&](auto kx, auto ky, auto ir, auto dg) {
+    for (int j = ty; j < s.my; j += TAIL_WARPS)
+      for (int i = tx; i < s.mx; i += 32) r[j * s.mx + i] = residual_pt<MGC_KINDS(kx, ky, ir, dg), false>(s, u, f, i, j);
+  });
 }
 
 template <class C>
@@ -408,9 +393,11 @@ __global__ void __launch_bounds__(BX * BY) k_apply(StencilViewT<C> s, const C* _
   typename CT<C>::R n2 = 0;
   if (i < s.mx && j < s.my) {
     const int p = j * s.mx + i;
-    C v = apply_any<true>(s, x, i, j, __ldg(x + p));
-    y[p] = v;
-    n2 = cabs2(v);
+    block_kinds(s, [&](auto kx, auto ky, auto ir, auto dg) {
+      C v = apply_pt<MGC_KINDS(kx, ky, ir, dg), true>(s, x, i, j, __ldg(x + p));
+      y[p] = v;
+      n2 = cabs2(v);
+    });
   }
   if (norm_part) {
     double tot = block_sum_r<BX * BY>(n2, sh);

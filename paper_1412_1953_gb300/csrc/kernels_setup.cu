@@ -653,8 +653,9 @@ cudaError_t launch_compare(int n, const cplx* a, const cplx* b, int* flag, cudaS
 }
 
 cudaError_t launch_box_real_check(const StencilView& s, int* flag, cudaStream_t st) {
-  if (s.ux <= 0 || s.uy <= 0) return cudaSuccess;
-  k_box_real_check<<<dim3((s.ux + 31) / 32, (s.uy + 7) / 8), dim3(32, 8), 0, st>>>(s.mx, s.ux, s.uy, s.D, flag);
+  if (s.cx.u <= 0 || s.cy.u <= 0) return cudaSuccess;
+  k_box_real_check<<<dim3((s.cx.u + 31) / 32, (s.cy.u + 7) / 8), dim3(32, 8), 0, st>>>(s.mx, s.cx.u, s.cy.u, s.D,
+                                                                                        flag);
   return cudaGetLastError();
 }
 

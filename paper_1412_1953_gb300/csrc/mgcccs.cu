@@ -298,6 +298,24 @@ int uniform_count(int n, double L, double R0) {
   return cnt;
 }
 
+// Inner uniform region of one axis and its coefficient (Eq. (11) with equal adjacent
+// cells h e^{i gamma}: west = east = -1/(2 h^2) e^{-2 i gamma}).
+AxisCoefT<cplx> axis_coef(int n, double L, double R0, double gamma) {
+  AxisCoefT<cplx> a;
+  const double h = L / n, c = -0.5 / (h * h);
+  a.u = uniform_count(n, L, R0);
+  a.cin = cmk(c * std::cos(2.0 * gamma), -c * std::sin(2.0 * gamma));
+  a.in_real = a.cin.y == 0.0;
+  return a;
+}
+
+AxisCoefT<float2> axis_coef32(const AxisCoefT<cplx>& a) {
+  AxisCoefT<float2> b;
+  b.u = a.u; b.in_real = a.in_real;
+  b.cin = make_float2((float)a.cin.x, (float)a.cin.y);
+  return b;
+}
+
 #define MGC_LAUNCH(expr)                         \
   do {                                           \
     cudaError_t e_ = (expr);                     \
@@ -355,25 +373,16 @@ int do_setup(mgcccs_handle* h, const cplx* v1, const cplx* v2, const cplx* v12, 
     s.mx = b.mx; s.my = b.my;
     s.west_x = b.west_x; s.east_x = b.east_x; s.west_y = b.west_y; s.east_y = b.east_y;
     s.D = b.D; s.Dinv = b.Dinv;
-    const double hx = p.Lx / b.nxc, hy = p.Ly / b.nyc;
-    if (hx == hy) {
-      s.ux = uniform_count(b.nxc, p.Lx, p.R0x);
-      s.uy = uniform_count(b.nyc, p.Ly, p.R0y);
-      // -1/(2 h^2) e^{-2 i gamma}
-      const double a = -0.5 / (hx * hx);
-      s.cu = cmk(a * std::cos(2.0 * b.gamma), -a * std::sin(2.0 * b.gamma));
-      if (s.ux == 0 || s.uy == 0) s.ux = s.uy = 0;
-    } else {
-      s.ux = s.uy = 0;
-      s.cu = cmk(0.0, 0.0);
-    }
+    s.cx = axis_coef(b.nxc, p.Lx, p.R0x, b.gamma);
+    s.cy = axis_coef(b.nyc, p.Ly, p.R0y, b.gamma);
+    s.keep = 1.0 - p.omega;
     s.rbox = 0;
   }
-  // a level whose uniform box has a real coefficient and a real diagonal everywhere
-  // uses the real-coefficient path there (scan on the device, flag read back)
+  // a level whose inner coefficients are real and whose diagonal is real on the inner
+  // box uses real arithmetic for D and omega/D there (scan on the device, flag read back)
   for (int l = 0; l < h->L; ++l) {
     StencilView& s = h->lv[l].sv;
-    if (s.ux > 0 && s.cu.y == 0.0) {
+    if (s.cx.u > 0 && s.cy.u > 0 && s.cx.in_real && s.cy.in_real) {
       int complex_seen = 0;
       MGC_CUDA(cudaMemsetAsync(h->status + 3, 0, sizeof(int), st));
       MGC_LAUNCH(launch_box_real_check(s, h->status + 3, st));
@@ -437,8 +446,9 @@ int do_setup(mgcccs_handle* h, const cplx* v1, const cplx* v2, const cplx* v12, 
     MGC_LAUNCH(launch_round_copy(n2, b.D, b.D32, st));
     MGC_LAUNCH(launch_round_copy(n2, b.Dinv, b.Dinv32, st));
     StencilView32& s3 = b.sv32;
-    s3.mx = b.mx; s3.my = b.my; s3.ux = b.sv.ux; s3.uy = b.sv.uy; s3.rbox = b.sv.rbox;
-    s3.cu = make_float2((float)b.sv.cu.x, (float)b.sv.cu.y);
+    s3.mx = b.mx; s3.my = b.my; s3.rbox = b.sv.rbox;
+    s3.cx = axis_coef32(b.sv.cx); s3.cy = axis_coef32(b.sv.cy);
+    s3.keep = (float)b.sv.keep;
     s3.west_x = b.west_x32; s3.east_x = b.east_x32; s3.west_y = b.west_y32; s3.east_y = b.east_y32;
     s3.D = b.D32; s3.Dinv = b.Dinv32;
   }
