@@ -62,11 +62,11 @@ __device__ __forceinline__ C residual_pt(const StencilViewT<C>& s, const C* __re
                                        ldm<NC>(f + p));
 }
 
-// dispatch_kinds for the BX x BY block of this thread.
+// dispatch_kinds for the block of this thread.
 template <class C, class F>
 __device__ __forceinline__ void block_kinds(const StencilViewT<C>& s, F&& f) {
-  const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
-  dispatch_kinds(s, i0, min(i0 + BX, s.mx), j0, min(j0 + BY, s.my), f);
+  const int i0 = blockIdx.x * blockDim.x, j0 = blockIdx.y * blockDim.y;
+  dispatch_kinds(s, i0, min(i0 + (int)blockDim.x, s.mx), j0, min(j0 + (int)blockDim.y, s.my), f);
 }
 
 // Whole-level kinds (the fused coarse-level kernel): a test per node.
@@ -133,8 +133,8 @@ __device__ __forceinline__ void coarse_row(int nc, const cplx* __restrict__ Ainv
 template <class C>
 __global__ void __launch_bounds__(BX * BY) k_jacobi(StencilViewT<C> s, const C* __restrict__ u_in,
                                                     C* __restrict__ u_out, const C* __restrict__ f) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= s.mx || j >= s.my) return;
   block_kinds(s, [&](auto kx, auto ky, auto ir, auto dg) {
     u_out[j * s.mx + i] = jacobi_pt<MGC_KINDS(kx, ky, ir, dg), true>(s, u_in, f, i, j);
@@ -208,8 +208,8 @@ __global__ void __launch_bounds__(BX * BY) k_residual(StencilViewT<C> s, const C
                                                       const C* __restrict__ f, C* __restrict__ r,
                                                       double* __restrict__ norm_part) {
   __shared__ double sh[BX * BY / 32];
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
   typename CT<C>::R n2 = 0;
   if (i < s.mx && j < s.my) {
     const int p = j * s.mx + i;
@@ -228,21 +228,56 @@ __global__ void __launch_bounds__(BX * BY) k_residual(StencilViewT<C> s, const C
 template <class C>
 __global__ void __launch_bounds__(256) k_restrict(int mx, int mcx, int mcy, const C* __restrict__ r,
                                                   C* __restrict__ rc) {
-  const int I = blockIdx.x * 32 + threadIdx.x;
-  const int J = blockIdx.y * 8 + threadIdx.y;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= mcx || J >= mcy) return;
   rc[J * mcx + I] = restrict_pt<true>(mx, r, I, J);
 }
 
-// u += bilinear interpolation of the coarse correction (fine node k = i+1).
+// u += bilinear interpolation of the coarse correction, one thread per coarse cell
+// [K, K+1] x [L, L+1] (coarse nodes; 0 and mc+1 are the boundary): the fine nodes
+// k = 2K+1, 2K+2 by l = 2L+1, 2L+2 inside it share the cell's corner values and pair
+// sums, so the four updates take 16 FP64 operations and no thread takes a parity branch.
+// Each sum is formed in the order prolong_pt uses, so the results are the same.
 template <class C>
 __global__ void __launch_bounds__(BX * BY) k_prolong_add(int mx, int my, int mcx, int mcy, const C* __restrict__ ec,
                                                          C* __restrict__ u) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  if (i >= mx || j >= my) return;
-  const int p = j * mx + i;
-  u[p] = cadd(u[p], prolong_pt<true>(mcx, mcy, ec, i, j));
+  typedef typename CT<C>::R R;
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  const int L = blockIdx.y * blockDim.y + threadIdx.y;
+  if (K > mcx || L > mcy) return;
+  const C a = coarse_at<true>(ec, mcx, mcy, K, L), b = coarse_at<true>(ec, mcx, mcy, K + 1, L);
+  const C c = coarse_at<true>(ec, mcx, mcy, K, L + 1), d = coarse_at<true>(ec, mcx, mcy, K + 1, L + 1);
+  const int i = 2 * K, j = 2 * L;             // fine interior indices of the nodes k = 2K+1, l = 2L+1
+  const bool xe = i + 1 < mx, ye = j + 1 < my;  // whether k = 2K+2 (l = 2L+2) is interior
+  const C cd = cadd(c, d);
+  {
+    const C s4 = cadd(cadd(a, b), cd);
+    C& v = u[j * mx + i];
+    C w = v;
+    w.x = fma(R(0.25), s4.x, w.x);
+    w.y = fma(R(0.25), s4.y, w.y);
+    v = w;
+  }
+  if (xe) {
+    const C bd = cadd(b, d);
+    C& v = u[j * mx + i + 1];
+    C w = v;
+    w.x = fma(R(0.5), bd.x, w.x);
+    w.y = fma(R(0.5), bd.y, w.y);
+    v = w;
+  }
+  if (ye) {
+    C& v = u[(j + 1) * mx + i];
+    C w = v;
+    w.x = fma(R(0.5), cd.x, w.x);
+    w.y = fma(R(0.5), cd.y, w.y);
+    v = w;
+    if (xe) {
+      C& v2 = u[(j + 1) * mx + i + 1];
+      v2 = cadd(v2, d);
+    }
+  }
 }
 
 // Coarsest level: u = A_c^{-1} f with the FP64 dense inverse built at setup; one warp
@@ -388,8 +423,8 @@ template <class C>
 __global__ void __launch_bounds__(BX * BY) k_apply(StencilViewT<C> s, const C* __restrict__ x, C* __restrict__ y,
                                                    double* __restrict__ norm_part) {
   __shared__ double sh[BX * BY / 32];
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
   typename CT<C>::R n2 = 0;
   if (i < s.mx && j < s.my) {
     const int p = j * s.mx + i;
@@ -446,6 +481,11 @@ __global__ void __launch_bounds__(256) k_round_copy(long long n, const cplx* __r
 
 inline dim3 grid2(int mx, int my) { return dim3((mx + BX - 1) / BX, (my + BY - 1) / BY); }
 
+// Block height for a level of mx x my nodes: 64-thread blocks below two full 256-thread
+// blocks per SM, so the work of a small level spreads over more SMs' FP64 pipes.
+inline int level_by(int mx, int my) { return (long long)mx * my < 2LL * 152 * BX * BY ? 2 : BY; }
+inline dim3 level_grid(int mx, int my, int by) { return dim3((mx + BX - 1) / BX, (my + by - 1) / by); }
+
 inline unsigned stride_blocks(long long n) {
   long long b = (n + 255) / 256;
   return (unsigned)(b < 1216 ? (b < 1 ? 1 : b) : 1216);
@@ -455,7 +495,8 @@ inline unsigned stride_blocks(long long n) {
 
 template <class C>
 cudaError_t launch_jacobi(const StencilViewT<C>& s, const C* u_in, C* u_out, const C* f, cudaStream_t st) {
-  k_jacobi<C><<<grid2(s.mx, s.my), dim3(BX, BY), 0, st>>>(s, u_in, u_out, f);
+  const int by = level_by(s.mx, s.my);
+  k_jacobi<C><<<level_grid(s.mx, s.my, by), dim3(BX, by), 0, st>>>(s, u_in, u_out, f);
   return cudaGetLastError();
 }
 
@@ -483,21 +524,25 @@ int residual_norm_blocks(const StencilViewT<C>& s) {
 template <class C>
 cudaError_t launch_residual(const StencilViewT<C>& s, const C* u, const C* f, C* r, double* norm_part,
                             cudaStream_t st) {
-  k_residual<C><<<grid2(s.mx, s.my), dim3(BX, BY), 0, st>>>(s, u, f, r, norm_part);
+  const int by = norm_part ? BY : level_by(s.mx, s.my);   // norm partials: one per full block
+  k_residual<C><<<level_grid(s.mx, s.my, by), dim3(BX, by), 0, st>>>(s, u, f, r, norm_part);
   return cudaGetLastError();
 }
 
 template <class C>
 cudaError_t launch_restrict(int mx, int my, const C* r, C* rc, cudaStream_t st) {
   int mcx = (mx - 1) / 2, mcy = (my - 1) / 2;
-  k_restrict<C><<<dim3((mcx + 31) / 32, (mcy + 7) / 8), dim3(32, 8), 0, st>>>(mx, mcx, mcy, r, rc);
+  const int by = level_by(mcx, mcy);
+  k_restrict<C><<<level_grid(mcx, mcy, by), dim3(BX, by), 0, st>>>(mx, mcx, mcy, r, rc);
   return cudaGetLastError();
 }
 
 template <class C>
 cudaError_t launch_prolong_add(int mx, int my, const C* ec, C* u, cudaStream_t st) {
   int mcx = (mx - 1) / 2, mcy = (my - 1) / 2;
-  k_prolong_add<C><<<grid2(mx, my), dim3(BX, BY), 0, st>>>(mx, my, mcx, mcy, ec, u);
+  if (mx != 2 * mcx + 1 || my != 2 * mcy + 1) return cudaErrorInvalidValue;   // coarse = every other fine node
+  const int by = level_by(mcx + 1, mcy + 1);
+  k_prolong_add<C><<<dim3((mcx + BX) / BX, (mcy + by) / by), dim3(BX, by), 0, st>>>(mx, my, mcx, mcy, ec, u);
   return cudaGetLastError();
 }
 
@@ -515,7 +560,8 @@ cudaError_t launch_vcycle_tail(const TailArgs<C>& a, cudaStream_t st) {
 
 template <class C>
 cudaError_t launch_apply(const StencilViewT<C>& s, const C* x, C* y, cudaStream_t st, double* norm_part) {
-  k_apply<C><<<grid2(s.mx, s.my), dim3(BX, BY), 0, st>>>(s, x, y, norm_part);
+  const int by = norm_part ? BY : level_by(s.mx, s.my);
+  k_apply<C><<<level_grid(s.mx, s.my, by), dim3(BX, by), 0, st>>>(s, x, y, norm_part);
   return cudaGetLastError();
 }
 
