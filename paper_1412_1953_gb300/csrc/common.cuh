@@ -417,8 +417,6 @@ typedef CCViewT<float2> CCView32;
 // One coupled-channel system (Eqs. (28)-(29)) with its parallel-cyclic-reduction factors.
 struct CRSystem {
   int m, nb;
-  cplx* X;                 // [m*nb] reduced right-hand side (solve scratch)
-  cplx* Y;                 // [m*nb] second buffer of the levels
   const cplx* r;           // [nb][m] right-hand side
   cplx* e;                 // [nb][m] solution
   float2* e32;             // [nb][m] solution rounded to complex64 (mixed precision), or null
@@ -438,7 +436,7 @@ cudaError_t launch_residual_project(const StencilViewT<C>& s, const CCViewT<C>& 
                                     cudaStream_t st);
 template <class C>
 cudaError_t launch_cc_rhs(const CCViewT<C>& c, cudaStream_t st);
-cudaError_t channel_solve_prepare(int nb);
+cudaError_t channel_solve_prepare(int nb, int m_max);
 cudaError_t launch_channel_solve(const CRSystem& A, const CRSystem& B, cudaStream_t st);
 template <class C>
 cudaError_t launch_cccs_correct(const CCViewT<C>& c, C* u, cudaStream_t st);

@@ -11,7 +11,13 @@
 // The projections are fused into the residual pass and reduced deterministically:
 // per 32 x 32 tile, sums along x and along y through a shared-memory tile give
 // per-tile partials, which a second kernel sums in a fixed order.
+#include <cooperative_groups.h>
+
+#include <mutex>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -187,55 +193,75 @@ __device__ __forceinline__ cplx dot_row(const cplx (&a)[NB], const cplx* x) {
 // reduction (2 log2 m dependent levels on half the rows) this halves the dependent levels
 // for log2(m)/2 times the arithmetic, which 16-CTA clusters absorb: 37 us against 57 us
 // per CCCS at 1023 rows, n_b = 3.
+// Rows per CTA when one 16-CTA cluster holds the m block rows of a system.
+__host__ __device__ __forceinline__ int cr_rows(int m) { return (m + CR_CLUSTER - 1) / CR_CLUSTER; }
+
+// One system per 16-CTA cluster.  CTA `rank` owns block rows [rank R, rank R + R) and keeps
+// their current right-hand sides in its shared memory (two buffers, one per parity of the
+// level); a level reads rows k - s and k + s from the shared memory of the CTAs that own
+// them (distributed shared memory), and the split cluster barrier between levels orders
+// those reads against the next level's writes.  The factor rows of the next level are
+// fetched between the barrier's arrive and wait.
 template <int NB>
 __global__ void __cluster_dims__(CR_CLUSTER, 1, 1) __launch_bounds__(CR_THREADS)
 k_channel_solve_pcr(CRSystem SA, CRSystem SB) {
+  extern __shared__ cplx cr_x[];   // [2][R * NB]
+  cg::cluster_group cl = cg::this_cluster();
   const int sys = blockIdx.x / CR_CLUSTER;
-  const int rank = blockIdx.x % CR_CLUSTER;
+  const int rank = (int)cl.block_rank();
   const CRSystem S = sys == 0 ? SA : SB;
   constexpr int nb2 = NB * NB;
   const int m = S.m, pq = S.pq;
-  const int t0 = rank * CR_THREADS + threadIdx.x, nt = CR_CLUSTER * CR_THREADS;
-  const int total = m * NB;
-  cplx* X = S.X;
-  cplx* Y = S.Y;
-  for (int idx = t0; idx < total; idx += nt) {
-    const int k = idx / NB, comp = idx % NB;
-    X[idx] = S.r[comp * m + k];
+  const int R = cr_rows(m), nloc = R * NB, k0 = rank * R;
+  cplx* X = cr_x;
+  cplx* Y = cr_x + nloc;
+  for (int e = threadIdx.x; e < nloc; e += CR_THREADS) {
+    const int k = k0 + e / NB, comp = e % NB;
+    X[e] = k < m ? S.r[comp * m + k] : cmk(0.0, 0.0);
   }
   cluster_arrive();
+  const int e0 = threadIdx.x, kf = k0 + e0 / NB;
+  const bool first_ok = e0 < nloc && kf < m;
   cplx fa[NB], fb[NB];
   for (int l = 0; l < pq; ++l) {
     const int s = 1 << l;
     const cplx* pa = S.pa + (size_t)l * m * nb2;
     const cplx* pg = S.pg + (size_t)l * m * nb2;
-    if (t0 < total) {
-      const size_t fo = (size_t)(t0 / NB) * nb2 + (t0 % NB) * NB;
+    if (first_ok) {
+      const size_t fo = (size_t)kf * nb2 + (e0 % NB) * NB;
       load_row<NB>(fa, pa + fo);
       load_row<NB>(fb, pg + fo);
     }
     cluster_wait();
-    for (int w = t0; w < total; w += nt) {
-      const int k = w / NB, comp = w % NB;
-      if (w != t0) {
+    for (int e = e0; e < nloc; e += CR_THREADS) {
+      const int k = k0 + e / NB, comp = e % NB;
+      if (k >= m) break;
+      if (e != e0) {
         const size_t fo = (size_t)k * nb2 + comp * NB;
         load_row<NB>(fa, pa + fo);
         load_row<NB>(fb, pg + fo);
       }
-      cplx acc = X[w];
-      if (k - s >= 0) acc = csub(acc, dot_row<NB>(fa, X + (size_t)(k - s) * NB));
-      if (k + s < m) acc = csub(acc, dot_row<NB>(fb, X + (size_t)(k + s) * NB));
-      Y[w] = acc;
+      cplx acc = X[e];
+      if (k - s >= 0) {
+        const int q = (k - s) / R;
+        acc = csub(acc, dot_row<NB>(fa, cl.map_shared_rank(X + (k - s - q * R) * NB, q)));
+      }
+      if (k + s < m) {
+        const int q = (k + s) / R;
+        acc = csub(acc, dot_row<NB>(fb, cl.map_shared_rank(X + (k + s - q * R) * NB, q)));
+      }
+      Y[e] = acc;
     }
     cluster_arrive();
     cplx* t = X; X = Y; Y = t;
   }
-  if (t0 < total) load_row<NB>(fa, S.pbinv + (size_t)(t0 / NB) * nb2 + (t0 % NB) * NB);
-  cluster_wait();
-  for (int w = t0; w < total; w += nt) {
-    const int k = w / NB, comp = w % NB;
-    if (w != t0) load_row<NB>(fa, S.pbinv + (size_t)k * nb2 + comp * NB);
-    const cplx v = dot_row<NB>(fa, X + (size_t)k * NB);
+  if (first_ok) load_row<NB>(fa, S.pbinv + (size_t)kf * nb2 + (e0 % NB) * NB);
+  cluster_wait();   // every CTA is past its last remote read: each now reads only its own rows
+  for (int e = e0; e < nloc; e += CR_THREADS) {
+    const int k = k0 + e / NB, comp = e % NB;
+    if (k >= m) break;
+    if (e != e0) load_row<NB>(fa, S.pbinv + (size_t)k * nb2 + comp * NB);
+    const cplx v = dot_row<NB>(fa, X + (e / NB) * NB);
     S.e[comp * m + k] = v;
     if (S.e32) S.e32[comp * m + k] = make_float2((float)v.x, (float)v.y);
   }
@@ -308,27 +334,43 @@ cudaError_t launch_cc_rhs(const CCViewT<C>& c, cudaStream_t st) {
 
 // Clusters of more than 8 CTAs must be allowed per kernel (once, before any launch or
 // capture); called by setup.
-cudaError_t channel_solve_prepare(int nb) {
+// Raises (never lowers) the kernel's dynamic shared-memory limit to what m_max rows need,
+// so every handle set up so far can still launch.
+cudaError_t channel_solve_prepare(int nb, int m_max) {
+  static std::mutex mu;
+  static int granted[MGC_MAX_NB + 1] = {0};
+  if (nb < 1 || nb > MGC_MAX_NB) return cudaErrorInvalidValue;
+  const int smem = 2 * cr_rows(m_max) * nb * (int)sizeof(cplx);
+  std::lock_guard<std::mutex> lock(mu);
+  if (granted[nb] > 0 && smem <= granted[nb]) return cudaSuccess;
+  const int want = smem > 48 * 1024 ? smem : 48 * 1024;
+  cudaError_t e = cudaErrorInvalidValue;
   switch (nb) {
-#define MGC_PREP(K)                                                                                         \
-  case K:                                                                                                   \
-    return cudaFuncSetAttribute(k_channel_solve_pcr<K>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+#define MGC_PREP(K)                                                                                        \
+  case K:                                                                                                  \
+    e = cudaFuncSetAttribute(k_channel_solve_pcr<K>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1); \
+    if (e == cudaSuccess)                                                                                \
+      e = cudaFuncSetAttribute(k_channel_solve_pcr<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, want); \
+    break;
     MGC_PREP(1) MGC_PREP(2) MGC_PREP(3) MGC_PREP(4) MGC_PREP(5) MGC_PREP(6) MGC_PREP(7) MGC_PREP(8)
 #undef MGC_PREP
   }
-  return cudaErrorInvalidValue;
+  if (e == cudaSuccess) granted[nb] = want;
+  return e;
 }
 
 cudaError_t launch_channel_solve(const CRSystem& A, const CRSystem& B, cudaStream_t st) {
+  const int mm = A.m > B.m ? A.m : B.m;
+  const size_t smem = 2 * (size_t)cr_rows(mm) * A.nb * sizeof(cplx);
   switch (A.nb) {
-    case 1: k_channel_solve_pcr<1><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
-    case 2: k_channel_solve_pcr<2><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
-    case 3: k_channel_solve_pcr<3><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
-    case 4: k_channel_solve_pcr<4><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
-    case 5: k_channel_solve_pcr<5><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
-    case 6: k_channel_solve_pcr<6><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
-    case 7: k_channel_solve_pcr<7><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
-    case 8: k_channel_solve_pcr<8><<<2 * CR_CLUSTER, CR_THREADS, 0, st>>>(A, B); break;
+    case 1: k_channel_solve_pcr<1><<<2 * CR_CLUSTER, CR_THREADS, smem, st>>>(A, B); break;
+    case 2: k_channel_solve_pcr<2><<<2 * CR_CLUSTER, CR_THREADS, smem, st>>>(A, B); break;
+    case 3: k_channel_solve_pcr<3><<<2 * CR_CLUSTER, CR_THREADS, smem, st>>>(A, B); break;
+    case 4: k_channel_solve_pcr<4><<<2 * CR_CLUSTER, CR_THREADS, smem, st>>>(A, B); break;
+    case 5: k_channel_solve_pcr<5><<<2 * CR_CLUSTER, CR_THREADS, smem, st>>>(A, B); break;
+    case 6: k_channel_solve_pcr<6><<<2 * CR_CLUSTER, CR_THREADS, smem, st>>>(A, B); break;
+    case 7: k_channel_solve_pcr<7><<<2 * CR_CLUSTER, CR_THREADS, smem, st>>>(A, B); break;
+    case 8: k_channel_solve_pcr<8><<<2 * CR_CLUSTER, CR_THREADS, smem, st>>>(A, B); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

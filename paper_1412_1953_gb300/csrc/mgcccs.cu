@@ -201,8 +201,6 @@ void layout(mgcccs_handle* h, Carver& cv) {
       S.m = c == 0 ? my : mx;
       S.nb = nb;
       const size_t nb2 = (size_t)nb * nb;
-      S.X = cv.take<cplx>((size_t)S.m * nb);
-      S.Y = cv.take<cplx>((size_t)S.m * nb);
       S.pq = pcr_levels(S.m);
       S.pa = cv.take<cplx>((size_t)S.pq * S.m * nb2);
       S.pg = cv.take<cplx>((size_t)S.pq * S.m * nb2);
@@ -395,7 +393,7 @@ int do_setup(mgcccs_handle* h, const cplx* v1, const cplx* v2, const cplx* v12, 
   if (h->nb > 0) {
     const LevelBufs& b = h->lv[0];
     const int nb = h->nb;
-    MGC_CUDA(channel_solve_prepare(nb));
+    MGC_CUDA(channel_solve_prepare(nb, h->crA.m > h->crB.m ? h->crA.m : h->crB.m));
     if (lam_in) {
       // states supplied by the caller (a previous setup on the same grid and V1, V2)
       MGC_CUDA(cudaMemcpyAsync(h->lam, lam_in, sizeof(cplx) * nb, cudaMemcpyHostToDevice, st));
