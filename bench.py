@@ -210,7 +210,7 @@ def measured_peaks():
 
 def kernel_source_sha():
     """Hash of the source text that defines the fine-level complex128 k_jacobi launch: the
-    level descriptor and per-node arithmetic in common.cuh, the load helpers it calls and
+    level descriptor and per-node arithmetic in common.cuh, the neighbour loads it calls and
     the kernel itself (edits elsewhere do not change the kernel, so they keep its committed
     ncu counters valid)."""
     csrc = os.path.join(ROOT, "paper_1412_1953_gb300", "csrc")
@@ -220,7 +220,7 @@ def kernel_source_sha():
     a = hdr.index("template <class C>\nstruct AxisCoefT")
     b = hdr.index("\n}\n", hdr.index("__device__ __forceinline__ void dispatch_kinds("))
     h.update(hdr[a:b].encode())
-    a = src.index("__device__ __forceinline__ T ldm(")
+    a = src.index("__device__ __forceinline__ C ldz(")
     b = src.index("// Full weighting 1/16")
     k = src.index("__launch_bounds__(BX * BY) k_jacobi(")
     e = src.index("\n}\n", k)

@@ -279,21 +279,6 @@ __device__ __forceinline__ void dispatch_kinds(const StencilViewT<C>& s, int i0,
   }
 }
 
-// One level of the fused coarse-level V-cycle (k_vcycle_tail): stencil, iterate,
-// right-hand side, smoother scratch and residual.
-template <class C>
-struct TailLevel {
-  StencilViewT<C> sv;
-  C *u, *f, *t, *r;
-};
-// Levels l0..L-1 of a hierarchy (lv[0] = level l0, lv[n-1] = the coarsest).
-template <class C>
-struct TailArgs {
-  int n, nu1, nu2, zero_init, nc;
-  const cplx* Ainv;
-  TailLevel<C> lv[MGC_MAX_LEVELS];
-};
-constexpr int TAIL_THREADS = 1024;
 
 // Error bits written by kernels into the handle's device status word.
 enum {
@@ -323,8 +308,6 @@ template <class C>
 cudaError_t launch_restrict(int mx, int my, const C* r, C* rc, cudaStream_t st);
 template <class C>
 cudaError_t launch_prolong_add(int mx, int my, const C* ec, C* u, cudaStream_t st);
-template <class C>
-cudaError_t launch_vcycle_tail(const TailArgs<C>& a, cudaStream_t st);
 template <class C>
 cudaError_t launch_coarse_solve(int nc, const cplx* Ainv, const C* f, C* u, cudaStream_t st);
 template <class C>

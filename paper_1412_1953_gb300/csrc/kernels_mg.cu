@@ -14,52 +14,44 @@ namespace {
 
 constexpr int BX = 32, BY = 8;
 
-// Loads of arrays a kernel may also write: through the read-only path (NC) in the
-// one-step kernels, plain loads in the fused coarse-level kernel (which rewrites them
-// between its stages).  Stencil coefficients always use the read-only path.
-template <bool NC, class T>
-__device__ __forceinline__ T ldm(const T* __restrict__ a) {
-  if constexpr (NC) return __ldg(a);
-  else return *a;
-}
-
-template <bool NC, class C>
+// u_p, or zero outside the interior (the homogeneous Dirichlet boundary).
+template <class C>
 __device__ __forceinline__ C ldz(const C* __restrict__ a, int p, bool ok) {
-  return ok ? ldm<NC>(a + p) : CT<C>::make(0.0, 0.0);
+  return ok ? __ldg(a + p) : CT<C>::make(0.0, 0.0);
 }
 
 // The four neighbour values of interior node p = (i, j) (zero outside the interior).
-#define MGC_NEIGHBOURS(NC, s, u, p, i, j)                                                             \
-  ldz<NC>(u, (p) - 1, (i) > 0), ldz<NC>(u, (p) + 1, (i) + 1 < (s).mx), ldz<NC>(u, (p) - (s).mx, (j) > 0), \
-      ldz<NC>(u, (p) + (s).mx, (j) + 1 < (s).my)
+#define MGC_NEIGHBOURS(s, u, p, i, j)                                                          \
+  ldz(u, (p) - 1, (i) > 0), ldz(u, (p) + 1, (i) + 1 < (s).mx), ldz(u, (p) - (s).mx, (j) > 0), \
+      ldz(u, (p) + (s).mx, (j) + 1 < (s).my)
 
 // Template arguments of the per-node helpers from the IntC arguments of dispatch_kinds.
 #define MGC_KINDS(kx, ky, ir, dg) decltype(kx)::value, decltype(ky)::value, decltype(ir)::value, decltype(dg)::value
 
 // (H - E) u at interior node (i, j), given the centre value uc.
-template <int KX, int KY, int IR, int DG, bool NC, class C>
+template <int KX, int KY, int IR, int DG, class C>
 __device__ __forceinline__ C apply_pt(const StencilViewT<C>& s, const C* __restrict__ u, int i, int j, C uc) {
   const int p = j * s.mx + i;
-  return apply_vals<KX, KY, IR, DG>(s, i, j, p, uc, MGC_NEIGHBOURS(NC, s, u, p, i, j));
+  return apply_vals<KX, KY, IR, DG>(s, i, j, p, uc, MGC_NEIGHBOURS(s, u, p, i, j));
 }
 
-// ---- per-node arithmetic shared by the one-step kernels and the fused coarse-level kernel
+// ---- per-node arithmetic
 
 // One omega-Jacobi update at (i, j): u + (omega/D)(f - (H-E)u).
-template <int KX, int KY, int IR, int DG, bool NC, class C>
+template <int KX, int KY, int IR, int DG, class C>
 __device__ __forceinline__ C jacobi_pt(const StencilViewT<C>& s, const C* __restrict__ u_in,
                                        const C* __restrict__ f, int i, int j) {
   const int p = j * s.mx + i;
-  return jacobi_vals<KX, KY, IR, DG>(s, i, j, p, ldm<NC>(u_in + p), MGC_NEIGHBOURS(NC, s, u_in, p, i, j),
-                                     ldm<NC>(f + p));
+  return jacobi_vals<KX, KY, IR, DG>(s, i, j, p, __ldg(u_in + p), MGC_NEIGHBOURS(s, u_in, p, i, j),
+                                     __ldg(f + p));
 }
 
-template <int KX, int KY, int IR, int DG, bool NC, class C>
+template <int KX, int KY, int IR, int DG, class C>
 __device__ __forceinline__ C residual_pt(const StencilViewT<C>& s, const C* __restrict__ u, const C* __restrict__ f,
                                          int i, int j) {
   const int p = j * s.mx + i;
-  return residual_vals<KX, KY, IR, DG>(s, i, j, p, ldm<NC>(u + p), MGC_NEIGHBOURS(NC, s, u, p, i, j),
-                                       ldm<NC>(f + p));
+  return residual_vals<KX, KY, IR, DG>(s, i, j, p, __ldg(u + p), MGC_NEIGHBOURS(s, u, p, i, j),
+                                       __ldg(f + p));
 }
 
 // dispatch_kinds for the block of this thread.
@@ -69,59 +61,37 @@ __device__ __forceinline__ void block_kinds(const StencilViewT<C>& s, F&& f) {
   dispatch_kinds(s, i0, min(i0 + (int)blockDim.x, s.mx), j0, min(j0 + (int)blockDim.y, s.my), f);
 }
 
-// Whole-level kinds (the fused coarse-level kernel): a test per node.
-template <class C, class F>
-__device__ __forceinline__ void level_kinds(const StencilViewT<C>& s, F&& f) {
-  const bool ir = s.cx.in_real && s.cy.in_real;
-  dispatch_ir_dg<AX_GEN, AX_GEN>(ir, s.rbox && ir, f);
-}
 
 // Full weighting 1/16 [1 2 1; 2 4 2; 1 2 1] onto coarse interior node (I, J), which sits
 // on fine interior node (2I+1, 2J+1); all nine taps are interior nodes.
-template <bool NC, class C>
+template <class C>
 __device__ __forceinline__ C restrict_pt(int mx, const C* __restrict__ r, int I, int J) {
   typedef typename CT<C>::R R;
   const int c = (2 * J + 1) * mx + (2 * I + 1);
-  C corners = cadd(cadd(ldm<NC>(r + c - mx - 1), ldm<NC>(r + c - mx + 1)),
-                   cadd(ldm<NC>(r + c + mx - 1), ldm<NC>(r + c + mx + 1)));
-  C edges = cadd(cadd(ldm<NC>(r + c - 1), ldm<NC>(r + c + 1)), cadd(ldm<NC>(r + c - mx), ldm<NC>(r + c + mx)));
-  C centre = ldm<NC>(r + c);
+  C corners = cadd(cadd(__ldg(r + c - mx - 1), __ldg(r + c - mx + 1)),
+                   cadd(__ldg(r + c + mx - 1), __ldg(r + c + mx + 1)));
+  C edges = cadd(cadd(__ldg(r + c - 1), __ldg(r + c + 1)), cadd(__ldg(r + c - mx), __ldg(r + c + mx)));
+  C centre = __ldg(r + c);
   C acc;
   acc.x = fma(R(2), edges.x, fma(R(4), centre.x, corners.x));
   acc.y = fma(R(2), edges.y, fma(R(4), centre.y, corners.y));
   return cscal(R(0.0625), acc);
 }
 
-template <bool NC, class C>
+template <class C>
 __device__ __forceinline__ C coarse_at(const C* __restrict__ ec, int mcx, int mcy, int K, int Kp) {
   // coarse node (K, Kp), 0..mc+1; boundary nodes carry zero
-  return (K >= 1 && K <= mcx && Kp >= 1 && Kp <= mcy) ? ldm<NC>(ec + (Kp - 1) * mcx + (K - 1))
+  return (K >= 1 && K <= mcx && Kp >= 1 && Kp <= mcy) ? __ldg(ec + (Kp - 1) * mcx + (K - 1))
                                                        : CT<C>::make(0.0, 0.0);
 }
 
-// Bilinear interpolation of the coarse correction at fine interior node (i, j).
-template <bool NC, class C>
-__device__ __forceinline__ C prolong_pt(int mcx, int mcy, const C* __restrict__ ec, int i, int j) {
-  typedef typename CT<C>::R R;
-  const int kx = i + 1, ky = j + 1;
-  const int Kx = kx >> 1, Ky = ky >> 1;
-  if (!(kx & 1) && !(ky & 1)) return coarse_at<NC>(ec, mcx, mcy, Kx, Ky);
-  if (!(ky & 1))
-    return cscal(R(0.5), cadd(coarse_at<NC>(ec, mcx, mcy, Kx, Ky), coarse_at<NC>(ec, mcx, mcy, Kx + 1, Ky)));
-  if (!(kx & 1))
-    return cscal(R(0.5), cadd(coarse_at<NC>(ec, mcx, mcy, Kx, Ky), coarse_at<NC>(ec, mcx, mcy, Kx, Ky + 1)));
-  return cscal(R(0.25), cadd(cadd(coarse_at<NC>(ec, mcx, mcy, Kx, Ky), coarse_at<NC>(ec, mcx, mcy, Kx + 1, Ky)),
-                             cadd(coarse_at<NC>(ec, mcx, mcy, Kx, Ky + 1),
-                                  coarse_at<NC>(ec, mcx, mcy, Kx + 1, Ky + 1))));
-}
-
 // Row `row` of the coarsest solve u = A_c^{-1} f by one warp (FP64 inverse, FP64 sums).
-template <bool NC, class C>
+template <class C>
 __device__ __forceinline__ void coarse_row(int nc, const cplx* __restrict__ Ainv, const C* __restrict__ f,
                                            C* __restrict__ u, int row, int lane) {
   cplx acc = cmk(0.0, 0.0);
   const cplx* a = Ainv + (size_t)row * nc;
-  for (int c = lane; c < nc; c += 32) acc = cfma(__ldg(a + c), to_c128(ldm<NC>(f + c)), acc);
+  for (int c = lane; c < nc; c += 32) acc = cfma(__ldg(a + c), to_c128(__ldg(f + c)), acc);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
@@ -137,7 +107,7 @@ __global__ void __launch_bounds__(BX * BY) k_jacobi(StencilViewT<C> s, const C* 
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= s.mx || j >= s.my) return;
   block_kinds(s, [&](auto kx, auto ky, auto ir, auto dg) {
-    u_out[j * s.mx + i] = jacobi_pt<MGC_KINDS(kx, ky, ir, dg), true>(s, u_in, f, i, j);
+    u_out[j * s.mx + i] = jacobi_pt<MGC_KINDS(kx, ky, ir, dg)>(s, u_in, f, i, j);
   });
 }
 
@@ -214,7 +184,7 @@ __global__ void __launch_bounds__(BX * BY) k_residual(StencilViewT<C> s, const C
   if (i < s.mx && j < s.my) {
     const int p = j * s.mx + i;
     block_kinds(s, [&](auto kx, auto ky, auto ir, auto dg) {
-      C rv = residual_pt<MGC_KINDS(kx, ky, ir, dg), true>(s, u, f, i, j);
+      C rv = residual_pt<MGC_KINDS(kx, ky, ir, dg)>(s, u, f, i, j);
       if (r) r[p] = rv;
       n2 = cabs2(rv);
     });
@@ -231,23 +201,20 @@ __global__ void __launch_bounds__(256) k_restrict(int mx, int mcx, int mcy, cons
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= mcx || J >= mcy) return;
-  rc[J * mcx + I] = restrict_pt<true>(mx, r, I, J);
+  rc[J * mcx + I] = restrict_pt(mx, r, I, J);
 }
 
-// u += bilinear interpolation of the coarse correction, one thread per coarse cell
+// u += bilinear interpolation of the coarse correction on the fine nodes of coarse cell
 // [K, K+1] x [L, L+1] (coarse nodes; 0 and mc+1 are the boundary): the fine nodes
 // k = 2K+1, 2K+2 by l = 2L+1, 2L+2 inside it share the cell's corner values and pair
-// sums, so the four updates take 16 FP64 operations and no thread takes a parity branch.
-// Each sum is formed in the order prolong_pt uses, so the results are the same.
+// sums, so the four updates take 16 FP64 operations and need no parity branch.  The
+// interpolated value at a fine node is d, (b + d)/2, (c + d)/2 or ((a + b) + (c + d))/4.
 template <class C>
-__global__ void __launch_bounds__(BX * BY) k_prolong_add(int mx, int my, int mcx, int mcy, const C* __restrict__ ec,
-                                                         C* __restrict__ u) {
+__device__ __forceinline__ void prolong_cell(int mx, int my, int mcx, int mcy, const C* __restrict__ ec,
+                                             C* __restrict__ u, int K, int L) {
   typedef typename CT<C>::R R;
-  const int K = blockIdx.x * blockDim.x + threadIdx.x;
-  const int L = blockIdx.y * blockDim.y + threadIdx.y;
-  if (K > mcx || L > mcy) return;
-  const C a = coarse_at<true>(ec, mcx, mcy, K, L), b = coarse_at<true>(ec, mcx, mcy, K + 1, L);
-  const C c = coarse_at<true>(ec, mcx, mcy, K, L + 1), d = coarse_at<true>(ec, mcx, mcy, K + 1, L + 1);
+  const C a = coarse_at(ec, mcx, mcy, K, L), b = coarse_at(ec, mcx, mcy, K + 1, L);
+  const C c = coarse_at(ec, mcx, mcy, K, L + 1), d = coarse_at(ec, mcx, mcy, K + 1, L + 1);
   const int i = 2 * K, j = 2 * L;             // fine interior indices of the nodes k = 2K+1, l = 2L+1
   const bool xe = i + 1 < mx, ye = j + 1 < my;  // whether k = 2K+2 (l = 2L+2) is interior
   const C cd = cadd(c, d);
@@ -280,6 +247,16 @@ __global__ void __launch_bounds__(BX * BY) k_prolong_add(int mx, int my, int mcx
   }
 }
 
+// One thread per coarse cell (no warp diverges on the parity of a fine node).
+template <class C>
+__global__ void __launch_bounds__(BX * BY) k_prolong_add(int mx, int my, int mcx, int mcy, const C* __restrict__ ec,
+                                                         C* __restrict__ u) {
+  const int K = blockIdx.x * blockDim.x + threadIdx.x;
+  const int L = blockIdx.y * blockDim.y + threadIdx.y;
+  if (K > mcx || L > mcy) return;
+  prolong_cell(mx, my, mcx, mcy, ec, u, K, L);
+}
+
 // Coarsest level: u = A_c^{-1} f with the FP64 dense inverse built at setup; one warp
 // per row, accumulated in FP64 for either element type.
 template <class C>
@@ -287,115 +264,9 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int nc, const cplx* __rest
                                                       C* __restrict__ u) {
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (row >= nc) return;
-  coarse_row<true>(nc, Ainv, f, u, row, threadIdx.x & 31);
+  coarse_row(nc, Ainv, f, u, row, threadIdx.x & 31);
 }
 
-// Stages of the fused kernel: one pass over a level's nodes by the whole CTA, lane x of
-// warp y taking the nodes (x + 32a, y + 32b) (no index division, rows read by whole
-// warps).  The restrict-qualified pointers let the loads of a thread's nodes overlap.
-constexpr int TAIL_WARPS = TAIL_THREADS / 32;
-
-template <class C>
-__device__ __forceinline__ void tail_jacobi(const StencilViewT<C>& s, const C* __restrict__ u, C* __restrict__ o,
-                                            const C* __restrict__ f, bool zero) {
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  level_kinds(s, [&](auto kx, auto ky, auto ir, auto dg) {
-    for (int j = ty; j < s.my; j += TAIL_WARPS)
-      for (int i = tx; i < s.mx; i += 32) {
-        const int p = j * s.mx + i;
-        o[p] = zero ? cmul(__ldg(s.Dinv + p), ldm<false>(f + p))
-                    : jacobi_pt<MGC_KINDS(kx, ky, ir, dg), false>(s, u, f, i, j);
-      }
-  });
-}
-
-template <class C>
-__device__ __forceinline__ void tail_residual(const StencilViewT<C>& s, const C* __restrict__ u,
-                                              const C* __restrict__ f, C* __restrict__ r) {
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  level_kinds(s, [&](auto kx, auto ky, auto ir, auto dg) {
-    for (int j = ty; j < s.my; j += TAIL_WARPS)
-      for (int i = tx; i < s.mx; i += 32) r[j * s.mx + i] = residual_pt<MGC_KINDS(kx, ky, ir, dg), false>(s, u, f, i, j);
-  });
-}
-
-template <class C>
-__device__ __forceinline__ void tail_restrict(int mx, int mcx, int mcy, const C* __restrict__ r, C* __restrict__ fc) {
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int J = ty; J < mcy; J += TAIL_WARPS)
-    for (int I = tx; I < mcx; I += 32) fc[J * mcx + I] = restrict_pt<false>(mx, r, I, J);
-}
-
-template <class C>
-__device__ __forceinline__ void tail_prolong(int mx, int my, int mcx, int mcy, const C* __restrict__ ec,
-                                             C* __restrict__ u) {
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int j = ty; j < my; j += TAIL_WARPS)
-    for (int i = tx; i < mx; i += 32) {
-      const int p = j * mx + i;
-      u[p] = cadd(u[p], prolong_pt<false>(mcx, mcy, ec, i, j));
-    }
-}
-
-// ---- fused coarse levels: the V-cycle below a size threshold in one CTA ----------
-// Levels 0..n-1 of `a` are consecutive multigrid levels ending at the coarsest.  The
-// kernel runs the same steps as the one-step kernels in the same order (pre-smoothing,
-// residual, restriction, ..., the dense coarsest solve, prolongation, post-smoothing)
-// with __syncthreads() between steps instead of kernel boundaries, so a V-cycle's
-// coarse tail costs one launch instead of six per level.  The result is left in lv[0].u.
-template <class C>
-__global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_constant__ TailArgs<C> a) {
-  const int tid = threadIdx.x;
-  C* cur[MGC_MAX_LEVELS];
-  C* oth[MGC_MAX_LEVELS];
-  for (int l = 0; l < a.n - 1; ++l) {
-    const TailLevel<C>& L = a.lv[l];
-    C* c = L.u;
-    C* o = L.t;
-    bool zero = l == 0 ? a.zero_init != 0 : true;
-    for (int sw = 0; sw < a.nu1; ++sw) {
-      tail_jacobi(L.sv, c, o, L.f, zero);
-      zero = false;
-      C* x = c; c = o; o = x;
-      __syncthreads();
-    }
-    if (zero) {
-      for (int p = tid; p < L.sv.mx * L.sv.my; p += TAIL_THREADS) c[p] = CT<C>::make(0.0, 0.0);
-      __syncthreads();
-    }
-    tail_residual(L.sv, c, L.f, L.r);
-    __syncthreads();
-    tail_restrict(L.sv.mx, a.lv[l + 1].sv.mx, a.lv[l + 1].sv.my, L.r, a.lv[l + 1].f);
-    __syncthreads();
-    cur[l] = c;
-    oth[l] = o;
-  }
-  {
-    const TailLevel<C>& Lc = a.lv[a.n - 1];
-    for (int row = tid >> 5; row < a.nc; row += TAIL_THREADS >> 5)
-      coarse_row<false>(a.nc, a.Ainv, Lc.f, Lc.u, row, tid & 31);
-    __syncthreads();
-  }
-  const C* ec = a.lv[a.n - 1].u;
-  for (int l = a.n - 2; l >= 0; --l) {
-    const TailLevel<C>& L = a.lv[l];
-    C* c = cur[l];
-    C* o = oth[l];
-    tail_prolong(L.sv.mx, L.sv.my, a.lv[l + 1].sv.mx, a.lv[l + 1].sv.my, ec, c);
-    __syncthreads();
-    for (int sw = 0; sw < a.nu2; ++sw) {
-      tail_jacobi(L.sv, c, o, L.f, false);
-      C* x = c; c = o; o = x;
-      __syncthreads();
-    }
-    cur[l] = c;
-    ec = c;
-  }
-  if (cur[0] != a.lv[0].u) {
-    const int np = a.lv[0].sv.mx * a.lv[0].sv.my;
-    for (int p = tid; p < np; p += TAIL_THREADS) a.lv[0].u[p] = cur[0][p];
-  }
-}
 
 // Sum of n partials in a fixed order (one block), result to out[0]; skipped when
 // `gate` is given and *gate == 0.
@@ -429,7 +300,7 @@ __global__ void __launch_bounds__(BX * BY) k_apply(StencilViewT<C> s, const C* _
   if (i < s.mx && j < s.my) {
     const int p = j * s.mx + i;
     block_kinds(s, [&](auto kx, auto ky, auto ir, auto dg) {
-      C v = apply_pt<MGC_KINDS(kx, ky, ir, dg), true>(s, x, i, j, __ldg(x + p));
+      C v = apply_pt<MGC_KINDS(kx, ky, ir, dg)>(s, x, i, j, __ldg(x + p));
       y[p] = v;
       n2 = cabs2(v);
     });
@@ -552,11 +423,6 @@ cudaError_t launch_coarse_solve(int nc, const cplx* Ainv, const C* f, C* u, cuda
   return cudaGetLastError();
 }
 
-template <class C>
-cudaError_t launch_vcycle_tail(const TailArgs<C>& a, cudaStream_t st) {
-  k_vcycle_tail<C><<<1, TAIL_THREADS, 0, st>>>(a);
-  return cudaGetLastError();
-}
 
 template <class C>
 cudaError_t launch_apply(const StencilViewT<C>& s, const C* x, C* y, cudaStream_t st, double* norm_part) {
@@ -582,7 +448,6 @@ cudaError_t launch_norm2(const C* v, long long n, double* part, int nblocks, cud
   template cudaError_t launch_restrict<C>(int, int, const C*, C*, cudaStream_t);                          \
   template cudaError_t launch_prolong_add<C>(int, int, const C*, C*, cudaStream_t);                       \
   template cudaError_t launch_coarse_solve<C>(int, const cplx*, const C*, C*, cudaStream_t);              \
-  template cudaError_t launch_vcycle_tail<C>(const TailArgs<C>&, cudaStream_t);                           \
   template cudaError_t launch_apply<C>(const StencilViewT<C>&, const C*, C*, cudaStream_t, double*);      \
   template cudaError_t launch_norm2<C>(const C*, long long, double*, int, cudaStream_t);
 MGC_INSTANTIATE(double2)

@@ -34,7 +34,6 @@ struct mgcccs_handle {
   mgcccs_params p;
   cudaStream_t st;
   int L;
-  int tail64, tail32;      // first level of the fused coarse-level kernel (L: none)
   LevelBufs lv[MGC_MAX_LEVELS];
   int nc;
   cplx* Ainv;
@@ -167,15 +166,6 @@ void layout(mgcccs_handle* h, Carver& cv) {
   h->inner_rtol = p.inner_rtol > 0.0 ? p.inner_rtol : 1e-5;
   const LevelBufs& c = h->lv[L - 1];
   h->nc = c.mx * c.my;
-  // Fused coarse-level kernel (one CTA): from the first level with at most 64^2 nodes in
-  // complex64 (FP32 pipe), 16^2 in complex128 (the FP64 pipe of one SM is 1/152 of the
-  // GPU's, so larger FP64 levels stay on the one-step kernels).
-  h->tail64 = h->tail32 = L;
-  for (int l = L - 2; l >= 0; --l) {
-    const long long pts = (long long)h->lv[l].mx * h->lv[l].my;
-    if (pts <= 16 * 16) h->tail64 = l;
-    if (pts <= 64 * 64) h->tail32 = l;
-  }
   h->Ainv = cv.take<cplx>((size_t)h->nc * h->nc);
   h->aug = cv.take<cplx>(coarse_inverse_scratch(h->nc));
   {
@@ -489,40 +479,10 @@ const CCViewT<float2>& cc_view<float2>(mgcccs_handle* h) { return h->cc32; }
 
 // One V-cycle on level l.  `u` holds the initial guess unless zero_init; the result is
 // returned in *out (either u or the level's t buffer).
-template <class C> int tail_level(const mgcccs_handle* h);
-template <> int tail_level<cplx>(const mgcccs_handle* h) { return h->tail64; }
-template <> int tail_level<float2>(const mgcccs_handle* h) { return h->tail32; }
-
-// Levels l..L-1 in one launch of the fused coarse-level kernel; the result lands in u.
-template <class C>
-int vcycle_tail(mgcccs_handle* h, int l, C* u, const C* f, bool zero_init) {
-  TailArgs<C> a{};
-  a.n = h->L - l;
-  a.nu1 = h->p.nu1;
-  a.nu2 = h->p.nu2;
-  a.zero_init = zero_init ? 1 : 0;
-  a.nc = h->nc;
-  a.Ainv = h->Ainv;
-  for (int k = 0; k < a.n; ++k) {
-    LevelIO<C> b = level_io<C>(h, l + k);
-    a.lv[k].sv = *b.sv;
-    a.lv[k].u = k == 0 ? u : b.u;
-    a.lv[k].f = k == 0 ? const_cast<C*>(f) : b.f;
-    a.lv[k].t = b.t;
-    a.lv[k].r = b.r;
-  }
-  MGC_LAUNCH(launch_vcycle_tail(a, h->st));
-  return MGCCCS_OK;
-}
-
 template <class C>
 int vcycle_rec(mgcccs_handle* h, int l, C* u, const C* f, bool zero_init, C** out) {
   cudaStream_t st = h->st;
   LevelIO<C> b = level_io<C>(h, l);
-  if (l == tail_level<C>(h) && l < h->L - 1) {
-    *out = u;
-    return vcycle_tail<C>(h, l, u, f, zero_init);
-  }
   if (l == h->L - 1) {
     MGC_LAUNCH(launch_coarse_solve(h->nc, h->Ainv, f, u, st));
     *out = u;
@@ -708,7 +668,7 @@ int issue_arnoldi_step(mgcccs_handle* h, int j) {
   // cycle start): fused into the first pre-smoothing sweep of the preconditioner when
   // the fine level starts one, else a launch of its own
   if (j > 0) {
-    if (h->p.nu1 >= 1 && h->L > 1 && tail_level<C>(h) > 0) {
+    if (h->p.nu1 >= 1 && h->L > 1) {
       h->pend_norm2 = h->norm_out + 1;
     } else {
       MGC_LAUNCH(launch_scale_by_norm(N, (const C*)vj, vj, h->norm_out + 1, (cplx*)nullptr, nb, st));
