@@ -308,6 +308,15 @@ template <class C>
 cudaError_t launch_restrict(int mx, int my, const C* r, C* rc, cudaStream_t st);
 template <class C>
 cudaError_t launch_prolong_add(int mx, int my, const C* ec, C* u, cudaStream_t st);
+// o = one omega-Jacobi sweep from u + P ec (the level's prolongation and first
+// post-smoothing sweep in one pass; u itself is left unchanged)
+template <class C>
+cudaError_t launch_prolong_jacobi(const StencilViewT<C>& s, const C* ec, const C* u, C* o, const C* f,
+                                  cudaStream_t st);
+// u0 = omega D^{-1} f and fc = restriction of f - (H - E) u0 (zero-start sweep, residual and
+// restriction of a level in one pass)
+template <class C>
+cudaError_t launch_zero_residual_restrict(const StencilViewT<C>& s, const C* f, C* u0, C* fc, cudaStream_t st);
 template <class C>
 cudaError_t launch_coarse_solve(int nc, const cplx* Ainv, const C* f, C* u, cudaStream_t st);
 template <class C>

@@ -62,20 +62,34 @@ __device__ __forceinline__ void block_kinds(const StencilViewT<C>& s, F&& f) {
 }
 
 
-// Full weighting 1/16 [1 2 1; 2 4 2; 1 2 1] onto coarse interior node (I, J), which sits
-// on fine interior node (2I+1, 2J+1); all nine taps are interior nodes.
-template <class C>
-__device__ __forceinline__ C restrict_pt(int mx, const C* __restrict__ r, int I, int J) {
+// Full weighting 1/16 [1 2 1; 2 4 2; 1 2 1] from the residuals r(dx, dy) at offsets
+// dx, dy in {-1, 0, 1} around the coincident fine node.
+template <class C, class G>
+__device__ __forceinline__ C restrict_at(G&& r) {
   typedef typename CT<C>::R R;
-  const int c = (2 * J + 1) * mx + (2 * I + 1);
-  C corners = cadd(cadd(__ldg(r + c - mx - 1), __ldg(r + c - mx + 1)),
-                   cadd(__ldg(r + c + mx - 1), __ldg(r + c + mx + 1)));
-  C edges = cadd(cadd(__ldg(r + c - 1), __ldg(r + c + 1)), cadd(__ldg(r + c - mx), __ldg(r + c + mx)));
-  C centre = __ldg(r + c);
+  C corners = cadd(cadd(r(-1, -1), r(1, -1)), cadd(r(-1, 1), r(1, 1)));
+  C edges = cadd(cadd(r(-1, 0), r(1, 0)), cadd(r(0, -1), r(0, 1)));
+  C centre = r(0, 0);
   C acc;
   acc.x = fma(R(2), edges.x, fma(R(4), centre.x, corners.x));
   acc.y = fma(R(2), edges.y, fma(R(4), centre.y, corners.y));
   return cscal(R(0.0625), acc);
+}
+
+// Full weighting onto coarse interior node (I, J), which sits on fine interior node
+// (2I+1, 2J+1); all nine taps are interior nodes.
+template <class C>
+__device__ __forceinline__ C restrict_pt(int mx, const C* __restrict__ r, int I, int J) {
+  const int c = (2 * J + 1) * mx + (2 * I + 1);
+  return restrict_at<C>([&](int dx, int dy) { return __ldg(r + c + dy * mx + dx); });
+}
+
+// v + w s (w a power of two, so w s is exact and the update rounds once).
+template <class C>
+__device__ __forceinline__ C add_scaled(typename CT<C>::R w, C s, C v) {
+  v.x = fma(w, s.x, v.x);
+  v.y = fma(w, s.y, v.y);
+  return v;
 }
 
 template <class C>
@@ -218,32 +232,11 @@ __device__ __forceinline__ void prolong_cell(int mx, int my, int mcx, int mcy, c
   const int i = 2 * K, j = 2 * L;             // fine interior indices of the nodes k = 2K+1, l = 2L+1
   const bool xe = i + 1 < mx, ye = j + 1 < my;  // whether k = 2K+2 (l = 2L+2) is interior
   const C cd = cadd(c, d);
-  {
-    const C s4 = cadd(cadd(a, b), cd);
-    C& v = u[j * mx + i];
-    C w = v;
-    w.x = fma(R(0.25), s4.x, w.x);
-    w.y = fma(R(0.25), s4.y, w.y);
-    v = w;
-  }
-  if (xe) {
-    const C bd = cadd(b, d);
-    C& v = u[j * mx + i + 1];
-    C w = v;
-    w.x = fma(R(0.5), bd.x, w.x);
-    w.y = fma(R(0.5), bd.y, w.y);
-    v = w;
-  }
+  u[j * mx + i] = add_scaled(R(0.25), cadd(cadd(a, b), cd), u[j * mx + i]);
+  if (xe) u[j * mx + i + 1] = add_scaled(R(0.5), cadd(b, d), u[j * mx + i + 1]);
   if (ye) {
-    C& v = u[(j + 1) * mx + i];
-    C w = v;
-    w.x = fma(R(0.5), cd.x, w.x);
-    w.y = fma(R(0.5), cd.y, w.y);
-    v = w;
-    if (xe) {
-      C& v2 = u[(j + 1) * mx + i + 1];
-      v2 = cadd(v2, d);
-    }
+    u[(j + 1) * mx + i] = add_scaled(R(0.5), cd, u[(j + 1) * mx + i]);
+    if (xe) u[(j + 1) * mx + i + 1] = cadd(u[(j + 1) * mx + i + 1], d);
   }
 }
 
@@ -255,6 +248,115 @@ __global__ void __launch_bounds__(BX * BY) k_prolong_add(int mx, int my, int mcx
   const int L = blockIdx.y * blockDim.y + threadIdx.y;
   if (K > mcx || L > mcy) return;
   prolong_cell(mx, my, mcx, mcy, ec, u, K, L);
+}
+
+// ---- fused level passes: the small levels are bound by launch latency, not by their work
+
+// Prolongation and the first post-smoothing sweep of a level in one pass.  A block forms
+// u + P e on its BX x by fine nodes and a one-node halo in shared memory (one thread per
+// coarse cell, the arithmetic of prolong_cell; zero outside the interior), then applies
+// the omega-Jacobi update from there.  u + P e is not stored: only the smoothed values
+// are, so the results are those of k_prolong_add followed by k_jacobi.
+template <class C>
+__global__ void __launch_bounds__(BX * BY) k_prolong_jacobi(StencilViewT<C> s, int mcx, int mcy,
+                                                            const C* __restrict__ ec, const C* __restrict__ u,
+                                                            C* __restrict__ o, const C* __restrict__ f) {
+  typedef typename CT<C>::R R;
+  constexpr int TW = BX + 2;
+  __shared__ C T[BY + 2][TW];
+  const int by = blockDim.y;
+  const int i0 = blockIdx.x * BX, j0 = blockIdx.y * by;
+  const int tid = threadIdx.y * BX + threadIdx.x, nth = BX * by;
+  for (int q = tid; q < TW * (by + 2); q += nth) T[q / TW][q % TW] = CT<C>::make(0.0, 0.0);
+  __syncthreads();
+  // coarse cells K (fine i = 2K, 2K+1) meeting the tile's fine range [i0 - 1, i0 + BX]
+  const int K0 = (i0 - 1) >> 1, K1 = (i0 + BX) >> 1;
+  const int L0 = (j0 - 1) >> 1, L1 = (j0 + by) >> 1;
+  const int nkx = K1 - K0 + 1, ncell = nkx * (L1 - L0 + 1);
+  for (int q = tid; q < ncell; q += nth) {
+    const int K = K0 + q % nkx, L = L0 + q / nkx;
+    if (K < 0 || L < 0 || K > mcx || L > mcy) continue;   // no interior fine node in the cell
+    const C a = coarse_at(ec, mcx, mcy, K, L), b = coarse_at(ec, mcx, mcy, K + 1, L);
+    const C c = coarse_at(ec, mcx, mcy, K, L + 1), d = coarse_at(ec, mcx, mcy, K + 1, L + 1);
+    const C cd = cadd(c, d);
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      const int i = 2 * K + (n & 1), j = 2 * L + (n >> 1);
+      if (i >= s.mx || j >= s.my || i < i0 - 1 || i > i0 + BX || j < j0 - 1 || j > j0 + by) continue;
+      const C v = __ldg(u + j * s.mx + i);
+      T[j - j0 + 1][i - i0 + 1] = n == 0   ? add_scaled(R(0.25), cadd(cadd(a, b), cd), v)
+                                  : n == 1 ? add_scaled(R(0.5), cadd(b, d), v)
+                                  : n == 2 ? add_scaled(R(0.5), cd, v)
+                                           : cadd(v, d);
+    }
+  }
+  __syncthreads();
+  const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+  if (i >= s.mx || j >= s.my) return;
+  const int p = j * s.mx + i, tx = threadIdx.x + 1, ty = threadIdx.y + 1;
+  block_kinds(s, [&](auto kx, auto ky, auto ir, auto dg) {
+    o[p] = jacobi_vals<MGC_KINDS(kx, ky, ir, dg)>(s, i, j, p, T[ty][tx], T[ty][tx - 1], T[ty][tx + 1], T[ty - 1][tx],
+                                                  T[ty + 1][tx], __ldg(f + p));
+  });
+}
+
+// The zero-start sweep, the residual and the full-weighting restriction of a level in
+// one pass.  A block takes DBX x cby coarse nodes and runs one thread per entry of each
+// stage, so every stage costs one round of memory latency: the zero-start values
+// u0 = (omega/D) f on the fine nodes [2 I0 - 1, 2 I0 + 2 DBX + 1] x [2 J0 - 1, 2 J0 + 2 cby + 1]
+// (zero outside the interior) into shared memory, the residuals on
+// [2 I0, 2 I0 + 2 DBX] x [2 J0, 2 J0 + 2 cby], then the restriction.  u0 is written for the
+// fine nodes the block owns (i >> 1 and j >> 1, clamped to the last coarse index, inside
+// the block's coarse range); r is not stored.  The results are those of k_jacobi_zero,
+// k_residual and k_restrict.
+constexpr int DBX = 16, DBY = 8;
+constexpr int DUW = 2 * DBX + 3, DRW = 2 * DBX + 1;
+
+template <class C>
+__global__ void __launch_bounds__(DUW * (2 * DBY + 3)) k_zero_residual_restrict(StencilViewT<C> s, int mcx, int mcy,
+                                                                                const C* __restrict__ f,
+                                                                                C* __restrict__ u0,
+                                                                                C* __restrict__ fc) {
+  __shared__ C U[2 * DBY + 3][DUW];
+  __shared__ C Rt[2 * DBY + 1][DRW];
+  const int cby = (blockDim.x / DUW - 3) / 2;   // coarse rows of the block
+  const int I0 = blockIdx.x * DBX, J0 = blockIdx.y * cby;
+  const int t = threadIdx.x;
+  {
+    const int a = t % DUW, b = t / DUW;
+    const int i = 2 * I0 - 1 + a, j = 2 * J0 - 1 + b;
+    C v = CT<C>::make(0.0, 0.0);
+    if (i >= 0 && j >= 0 && i < s.mx && j < s.my) {
+      const int p = j * s.mx + i;
+      v = cmul(__ldg(s.Dinv + p), __ldg(f + p));
+      const int oi = min(i >> 1, mcx - 1), oj = min(j >> 1, mcy - 1);
+      if (oi >= I0 && oi < I0 + DBX && oj >= J0 && oj < J0 + cby) u0[p] = v;
+    }
+    U[b][a] = v;
+  }
+  __syncthreads();
+  const int rh = 2 * cby + 1;
+  if (t < DRW * rh) {
+    const int a = t % DRW, b = t / DRW;
+    const int i = 2 * I0 + a, j = 2 * J0 + b;
+    if (i < s.mx && j < s.my) {
+      const int p = j * s.mx + i;
+      dispatch_kinds(s, 2 * I0, min(2 * I0 + DRW, s.mx), 2 * J0, min(2 * J0 + rh, s.my),
+                     [&](auto kx, auto ky, auto ir, auto dg) {
+                       Rt[b][a] = residual_vals<MGC_KINDS(kx, ky, ir, dg)>(
+                           s, i, j, p, U[b + 1][a + 1], U[b + 1][a], U[b + 1][a + 2], U[b][a + 1], U[b + 2][a + 1],
+                           __ldg(f + p));
+                     });
+    }
+  }
+  __syncthreads();
+  if (t < DBX * cby) {
+    const int I = I0 + t % DBX, J = J0 + t / DBX;
+    if (I < mcx && J < mcy) {
+      const int a = 2 * (t % DBX) + 1, b = 2 * (t / DBX) + 1;   // (2I+1, 2J+1) in Rt
+      fc[J * mcx + I] = restrict_at<C>([&](int dx, int dy) { return Rt[b + dy][a + dx]; });
+    }
+  }
 }
 
 // Coarsest level: u = A_c^{-1} f with the FP64 dense inverse built at setup; one warp
@@ -409,6 +511,26 @@ cudaError_t launch_restrict(int mx, int my, const C* r, C* rc, cudaStream_t st) 
 }
 
 template <class C>
+cudaError_t launch_prolong_jacobi(const StencilViewT<C>& s, const C* ec, const C* u, C* o, const C* f,
+                                  cudaStream_t st) {
+  const int mcx = (s.mx - 1) / 2, mcy = (s.my - 1) / 2;
+  if (s.mx != 2 * mcx + 1 || s.my != 2 * mcy + 1) return cudaErrorInvalidValue;
+  const int by = level_by(s.mx, s.my);
+  k_prolong_jacobi<C><<<level_grid(s.mx, s.my, by), dim3(BX, by), 0, st>>>(s, mcx, mcy, ec, u, o, f);
+  return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_zero_residual_restrict(const StencilViewT<C>& s, const C* f, C* u0, C* fc, cudaStream_t st) {
+  const int mcx = (s.mx - 1) / 2, mcy = (s.my - 1) / 2;
+  if (s.mx != 2 * mcx + 1 || s.my != 2 * mcy + 1) return cudaErrorInvalidValue;
+  const int cby = (long long)mcx * mcy < 2LL * 152 * DBX * DBY ? 2 : DBY;
+  const dim3 grid((mcx + DBX - 1) / DBX, (mcy + cby - 1) / cby);
+  k_zero_residual_restrict<C><<<grid, DUW * (2 * cby + 3), 0, st>>>(s, mcx, mcy, f, u0, fc);
+  return cudaGetLastError();
+}
+
+template <class C>
 cudaError_t launch_prolong_add(int mx, int my, const C* ec, C* u, cudaStream_t st) {
   int mcx = (mx - 1) / 2, mcy = (my - 1) / 2;
   if (mx != 2 * mcx + 1 || my != 2 * mcy + 1) return cudaErrorInvalidValue;   // coarse = every other fine node
@@ -447,6 +569,9 @@ cudaError_t launch_norm2(const C* v, long long n, double* part, int nblocks, cud
                                           cudaStream_t);                                                  \
   template cudaError_t launch_restrict<C>(int, int, const C*, C*, cudaStream_t);                          \
   template cudaError_t launch_prolong_add<C>(int, int, const C*, C*, cudaStream_t);                       \
+  template cudaError_t launch_prolong_jacobi<C>(const StencilViewT<C>&, const C*, const C*, C*, const C*,   \
+                                               cudaStream_t);                                            \
+  template cudaError_t launch_zero_residual_restrict<C>(const StencilViewT<C>&, const C*, C*, C*, cudaStream_t); \
   template cudaError_t launch_coarse_solve<C>(int, const cplx*, const C*, C*, cudaStream_t);              \
   template cudaError_t launch_apply<C>(const StencilViewT<C>&, const C*, C*, cudaStream_t, double*);      \
   template cudaError_t launch_norm2<C>(const C*, long long, double*, int, cudaStream_t);

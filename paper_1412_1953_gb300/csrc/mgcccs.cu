@@ -479,6 +479,14 @@ const CCViewT<float2>& cc_view<float2>(mgcccs_handle* h) { return h->cc32; }
 
 // One V-cycle on level l.  `u` holds the initial guess unless zero_init; the result is
 // returned in *out (either u or the level's t buffer).
+// Whether level passes are fused (zero-start sweep + residual + restriction; prolongation +
+// first post-smoothing sweep): always for complex64, whose FP32 work is cheap; for
+// complex128 below 512^2 nodes, where launch latency outweighs the halo recomputation.
+template <class C>
+bool fuse_level(const LevelIO<C>& b) {
+  return sizeof(C) == sizeof(float2) || (long long)b.mx * b.my < 512LL * 512;
+}
+
 template <class C>
 int vcycle_rec(mgcccs_handle* h, int l, C* u, const C* f, bool zero_init, C** out) {
   cudaStream_t st = h->st;
@@ -491,31 +499,49 @@ int vcycle_rec(mgcccs_handle* h, int l, C* u, const C* f, bool zero_init, C** ou
   C* cur = u;
   C* oth = b.t;
   bool zero = zero_init;
-  for (int s = 0; s < h->p.nu1; ++s) {
-    if (zero && l == 0 && h->pend_norm2) {
-      // the Krylov vector f = w is normalised by the same pass (see issue_arnoldi_step)
-      MGC_LAUNCH(launch_scale_jacobi_zero(*b.sv, const_cast<C*>(f), h->pend_norm2, oth, st));
-      h->pend_norm2 = nullptr;
-    } else if (zero) {
-      MGC_LAUNCH(launch_jacobi_zero(*b.sv, oth, f, st));
-    } else {
-      MGC_LAUNCH(launch_jacobi(*b.sv, (const C*)cur, oth, f, st));
-    }
-    zero = false;
-    C* tmp = cur; cur = oth; oth = tmp;
-  }
-  if (zero) {
-    // no pre-smoothing and a zero guess: the residual is f itself
-    MGC_CUDA(cudaMemsetAsync(cur, 0, sizeof(C) * (size_t)b.mx * b.my, st));
-  }
   LevelIO<C> c = level_io<C>(h, l + 1);
-  MGC_LAUNCH(launch_residual(*b.sv, (const C*)cur, f, b.r, (double*)nullptr, st));
-  MGC_LAUNCH(launch_restrict(b.mx, b.my, (const C*)b.r, c.f, st));
+  const bool fuse = fuse_level(b);
+  if (fuse && zero && h->p.nu1 == 1 && !(l == 0 && h->pend_norm2)) {
+    // the zero-start sweep, residual and restriction in one pass
+    MGC_LAUNCH(launch_zero_residual_restrict(*b.sv, f, oth, c.f, st));
+    cur = oth;
+    oth = u;
+  } else {
+    for (int s = 0; s < h->p.nu1; ++s) {
+      if (zero && l == 0 && h->pend_norm2) {
+        // the Krylov vector f = w is normalised by the same pass (see issue_arnoldi_step)
+        MGC_LAUNCH(launch_scale_jacobi_zero(*b.sv, const_cast<C*>(f), h->pend_norm2, oth, st));
+        h->pend_norm2 = nullptr;
+      } else if (zero) {
+        MGC_LAUNCH(launch_jacobi_zero(*b.sv, oth, f, st));
+      } else {
+        MGC_LAUNCH(launch_jacobi(*b.sv, (const C*)cur, oth, f, st));
+      }
+      zero = false;
+      C* tmp = cur; cur = oth; oth = tmp;
+    }
+    if (zero) {
+      // no pre-smoothing and a zero guess: the residual is f itself
+      MGC_CUDA(cudaMemsetAsync(cur, 0, sizeof(C) * (size_t)b.mx * b.my, st));
+    }
+    MGC_LAUNCH(launch_residual(*b.sv, (const C*)cur, f, b.r, (double*)nullptr, st));
+    MGC_LAUNCH(launch_restrict(b.mx, b.my, (const C*)b.r, c.f, st));
+  }
   C* ec = nullptr;
   int rc = vcycle_rec<C>(h, l + 1, c.u, c.f, true, &ec);
   if (rc) return rc;
-  MGC_LAUNCH(launch_prolong_add(b.mx, b.my, (const C*)ec, cur, st));
-  for (int s = 0; s < h->p.nu2; ++s) {
+  if (h->p.nu2 == 0 || !fuse) {
+    MGC_LAUNCH(launch_prolong_add(b.mx, b.my, (const C*)ec, cur, st));
+    if (h->p.nu2 > 0) {
+      MGC_LAUNCH(launch_jacobi(*b.sv, (const C*)cur, oth, f, st));
+      C* tmp = cur; cur = oth; oth = tmp;
+    }
+  } else {
+    // the prolongation and the first post-smoothing sweep in one pass
+    MGC_LAUNCH(launch_prolong_jacobi(*b.sv, (const C*)ec, (const C*)cur, oth, f, st));
+    C* tmp = cur; cur = oth; oth = tmp;
+  }
+  for (int s = 1; s < h->p.nu2; ++s) {
     MGC_LAUNCH(launch_jacobi(*b.sv, (const C*)cur, oth, f, st));
     C* tmp = cur; cur = oth; oth = tmp;
   }
