@@ -393,15 +393,11 @@ struct CCViewT {
   cplx* Px;                // [nb][my]
   cplx* Py;                // [nb][mx]
   cplx* c;                 // [nb][nb]  c[a][b] = int int phi_a vphi_b r
-  cplx* rA;                // [nb][my]
-  cplx* rB;                // [nb][mx]
   cplx* eA;                // [nb][my]
   cplx* eB;                // [nb][mx]
   const C* eAc;            // eA, eB in the element precision (the same arrays for complex128)
   const C* eBc;
-  const cplx* phi64;       // [nb][mx] FP64 states for the channel right-hand sides
-  const cplx* vphi64;      // [nb][my]
-  const cplx* wvphi64;     // [nb][my]
+  const cplx* wvphi64;     // [nb][my] FP64 weighted states for the coupling coefficients
 };
 typedef CCViewT<cplx> CCView;
 typedef CCViewT<float2> CCView32;
@@ -409,7 +405,13 @@ typedef CCViewT<float2> CCView32;
 // One coupled-channel system (Eqs. (28)-(29)) with its parallel-cyclic-reduction factors.
 struct CRSystem {
   int m, nb;
-  const cplx* r;           // [nb][m] right-hand side
+  // right-hand side r[a][k] = P[a][k] - sum_l coef(a, l) basis[l][k] with the conventions of
+  // Eqs. (25)-(26): channel A (chan 0) l > a, coef = c[a][l], basis = vphi (along y);
+  // channel B (chan 1) l >= a, coef = c[l][a], basis = phi (along x)
+  int chan;
+  const cplx* P;           // [nb][m] projections P^x (channel A) or P^y (channel B)
+  const cplx* cmat;        // [nb][nb] c
+  const cplx* basis;       // [nb][m]
   cplx* e;                 // [nb][m] solution
   float2* e32;             // [nb][m] solution rounded to complex64 (mixed precision), or null
   // parallel cyclic reduction: pq = ceil(log2 m) levels; level l with stride s = 2^l

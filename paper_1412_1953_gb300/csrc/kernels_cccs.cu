@@ -135,26 +135,6 @@ __global__ void __launch_bounds__(256) k_cc_coef(int nb, int my, const cplx* __r
   }
 }
 
-// Channel right-hand sides with the uniqueness conventions.
-__global__ void __launch_bounds__(256) k_cc_split(int nb, int mx, int my, const cplx* __restrict__ cmat,
-                                                  const cplx* __restrict__ phi, const cplx* __restrict__ vphi,
-                                                  const cplx* __restrict__ Px, const cplx* __restrict__ Py,
-                                                  cplx* __restrict__ rA, cplx* __restrict__ rB) {
-  const int t = blockIdx.x * 256 + threadIdx.x;
-  if (t < nb * my) {
-    const int a = t / my, j = t % my;
-    cplx v = Px[t];
-    for (int l = a + 1; l < nb; ++l) v = cfms(cmat[a * nb + l], __ldg(vphi + l * my + j), v);   // b_al
-    rA[t] = v;
-  } else if (t < nb * my + nb * mx) {
-    const int q = t - nb * my;
-    const int b = q / mx, i = q % mx;
-    cplx v = Py[q];
-    for (int m = b; m < nb; ++m) v = cfms(cmat[m * nb + b], __ldg(phi + m * mx + i), v);        // a_bm
-    rB[q] = v;
-  }
-}
-
 // Coupled-channel solves (Eqs. (28)-(29)) by parallel cyclic reduction with setup-time
 // factors: each system is solved by one thread-block cluster of CR_CLUSTER CTAs (cluster
 // 0: channel A along y, cluster 1: channel B along x); every level is one pass over the
@@ -215,9 +195,19 @@ k_channel_solve_pcr(CRSystem SA, CRSystem SB) {
   const int R = cr_rows(m), nloc = R * NB, k0 = rank * R;
   cplx* X = cr_x;
   cplx* Y = cr_x + nloc;
+  // the channel right-hand sides with the uniqueness conventions (Eqs. (25)-(26))
   for (int e = threadIdx.x; e < nloc; e += CR_THREADS) {
     const int k = k0 + e / NB, comp = e % NB;
-    X[e] = k < m ? S.r[comp * m + k] : cmk(0.0, 0.0);
+    cplx v = cmk(0.0, 0.0);
+    if (k < m) {
+      v = S.P[comp * m + k];
+      if (S.chan == 0) {
+        for (int l = comp + 1; l < NB; ++l) v = cfms(S.cmat[comp * NB + l], __ldg(S.basis + l * m + k), v);   // b_al
+      } else {
+        for (int l = comp; l < NB; ++l) v = cfms(S.cmat[l * NB + comp], __ldg(S.basis + l * m + k), v);       // a_bl
+      }
+    }
+    X[e] = v;
   }
   cluster_arrive();
   const int e0 = threadIdx.x, kf = k0 + e0 / NB;
@@ -326,9 +316,6 @@ cudaError_t launch_cc_rhs(const CCViewT<C>& c, cudaStream_t st) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_cc_coef<<<c.nb * c.nb, 256, 0, st>>>(c.nb, c.my, c.wvphi64, c.Px, c.c);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_cc_split<<<(tot + 255) / 256, 256, 0, st>>>(c.nb, c.mx, c.my, c.c, c.phi64, c.vphi64, c.Px, c.Py, c.rA, c.rB);
   return cudaGetLastError();
 }
 

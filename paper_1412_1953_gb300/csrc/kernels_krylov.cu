@@ -33,6 +33,7 @@ __device__ __forceinline__ cplx block_sum_c(C v, double (*sh)[NTH / 32]) {
 
 // partial[i][b] = sum over block b's points of conj(V_i) w   (grid: nblk x k).
 // When `gate` is given and *gate == 0 the pass is skipped (partials set to zero).
+// A vector V_i that is w itself gives |w|^2 (two FMAs per point; the block's branch).
 // (Each thread accumulates in the element precision; the block sum is FP64.)
 template <class C>
 __global__ void __launch_bounds__(NT) k_multidot(long long n, const C* __restrict__ V, long long ld,
@@ -46,10 +47,17 @@ __global__ void __launch_bounds__(NT) k_multidot(long long n, const C* __restric
   }
   const C* v = V + (size_t)i * ld;
   C acc = CT<C>::make(0.0, 0.0);
-  for (long long p = blockIdx.x * (long long)NT + threadIdx.x; p < n; p += (long long)gridDim.x * NT) {
-    C a = __ldg(v + p), b = __ldg(w + p);
-    acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
-    acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
+  if (v == w) {
+    for (long long p = blockIdx.x * (long long)NT + threadIdx.x; p < n; p += (long long)gridDim.x * NT) {
+      C b = __ldg(w + p);
+      acc.x = fma(b.x, b.x, fma(b.y, b.y, acc.x));
+    }
+  } else {
+    for (long long p = blockIdx.x * (long long)NT + threadIdx.x; p < n; p += (long long)gridDim.x * NT) {
+      C a = __ldg(v + p), b = __ldg(w + p);
+      acc.x = fma(a.x, b.x, fma(a.y, b.y, acc.x));
+      acc.y = fma(a.x, b.y, fma(-a.y, b.x, acc.y));
+    }
   }
   cplx tot = block_sum_c<NT>(acc, sh);
   if (threadIdx.x == 0) partial[(size_t)i * gridDim.x + blockIdx.x] = tot;

@@ -77,8 +77,6 @@ struct mgcccs_handle {
   SolveCtl* ctl;
   SolveCtl* ctl_host;
   cudaStream_t gst[2];
-  cudaStream_t fork_st;                      // side branch of the Arnoldi step graphs
-  cudaEvent_t fev[2];                        // fork/join events of the side branch
   bool device_loop;
   const double* pend_norm2;                  // set: the next fine zero-start sweep first normalises f
   int driver;                                // MGCCCS_DRIVER_GRAPH or MGCCCS_DRIVER_HOST
@@ -205,19 +203,19 @@ void layout(mgcccs_handle* h, Carver& cv) {
     CCView& cc = h->cc;
     cc.mx = mx; cc.my = my; cc.nb = nb;
     cc.wphi = h->wphi; cc.wvphi = h->wvphi; cc.phi = h->phi; cc.vphi = h->vphi;
-    cc.phi64 = h->phi; cc.vphi64 = h->vphi; cc.wvphi64 = h->wvphi;
+    cc.wvphi64 = h->wvphi;
     cc.Px_part = cv.take<cplx>((size_t)cc_tiles_x(mx) * nb * my);
     cc.Py_part = cv.take<cplx>((size_t)cc_tiles_y(my) * nb * mx);
     cc.Px = cv.take<cplx>((size_t)nb * my);
     cc.Py = cv.take<cplx>((size_t)nb * mx);
     cc.c = cv.take<cplx>((size_t)nb * nb);
-    cc.rA = cv.take<cplx>((size_t)nb * my);
-    cc.rB = cv.take<cplx>((size_t)nb * mx);
     cc.eA = cv.take<cplx>((size_t)nb * my);
     cc.eB = cv.take<cplx>((size_t)nb * mx);
     cc.eAc = cc.eA; cc.eBc = cc.eB;
-    h->crA.r = cc.rA; h->crA.e = cc.eA; h->crA.e32 = nullptr;
-    h->crB.r = cc.rB; h->crB.e = cc.eB; h->crB.e32 = nullptr;
+    h->crA.chan = 0; h->crA.P = cc.Px; h->crA.cmat = cc.c; h->crA.basis = h->vphi;
+    h->crB.chan = 1; h->crB.P = cc.Py; h->crB.cmat = cc.c; h->crB.basis = h->phi;
+    h->crA.e = cc.eA; h->crA.e32 = nullptr;
+    h->crB.e = cc.eB; h->crB.e32 = nullptr;
     if (p.precision == 1) {
       h->phi32 = cv.take<float2>((size_t)nb * mx);
       h->vphi32 = cv.take<float2>((size_t)nb * my);
@@ -228,13 +226,13 @@ void layout(mgcccs_handle* h, Carver& cv) {
       c3.wphi = h->wphi32; c3.wvphi = h->wvphi32; c3.phi = h->phi32; c3.vphi = h->vphi32;
       c3.Px_part = cv.take<float2>((size_t)cc_tiles_x(mx) * nb * my);
       c3.Py_part = cv.take<float2>((size_t)cc_tiles_y(my) * nb * mx);
-      c3.Px = cc.Px; c3.Py = cc.Py; c3.c = cc.c; c3.rA = cc.rA; c3.rB = cc.rB; c3.eA = cc.eA; c3.eB = cc.eB;
+      c3.Px = cc.Px; c3.Py = cc.Py; c3.c = cc.c; c3.eA = cc.eA; c3.eB = cc.eB;
       float2* eA32 = cv.take<float2>((size_t)nb * my);
       float2* eB32 = cv.take<float2>((size_t)nb * mx);
       c3.eAc = eA32; c3.eBc = eB32;
       h->crA.e32 = eA32;
       h->crB.e32 = eB32;
-      c3.phi64 = h->phi; c3.vphi64 = h->vphi; c3.wvphi64 = h->wvphi;
+      c3.wvphi64 = h->wvphi;
     }
   }
   StencilView s0{};
@@ -567,7 +565,7 @@ int cccs_fine(mgcccs_handle* h, C* u, const C* f) {
   const CCViewT<C>& cc = cc_view<C>(h);
   MGC_LAUNCH(launch_residual_project(*level_io<C>(h, 0).sv, cc, (const C*)u, f, st));
   MGC_LAUNCH(launch_cc_rhs(cc, st));
-  h->launches += 2;   // launch_cc_rhs issues three kernels
+  h->launches += 1;   // launch_cc_rhs issues two kernels
   MGC_LAUNCH(launch_channel_solve(h->crA, h->crB, st));
   MGC_LAUNCH(launch_cccs_correct(cc, u, st));
   return MGCCCS_OK;
@@ -703,26 +701,22 @@ int issue_arnoldi_step(mgcccs_handle* h, int j) {
   int rc = precond<C>(h, zj, vj);
   h->pend_norm2 = nullptr;
   if (rc) return rc;
-  // w = A z_j, with |w|^2 for the reorthogonalisation test; the sum of its partials runs
-  // on a side branch beside the first multi-dot (the step is always captured as a graph,
-  // so the fork and join become graph edges)
-  MGC_LAUNCH(launch_apply(s0, (const C*)zj, w, st, h->norm_part));
-  MGC_CUDA(cudaEventRecord(h->fev[0], st));
-  MGC_CUDA(cudaStreamWaitEvent(h->fork_st, h->fev[0], 0));
-  MGC_LAUNCH(launch_sum_partials(h->norm_part, residual_norm_blocks(s0), h->norm_out + 3, h->fork_st));
-  MGC_CUDA(cudaEventRecord(h->fev[1], h->fork_st));
-  // Gram-Schmidt, first pass: H(0:j, j) = V^H w ; w -= V H(0:j, j)
-  const int nbd = multidot_blocks(N, j + 1);
-  MGC_LAUNCH(launch_multidot(N, j + 1, (const C*)V, N, (const C*)w, h->dotpart, nbd, (const int*)nullptr, st));
-  MGC_LAUNCH(launch_reduce_dots(nbd, j + 1, h->dotpart, col, nullptr, st));
-  MGC_CUDA(cudaStreamWaitEvent(st, h->fev[1], 0));     // norm_part is reused by the multi-axpy
+  // w = A z_j
+  MGC_LAUNCH(launch_apply(s0, (const C*)zj, w, st, (double*)nullptr));
+  // Gram-Schmidt, first pass: H(0:j, j) = V^H w ; w -= V H(0:j, j).  w is column j+1 of V,
+  // so the multi-dot over columns 0..j+1 also yields |w|^2 (for the reorthogonalisation
+  // test), left in H(j+1, j) until the Givens rotation writes that entry.
+  const int nbd = multidot_blocks(N, j + 2);
+  MGC_LAUNCH(launch_multidot(N, j + 2, (const C*)V, N, (const C*)w, h->dotpart, nbd, (const int*)nullptr, st));
+  MGC_LAUNCH(launch_reduce_dots(nbd, j + 2, h->dotpart, col, nullptr, st));
+  const double* w_norm2 = reinterpret_cast<const double*>(col + j + 1);
   MGC_LAUNCH(launch_multiaxpy(N, j + 1, (const C*)V, N, col, -1.0, w, h->norm_part, nb, (const int*)nullptr, st));
   // second pass only when the first one cancelled |w| by more than 1e3;
   // the corrections are added into H(0:j, j)
   if (h->device_loop) {
     // device-driven graph: the pass is the body of a conditional node, so it costs no
     // launch when it does not run
-    MGC_LAUNCH(launch_sum_dgks(h->norm_part, nb, h->norm_out + 1, h->norm_out + 3, h->gate, st, h->dgks_cond[j],
+    MGC_LAUNCH(launch_sum_dgks(h->norm_part, nb, h->norm_out + 1, w_norm2, h->gate, st, h->dgks_cond[j],
                                &h->ctl->dgks));
     cudaGraph_t* body = nullptr;
     int rc2 = add_conditional(st, h->dgks_cond[j], cudaGraphCondTypeIf, 1, &body);
@@ -741,7 +735,7 @@ int issue_arnoldi_step(mgcccs_handle* h, int j) {
     rc2 = capture_end(cg);
     if (rc2) return rc2;
   } else {
-    MGC_LAUNCH(launch_sum_dgks(h->norm_part, nb, h->norm_out + 1, h->norm_out + 3, h->gate, st));
+    MGC_LAUNCH(launch_sum_dgks(h->norm_part, nb, h->norm_out + 1, w_norm2, h->gate, st));
     MGC_LAUNCH(launch_multidot(N, j + 1, (const C*)V, N, (const C*)w, h->dotpart, nbd, (const int*)h->gate, st));
     MGC_LAUNCH(launch_reduce_dots(nbd, j + 1, h->dotpart, h->hc, col, st));
     MGC_LAUNCH(launch_multiaxpy(N, j + 1, (const C*)V, N, h->hc, -1.0, w, h->norm_part, nb, (const int*)h->gate,
@@ -1298,8 +1292,6 @@ int create_krylov_objects(mgcccs_handle* h) {
   MGC_CUDA(cudaMallocHost(reinterpret_cast<void**>(&h->est_host), sizeof(double) * (MGC_MAX_RESTART + 1)));
   MGC_CUDA(cudaMallocHost(reinterpret_cast<void**>(&h->ctl_host), sizeof(SolveCtl)));
   for (int q = 0; q < 2; ++q) MGC_CUDA(cudaStreamCreateWithFlags(&h->gst[q], cudaStreamNonBlocking));
-  MGC_CUDA(cudaStreamCreateWithFlags(&h->fork_st, cudaStreamNonBlocking));
-  for (int q = 0; q < 2; ++q) MGC_CUDA(cudaEventCreateWithFlags(&h->fev[q], cudaEventDisableTiming));
   return MGCCCS_OK;
 }
 
@@ -1727,9 +1719,6 @@ void mgcccs_destroy(mgcccs_t h) {
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
   for (int q = 0; q < 2; ++q)
     if (h->gst[q]) cudaStreamDestroy(h->gst[q]);
-  if (h->fork_st) cudaStreamDestroy(h->fork_st);
-  for (int q = 0; q < 2; ++q)
-    if (h->fev[q]) cudaEventDestroy(h->fev[q]);
   if (h->est_host) cudaFreeHost(h->est_host);
   if (h->ctl_host) cudaFreeHost(h->ctl_host);
   delete h;
