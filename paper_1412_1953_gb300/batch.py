@@ -8,11 +8,11 @@ independent branch of one CUDA graph, launched once) and the host lock-step driv
 a replayed graph on the problem's stream).  Either way small grids overlap on the GPU
 instead of running one by one.
 
-The autotuner picks, for each grid size and precision, the number of levels and the
-pre/post smoothing sweep counts (nu1, nu2) with the shortest measured setup + solve time
-to the tolerance on a probe problem of that size (each energy of a batch needs its own
-setup), and caches the choice in a JSON file keyed by (n, precision, GPU name).  Tile shapes of the kernels are fixed (chosen for the
-FP64 pipe and HBM), so the schedule is what varies with the grid.
+The autotuner picks the pre/post smoothing sweep counts (nu1, nu2) and the level count
+(the deepest hierarchy, or one level less) with the shortest measured setup + solve time
+of the batch itself, and caches the choice in a JSON file keyed by the batch's grids, the
+precision and the GPU name.  Tile shapes of the kernels are fixed (chosen for the FP64
+pipe and HBM), so the schedule is what varies.
 """
 from __future__ import annotations
 
@@ -46,8 +46,9 @@ def default_schedule(n: int) -> dict:
     return {"levels": lv[-1] if lv else 1, "nu1": 1, "nu2": 1}
 
 
-def _cache_key(n: int, precision: int, gpu: str) -> str:
-    return f"{n}|{'mixed' if precision else 'fp64'}|{gpu}"
+def _cache_key(problems, precision: int, gpu: str) -> str:
+    sig = ",".join(f"{p.nx}x{p.ny}" for p in problems)
+    return f"{len(problems)}|{sig}|{'mixed' if precision else 'fp64'}|{gpu}"
 
 
 def _load(path):
@@ -58,58 +59,71 @@ def _load(path):
         return {}
 
 
-def autotune(n: int, precision: int = 1, E: float = 1.0, n_b: int = 3, krylov_restart: int = 20,
-             rtol: float = 1e-10, max_iter: int = 2000, cache_path: str | None = DEFAULT_CACHE,
-             repeats: int = 2, force: bool = False) -> dict:
-    """Schedule {levels, nu1, nu2, seconds, iterations} for n x n grids of the batching
-    workload shape, measured on the problem at energy E (cached unless force)."""
+def autotune(problems, precision: int = 1, n_b: int = 3, krylov_restart: int = 20, rtol: float = 1e-10,
+             max_iter: int = 2000, cache_path: str | None = DEFAULT_CACHE, repeats: int = 2,
+             force: bool = False) -> dict:
+    """Schedules {n: {levels, nu1, nu2}} for a batch of problems: every candidate — a sweep
+    pair (nu1, nu2) and the level count (the deepest of level_candidates, or one level
+    less), the same choice for every grid size — is run on the whole batch as one batch
+    graph, and the shortest measured setup + solve time wins (each energy needs its own
+    setup; the bound states, which every schedule shares, are left out; cached unless
+    force).  The batch is
+    its own probe because a batch shares the GPU between its problems: throughput decides,
+    and a schedule with cheaper but more Arnoldi steps that wins a solve on its own (where
+    launch latency decides) can lose in the batch."""
     import torch
     gpu = torch.cuda.get_device_name()
-    key = _cache_key(n, precision, gpu)
+    key = _cache_key(problems, precision, gpu)
     cache = _load(cache_path) if cache_path else {}
     if key in cache and not force:
-        return cache[key]
-    L = 30.0 * n / 512
-    prob = inputs.temkin_poet(n, L=L, R0=2.0 * L / 3.0, theta=math.pi / 6, E=E, seed=0)
-    f = torch.as_tensor(prob.f).to("cuda")
-    u = torch.zeros_like(f)
+        return {int(n): sch for n, sch in cache[key]["schedules"].items()}
+    sizes = sorted({p.nx for p in problems})
+    # bound states are shared by every candidate (same grids and potentials): solve them
+    # once, so that the setup time below is the part a schedule changes
+    BatchSolver(problems, None, n_b=n_b, precision=precision, krylov_restart=krylov_restart).close()
     best = None
     trials = []
-    for lv in level_candidates(n):
+    for drop in (0, 1):
         for nu1, nu2 in SWEEPS:
+            sched = {}
+            for n in sizes:
+                lv = level_candidates(n)
+                levels = lv[max(len(lv) - 1 - drop, 0)] if lv else 1
+                sched[n] = {"levels": levels, "nu1": nu1, "nu2": nu2}
             torch.cuda.synchronize()
             t = time.perf_counter()
-            sv = M.Solver(M.params_for(prob, levels=lv, nu1=nu1, nu2=nu2, n_b=n_b, krylov_restart=krylov_restart,
-                                       precision=precision), prob.v1, prob.v2, prob.v12, reuse_states=True)
+            bs = BatchSolver(problems, sched, n_b=n_b, precision=precision, krylov_restart=krylov_restart)
             torch.cuda.synchronize()
             setup = time.perf_counter() - t
-            sv.solve(u, f, rtol=rtol, max_iter=5, raise_on_notconv=False)        # build the solve graph
-            times, its, rr = [], 0, math.inf
+            g = bs.graph()
+            g.run(rtol=rtol, max_iter=5)                  # instantiate the batch graph
+            times, its, rr, st = [], [], [math.inf], []
             for _ in range(repeats):
-                u.zero_()
+                for u in bs.u:
+                    u.zero_()
                 torch.cuda.synchronize()
                 t = time.perf_counter()
-                its, rr = sv.solve(u, f, rtol=rtol, max_iter=max_iter, raise_on_notconv=False)
+                its, rr, st = g.run(rtol=rtol, max_iter=max_iter)
                 torch.cuda.synchronize()
                 times.append(time.perf_counter() - t)
-            sv.close()
-            sec = min(times) + setup
-            trials.append({"levels": lv, "nu1": nu1, "nu2": nu2, "seconds": sec, "setup_seconds": setup,
-                           "iterations": its, "relres": rr})
-            if rr <= rtol and (best is None or sec < best["seconds"]):
-                best = trials[-1]
-    if best is None:
-        best = dict(default_schedule(n), seconds=None, iterations=None, relres=None)
-    best = dict(best, probe_E=E, trials=trials)
+            g.close()
+            bs.close()
+            ok = all(x == M.OK for x in st) and max(rr) <= rtol
+            cost = setup + min(times)
+            trials.append({"drop_levels": drop, "nu1": nu1, "nu2": nu2, "seconds": min(times), "setup_seconds": setup,
+                           "steps": int(sum(its)), "converged": ok})
+            if ok and (best is None or cost < best[0]):
+                best = (cost, sched)
+    schedules = best[1] if best else {n: default_schedule(n) for n in sizes}
     if cache_path:
         cache = _load(cache_path)
-        cache[key] = best
+        cache[key] = {"schedules": {str(n): sch for n, sch in schedules.items()}, "trials": trials}
         os.makedirs(os.path.dirname(cache_path), exist_ok=True)
         tmp = cache_path + ".tmp"
         with open(tmp, "w") as fh:
             json.dump(cache, fh, indent=1)
         os.replace(tmp, cache_path)
-    return best
+    return schedules
 
 
 class BatchSolver:
