@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(BX * BY) k_residual(StencilViewT<C> s, const C
     block_kinds(s, [&](auto kx, auto ky, auto ir, auto dg) {
       C rv = residual_pt<MGC_KINDS(kx, ky, ir, dg)>(s, u, f, i, j);
       if (r) r[p] = rv;
-      n2 = cabs2(rv);
+      if (norm_part) n2 = cabs2(rv);
     });
   }
   if (norm_part) {
@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(BX * BY) k_apply(StencilViewT<C> s, const C* _
     block_kinds(s, [&](auto kx, auto ky, auto ir, auto dg) {
       C v = apply_pt<MGC_KINDS(kx, ky, ir, dg)>(s, x, i, j, __ldg(x + p));
       y[p] = v;
-      n2 = cabs2(v);
+      if (norm_part) n2 = cabs2(v);
     });
   }
   if (norm_part) {
