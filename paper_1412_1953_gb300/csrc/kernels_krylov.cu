@@ -149,13 +149,15 @@ __global__ void k_givens(int j, int m, cplx* __restrict__ H, cplx* __restrict__ 
   }
   __syncthreads();
   if (threadIdx.x == 0) {
+    // x carries entry i of the column through the chain in a register (rotation i - 1
+    // wrote it), so each step waits on arithmetic only, not on a shared-memory round trip
+    cplx x = col[0];
     for (int i = 0; i < j; ++i) {
-      cplx x = col[i], y = col[i + 1];
-      cplx c = rc[i], s = rs[i];
+      const cplx y = col[i + 1], c = rc[i], s = rs[i];
       col[i] = cadd(cmul(cmk(c.x, -c.y), x), cmul(cmk(s.x, -s.y), y));
-      col[i + 1] = csub(cmul(c, y), cmul(s, x));
+      x = csub(cmul(c, y), cmul(s, x));
     }
-    cplx a = col[j], b = col[j + 1];
+    cplx a = x, b = col[j + 1];
     double rho = sqrt(cabs2(a) + cabs2(b));
     cplx c, s;
     if (rho == 0.0) {

@@ -90,3 +90,24 @@ def test_batch_rejects_bad_arguments():
     with pytest.raises(M.MGCCCSError) as e:
         M.mgcccs_batch_solve([s0], us[:1], fs[:1], max_iter=0)
     assert e.value.code == M.EINVAL
+
+
+def test_autotune_picks_a_converging_schedule_per_grid(tmp_path):
+    """The batch autotuner runs its candidate schedules on the batch itself: it returns one
+    schedule per grid size, drawn from its candidates, that converges every problem, and
+    reads it back from the cache file the second time."""
+    from paper_1412_1953_gb300 import batch as BT
+    problems = [_problem(n, E, seed=k) for k, (n, E) in enumerate([(64, 0.4), (128, 1.1), (64, 1.7), (128, 0.2)])]
+    cache = str(tmp_path / "tune.json")
+    sched = BT.autotune(problems, precision=1, cache_path=cache, repeats=1)
+    assert sorted(sched) == [64, 128]
+    for n, s in sched.items():
+        assert (s["nu1"], s["nu2"]) in BT.SWEEPS
+        assert s["levels"] in BT.level_candidates(n)
+    bs = BT.BatchSolver(problems, sched, n_b=3, precision=1)
+    g = bs.graph()
+    its, rr, st = g.run(rtol=1e-10, max_iter=2000)
+    assert st == [M.OK] * len(problems) and max(rr) <= 1e-10
+    g.close()
+    bs.close()
+    assert BT.autotune(problems, precision=1, cache_path=cache) == sched
