@@ -313,10 +313,11 @@ cudaError_t launch_prolong_add(int mx, int my, const C* ec, C* u, cudaStream_t s
 template <class C>
 cudaError_t launch_prolong_jacobi(const StencilViewT<C>& s, const C* ec, const C* u, C* o, const C* f,
                                   cudaStream_t st);
-// u0 = omega D^{-1} f and fc = restriction of f - (H - E) u0 (zero-start sweep, residual and
-// restriction of a level in one pass)
+// fc = restriction of f - (H - E) u: a level's residual and restriction in one pass, from the
+// given u, or (zero) after the zero-start sweep u = omega D^{-1} f, which is then stored
 template <class C>
-cudaError_t launch_zero_residual_restrict(const StencilViewT<C>& s, const C* f, C* u0, C* fc, cudaStream_t st);
+cudaError_t launch_zero_residual_restrict(const StencilViewT<C>& s, const C* f, C* u, C* fc, bool zero,
+                                          cudaStream_t st);
 template <class C>
 cudaError_t launch_coarse_solve(int nc, const cplx* Ainv, const C* f, C* u, cudaStream_t st);
 template <class C>

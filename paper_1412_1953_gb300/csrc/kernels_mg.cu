@@ -300,22 +300,22 @@ __global__ void __launch_bounds__(BX * BY) k_prolong_jacobi(StencilViewT<C> s, i
   });
 }
 
-// The zero-start sweep, the residual and the full-weighting restriction of a level in
-// one pass.  A block takes DBX x cby coarse nodes and runs one thread per entry of each
-// stage, so every stage costs one round of memory latency: the zero-start values
-// u0 = (omega/D) f on the fine nodes [2 I0 - 1, 2 I0 + 2 DBX + 1] x [2 J0 - 1, 2 J0 + 2 cby + 1]
-// (zero outside the interior) into shared memory, the residuals on
-// [2 I0, 2 I0 + 2 DBX] x [2 J0, 2 J0 + 2 cby], then the restriction.  u0 is written for the
-// fine nodes the block owns (i >> 1 and j >> 1, clamped to the last coarse index, inside
-// the block's coarse range); r is not stored.  The results are those of k_jacobi_zero,
-// k_residual and k_restrict.
+// The residual and the full-weighting restriction of a level in one pass, from a given
+// iterate u (ZERO false) or after the zero-start sweep u0 = (omega/D) f (ZERO true).  A
+// block takes DBX x cby coarse nodes and runs one thread per entry of each stage, so every
+// stage costs one round of memory latency: u on the fine nodes
+// [2 I0 - 1, 2 I0 + 2 DBX + 1] x [2 J0 - 1, 2 J0 + 2 cby + 1] (zero outside the interior)
+// into shared memory, the residuals on [2 I0, 2 I0 + 2 DBX] x [2 J0, 2 J0 + 2 cby], then the
+// restriction.  With ZERO, u0 is written for the fine nodes the block owns (i >> 1 and
+// j >> 1, clamped to the last coarse index, inside the block's coarse range); r is not
+// stored.  The results are those of (k_jacobi_zero,) k_residual and k_restrict.
 constexpr int DBX = 16, DBY = 8;
 constexpr int DUW = 2 * DBX + 3, DRW = 2 * DBX + 1;
 
-template <class C>
+template <bool ZERO, class C>
 __global__ void __launch_bounds__(DUW * (2 * DBY + 3)) k_zero_residual_restrict(StencilViewT<C> s, int mcx, int mcy,
                                                                                 const C* __restrict__ f,
-                                                                                C* __restrict__ u0,
+                                                                                C* __restrict__ u,
                                                                                 C* __restrict__ fc) {
   __shared__ C U[2 * DBY + 3][DUW];
   __shared__ C Rt[2 * DBY + 1][DRW];
@@ -328,9 +328,13 @@ __global__ void __launch_bounds__(DUW * (2 * DBY + 3)) k_zero_residual_restrict(
     C v = CT<C>::make(0.0, 0.0);
     if (i >= 0 && j >= 0 && i < s.mx && j < s.my) {
       const int p = j * s.mx + i;
-      v = cmul(__ldg(s.Dinv + p), __ldg(f + p));
-      const int oi = min(i >> 1, mcx - 1), oj = min(j >> 1, mcy - 1);
-      if (oi >= I0 && oi < I0 + DBX && oj >= J0 && oj < J0 + cby) u0[p] = v;
+      if constexpr (ZERO) {
+        v = cmul(__ldg(s.Dinv + p), __ldg(f + p));
+        const int oi = min(i >> 1, mcx - 1), oj = min(j >> 1, mcy - 1);
+        if (oi >= I0 && oi < I0 + DBX && oj >= J0 && oj < J0 + cby) u[p] = v;
+      } else {
+        v = __ldg(u + p);
+      }
     }
     U[b][a] = v;
   }
@@ -521,12 +525,16 @@ cudaError_t launch_prolong_jacobi(const StencilViewT<C>& s, const C* ec, const C
 }
 
 template <class C>
-cudaError_t launch_zero_residual_restrict(const StencilViewT<C>& s, const C* f, C* u0, C* fc, cudaStream_t st) {
+cudaError_t launch_zero_residual_restrict(const StencilViewT<C>& s, const C* f, C* u, C* fc, bool zero,
+                                          cudaStream_t st) {
   const int mcx = (s.mx - 1) / 2, mcy = (s.my - 1) / 2;
   if (s.mx != 2 * mcx + 1 || s.my != 2 * mcy + 1) return cudaErrorInvalidValue;
   const int cby = (long long)mcx * mcy < 2LL * 152 * DBX * DBY ? 2 : DBY;
   const dim3 grid((mcx + DBX - 1) / DBX, (mcy + cby - 1) / cby);
-  k_zero_residual_restrict<C><<<grid, DUW * (2 * cby + 3), 0, st>>>(s, mcx, mcy, f, u0, fc);
+  if (zero)
+    k_zero_residual_restrict<true, C><<<grid, DUW * (2 * cby + 3), 0, st>>>(s, mcx, mcy, f, u, fc);
+  else
+    k_zero_residual_restrict<false, C><<<grid, DUW * (2 * cby + 3), 0, st>>>(s, mcx, mcy, f, u, fc);
   return cudaGetLastError();
 }
 
@@ -571,7 +579,8 @@ cudaError_t launch_norm2(const C* v, long long n, double* part, int nblocks, cud
   template cudaError_t launch_prolong_add<C>(int, int, const C*, C*, cudaStream_t);                       \
   template cudaError_t launch_prolong_jacobi<C>(const StencilViewT<C>&, const C*, const C*, C*, const C*,   \
                                                cudaStream_t);                                            \
-  template cudaError_t launch_zero_residual_restrict<C>(const StencilViewT<C>&, const C*, C*, C*, cudaStream_t); \
+  template cudaError_t launch_zero_residual_restrict<C>(const StencilViewT<C>&, const C*, C*, C*, bool,      \
+                                                        cudaStream_t);                                   \
   template cudaError_t launch_coarse_solve<C>(int, const cplx*, const C*, C*, cudaStream_t);              \
   template cudaError_t launch_apply<C>(const StencilViewT<C>&, const C*, C*, cudaStream_t, double*);      \
   template cudaError_t launch_norm2<C>(const C*, long long, double*, int, cudaStream_t);

@@ -501,7 +501,7 @@ int vcycle_rec(mgcccs_handle* h, int l, C* u, const C* f, bool zero_init, C** ou
   const bool fuse = fuse_level(b);
   if (fuse && zero && h->p.nu1 == 1 && !(l == 0 && h->pend_norm2)) {
     // the zero-start sweep, residual and restriction in one pass
-    MGC_LAUNCH(launch_zero_residual_restrict(*b.sv, f, oth, c.f, st));
+    MGC_LAUNCH(launch_zero_residual_restrict(*b.sv, f, oth, c.f, true, st));
     cur = oth;
     oth = u;
   } else {
@@ -522,8 +522,8 @@ int vcycle_rec(mgcccs_handle* h, int l, C* u, const C* f, bool zero_init, C** ou
       // no pre-smoothing and a zero guess: the residual is f itself
       MGC_CUDA(cudaMemsetAsync(cur, 0, sizeof(C) * (size_t)b.mx * b.my, st));
     }
-    MGC_LAUNCH(launch_residual(*b.sv, (const C*)cur, f, b.r, (double*)nullptr, st));
-    MGC_LAUNCH(launch_restrict(b.mx, b.my, (const C*)b.r, c.f, st));
+    // the residual and the restriction in one pass
+    MGC_LAUNCH(launch_zero_residual_restrict(*b.sv, f, cur, c.f, false, st));
   }
   C* ec = nullptr;
   int rc = vcycle_rec<C>(h, l + 1, c.u, c.f, true, &ec);
