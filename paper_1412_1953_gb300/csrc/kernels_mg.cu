@@ -6,8 +6,9 @@
 // interior are the homogeneous Dirichlet boundary (zero).  Every kernel is a template
 // over the element type C: double2 (complex128, the plain path, bound by the FP64
 // pipe on this GPU) or float2 (complex64, the mixed-precision smoother and transfers,
-// bound by HBM).  Each output is computed exactly once (no overlapped halo
-// recomputation) and the uniform parts of each axis use a single neighbour coefficient.
+// bound by HBM).  The one-step kernels compute each output once; the fused level passes
+// further down recompute a one-node halo of their tiles instead of a launch.  The uniform
+// parts of each axis use a single neighbour coefficient.
 #include "common.cuh"
 
 namespace {
