@@ -9,7 +9,8 @@ a replayed graph on the problem's stream).  Either way small grids overlap on th
 instead of running one by one.
 
 The autotuner picks the pre/post smoothing sweep counts (nu1, nu2) and the level count
-(the deepest hierarchy, or one level less) with the shortest measured setup + solve time
+(from the deepest hierarchy to the shallowest whose coarsest grid has at most 32 cells)
+with the shortest measured setup + solve time
 of the batch itself, and caches the choice in a JSON file keyed by the batch's grids, the
 precision and the GPU name.  Tile shapes of the kernels are fixed (chosen for the FP64
 pipe and HBM), so the schedule is what varies.
@@ -63,8 +64,8 @@ def autotune(problems, precision: int = 1, n_b: int = 3, krylov_restart: int = 2
              max_iter: int = 2000, cache_path: str | None = DEFAULT_CACHE, repeats: int = 2,
              force: bool = False) -> dict:
     """Schedules {n: {levels, nu1, nu2}} for a batch of problems: every candidate — a sweep
-    pair (nu1, nu2) and the level count (the deepest of level_candidates, or one level
-    less), the same choice for every grid size — is run on the whole batch as one batch
+    pair (nu1, nu2) and the level count (the deepest of level_candidates, or one, two ...
+    levels less), the same choice for every grid size — is run on the whole batch as one batch
     graph, and the shortest measured setup + solve time wins (each energy needs its own
     setup; the bound states, which every schedule shares, are left out; cached unless
     force).  The batch is
@@ -83,7 +84,7 @@ def autotune(problems, precision: int = 1, n_b: int = 3, krylov_restart: int = 2
     BatchSolver(problems, None, n_b=n_b, precision=precision, krylov_restart=krylov_restart).close()
     best = None
     trials = []
-    for drop in (0, 1):
+    for drop in range(max(len(level_candidates(n)) for n in sizes)):
         for nu1, nu2 in SWEEPS:
             sched = {}
             for n in sizes:
