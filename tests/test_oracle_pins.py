@@ -484,3 +484,21 @@ def test_adjoint_gradients_match_central_differences():
         e[j, i] = h
         fd = (J(E, Z, dV + e) - J(E, Z, dV - e)) / (2 * h)
         assert abs(ddV[j, i] - fd) <= 1e-4 * abs(fd)
+
+
+@pytest.mark.parametrize("n,L,R0,gamma", [(128, 30.0, 20.0, 0.0), (1024, 30.0, 20.0, 0.0),
+                                          (64, 15.0, 10.0, math.radians(14.6)), (96, 30.0, 20.0, 0.3)])
+def test_inner_uniform_coefficients_have_the_closed_form(n, L, R0, gamma):
+    """Where both cells of a node lie inside R0, Eq. (11) with equal cells h e^{i gamma}
+    gives west = east = -1/(2 h^2) e^{-2 i gamma}: the single coefficient the GPU stencil
+    uses on that region.  The oracle's coefficients, formed from node differences, agree
+    to rounding, and the node just before R0 (one cell scaled) does not."""
+    ax = O.make_axis(n, L, R0, math.pi / 6, gamma)
+    h = L / n
+    c = -0.5 / h ** 2 * np.exp(-2j * gamma)
+    inner = [i for i in range(n - 1) if (i + 2) * L / n <= R0]       # interior index i = node i+1
+    assert inner == list(range(len(inner))) and len(inner) > 0
+    np.testing.assert_allclose(ax.west[inner], c, rtol=1e-12)
+    np.testing.assert_allclose(ax.east[inner], c, rtol=1e-12)
+    kink = len(inner)
+    assert abs(ax.east[kink] - c) > 1e-3 * abs(c)
