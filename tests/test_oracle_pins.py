@@ -212,6 +212,102 @@ def test_two_grid_cycle_matches_fourier_analysis():
     assert abs(Mhat - expect).max() <= 1e-12
 
 
+@pytest.mark.parametrize("n,levels,L,R0", [(64, 4, 15.0, 10.0), (128, 5, 30.0, 20.0), (96, 3, 22.5, 15.0)])
+def test_coarse_level_potentials_are_the_potentials_at_the_coarse_nodes(n, levels, L, R0):
+    """Sec. 3.2 re-discretises the operator on the coarser grid of the same box, so level l
+    needs V1, V2, V12 at its own n/2^l-cell nodes.  The oracle injects them from the fine
+    arrays; the values must equal, bit for bit, the potentials evaluated independently on an
+    (n >> l)-cell grid of the same box and ECS contour (the coarse node I is the fine node
+    I 2^l, and x = I L/(n/2^l) is the same double as (I 2^l) L/n)."""
+    prob = inputs.temkin_poet(n, L=L, R0=R0, theta=math.pi / 6, E=0.5)
+    lv = O.build_levels(O.params_from_problem(prob, levels=levels, n_b=0), prob.v1, prob.v2, prob.v12)
+    for l in range(levels):
+        ref = inputs.temkin_poet(n >> l, L=L, R0=R0, theta=math.pi / 6, E=0.5)
+        assert lv[l].v1.shape == ref.v1.shape and lv[l].v12.shape == ref.v12.shape
+        assert np.array_equal(lv[l].v1, ref.v1), l
+        assert np.array_equal(lv[l].v2, ref.v2), l
+        assert np.array_equal(lv[l].v12, ref.v12), l
+        # the operator of level l lives on the (n >> l)-cell contour, rotated by gamma for l >= 1
+        _, z = inputs.node_coordinates(n >> l, L, R0, math.pi / 6)
+        np.testing.assert_allclose(lv[l].ax.z, z * np.exp(1j * (O.COARSE_GAMMA_DEFAULT if l else 0.0)),
+                                   rtol=0, atol=1e-13 * L)
+
+
+def _lfa_symbols(n, h, rho, c, om):
+    """Fourier symbols on an n-cell Dirichlet grid of spacing h whose kinetic part is scaled
+    by rho (rho = e^{-2 i gamma} on a contour rotated by gamma) and whose potential minus
+    energy is the constant c: operator, omega-Jacobi smoother."""
+    ks = np.arange(1, n)
+    s2 = np.sin(ks * math.pi / (2 * n)) ** 2
+    lam = rho * 2.0 / h ** 2 * (s2[None, :] + s2[:, None]) + c        # [l][k]
+    D = rho * 2.0 / h ** 2 + c
+    return np.diag(lam.ravel()), np.diag((1 - om * lam / D).ravel())
+
+
+def _lfa_restriction(n):
+    """Full weighting in the sine bases: fine mode (a, b) -> coarse mode (k, l) with weight
+    w(a) w(b), w(k) = cos^2(k pi/2n), w(n-k) = -sin^2(k pi/2n); bilinear interpolation is the
+    transpose in these (DST-I) bases."""
+    m = n // 2
+    R = np.zeros(((m - 1) ** 2, (n - 1) ** 2))
+    c2 = lambda k: math.cos(k * math.pi / (2 * n)) ** 2
+    s2 = lambda k: math.sin(k * math.pi / (2 * n)) ** 2
+    for k in range(1, m):
+        for l in range(1, m):
+            for a, wa in ((k, c2(k)), (n - k, -s2(k))):
+                for b, wb in ((l, c2(l)), (n - l, -s2(l))):
+                    R[(l - 1) * (m - 1) + (k - 1), (b - 1) * (n - 1) + (a - 1)] = wa * wb
+    return R
+
+
+def _lfa_three_grid(n, h, gamma, c, om, nu1, nu2):
+    """Three-level V(nu1, nu2) error propagation for -1/2 Laplacian + c (c constant, complex)
+    with Dirichlet conditions: fine level on the real axis, levels 1 and 2 on the contour
+    rotated by gamma (kinetic symbol times e^{-2 i gamma}, potential unchanged), the coarsest
+    solved exactly, the coarse-grid correction on level 1 approximated by a two-grid cycle
+    from zero: B_1 = (I - M_1) A_1^{-1}."""
+    rho = np.exp(-2j * gamma)
+    A0, S0 = _lfa_symbols(n, h, 1.0, c, om)
+    A1, S1 = _lfa_symbols(n // 2, 2 * h, rho, c, om)
+    A2, _ = _lfa_symbols(n // 4, 4 * h, rho, c, om)
+    R0, R1 = _lfa_restriction(n), _lfa_restriction(n // 2)
+    mp = np.linalg.matrix_power
+    M1 = mp(S1, nu2) @ (np.eye(len(A1)) - R1.T @ np.linalg.solve(A2, R1) @ A1) @ mp(S1, nu1)
+    B1 = (np.eye(len(A1)) - M1) @ np.linalg.inv(A1)
+    return mp(S0, nu2) @ (np.eye(len(A0)) - R0.T @ B1 @ R0 @ A0) @ mp(S0, nu1)
+
+
+@pytest.mark.parametrize("nu1,nu2", [(1, 1), (2, 1)])
+def test_three_level_cycle_with_potential_matches_fourier_analysis(nu1, nu2):
+    """With constant potentials V1, V2, V12 (not zero) and E, the oracle's 3-level V-cycle,
+    with the coarse levels on the rotated contour of reading R5, written in the sine basis,
+    equals the three-level Fourier operator entry by entry.  This pins the recursion (the
+    coarse cycle from zero, the exact coarsest solve), the potential and energy on every
+    coarse level, and that the rotation scales the kinetic part only."""
+    n, L, gamma = 16, 4.0, math.radians(14.6)
+    h = L / n
+    v1c, v2c, v12c, E = -0.8 + 0.1j, -0.6, 0.3 - 0.05j, 0.4
+    p = O.Params(n, n, L, L, 99.0, 99.0, 0.0, E, levels=3, n_b=0, nu1=nu1, nu2=nu2, coarse_gamma=gamma)
+    v1 = np.full(n - 1, v1c, dtype=np.complex128)
+    v2 = np.full(n - 1, v2c, dtype=np.complex128)
+    v12 = np.full((n - 1, n - 1), v12c, dtype=np.complex128)
+    levels = O.build_levels(p, v1, v2, v12)
+    N = (n - 1) ** 2
+    M = np.zeros((N, N), dtype=np.complex128)
+    f0 = np.zeros((n - 1, n - 1), dtype=np.complex128)
+    for q in range(N):
+        e = np.zeros(N, dtype=np.complex128)
+        e[q] = 1
+        M[:, q] = O.vcycle(levels, p, e.reshape(n - 1, n - 1), f0).ravel()
+    i = np.arange(1, n)
+    Q1 = np.sin(np.outer(i, i) * math.pi / n)
+    Q = np.kron(Q1, Q1)
+    Mhat = (Q @ M @ Q) / (n / 2) ** 2
+    expect = _lfa_three_grid(n, h, gamma, v1c + v2c + v12c - E, 2.0 / 3.0, nu1, nu2)
+    assert abs(expect).max() > 0.05
+    assert abs(Mhat - expect).max() <= 1e-12
+
+
 def test_direct_solve_parity():
     """MG-CCCS iterated to 1e-13 agrees with sparse LU of the weighted system (the
     paper's direct reference method, Sec. 3.2), TP potentials, ECS grid."""
@@ -398,6 +494,39 @@ def test_planted_mistakes_are_caught(monkeypatch):
     with pytest.raises(AssertionError):
         test_bound_states_bilinear_orthonormal_and_refined()
     monkeypatch.setattr(O, "_normalise", orig_norm)
+
+
+def _planted_build_levels(offset=0, coarse_potential=1.0, rotate_potential=False, rotate=True):
+    """build_levels with one plausible mistake: the injection stride shifted by `offset`,
+    the coarse potentials scaled by `coarse_potential`, the contour rotation applied to the
+    potentials as well, or the coarse levels left unrotated."""
+    def bad(p, v1, v2, v12):
+        out = []
+        for l in range(p.levels):
+            s = 1 << l
+            g = p.coarse_gamma if (l > 0 and rotate) else 0.0
+            o = s - 1 + (offset if l > 0 else 0)
+            sc = (coarse_potential if l > 0 else 1.0) * (np.exp(-2j * p.coarse_gamma) if rotate_potential and l else 1.0)
+            out.append(O.Level(O.make_axis(p.nx >> l, p.Lx, p.R0x, p.theta, g),
+                               O.make_axis(p.ny >> l, p.Ly, p.R0y, p.theta, g),
+                               sc * v1[o::s][: (p.nx >> l) - 1].copy(), sc * v2[o::s][: (p.ny >> l) - 1].copy(),
+                               sc * v12[o::s, o::s][: (p.ny >> l) - 1, : (p.nx >> l) - 1].copy(), p.E))
+        return out
+    return bad
+
+
+@pytest.mark.parametrize("mistake", [dict(offset=1), dict(offset=-1), dict(coarse_potential=0.0),
+                                     dict(rotate_potential=True), dict(rotate=False)])
+def test_planted_coarse_level_mistakes_are_caught(monkeypatch, mistake):
+    """A mistake planted in the oracle's coarse levels (an injection offset off by one
+    either way, no potential on the coarse levels, the rotation applied to the potential,
+    unrotated coarse levels) fails the coarse-level pins; the unplanted oracle passes both."""
+    test_coarse_level_potentials_are_the_potentials_at_the_coarse_nodes(64, 4, 15.0, 10.0)
+    test_three_level_cycle_with_potential_matches_fourier_analysis(1, 1)
+    monkeypatch.setattr(O, "build_levels", _planted_build_levels(**mistake))
+    with pytest.raises(AssertionError):
+        test_coarse_level_potentials_are_the_potentials_at_the_coarse_nodes(64, 4, 15.0, 10.0)
+        test_three_level_cycle_with_potential_matches_fourier_analysis(1, 1)
 
 
 # ------------------------------------------------------------------ GMRES acceleration (Sec. 6)
