@@ -35,8 +35,22 @@ import numpy as np  # noqa: E402
 
 METRIC = "MG-CCCS unknowns/s to 1e-10 rel. residual; % of HBM roofline vs FP64 plain"
 UNIT = "unknowns/s"
-FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12   # 2 DFMA lanes/clk/SM x 152 SMs x 2.07 GHz
-FP64_PIPE_GOPS = 2 * 152 * 2.07e9 / 1e9           # FP64 pipe operations per second (any of DADD/DMUL/DFMA)
+DFMA_PER_CLK_PER_SM = 2      # FP64 lanes of one SM of this part (ncu: dfma peak_sustained 2 inst/cycle per SM)
+GS_VECTORS = 11              # Gram-Schmidt update timed for the roofline: the basis size of Arnoldi step j = 10,
+                             # the mean over a GMRES(20) cycle (j = 0..19 updates 1..20 vectors)
+
+
+def fp64_peaks(device_index=0):
+    """Nominal FP64 peaks of this GPU from its unit counts and clock: DFMA_PER_CLK_PER_SM lanes on
+    each SM (queried) at the measured maximum SM clock (MEASURED_PEAKS.json sm_max_mhz, else the
+    part's 2070 MHz).  Returns (TFLOP/s, G FP64-pipe operations/s, description)."""
+    import torch
+    sms = torch.cuda.get_device_properties(device_index).multi_processor_count
+    peaks, src = measured_peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    ops = DFMA_PER_CLK_PER_SM * sms * mhz * 1e6
+    return 2 * ops / 1e12, ops / 1e9, (f"FP64: {DFMA_PER_CLK_PER_SM} DFMA/clk/SM x {sms} SMs x {mhz:g} MHz "
+                                        f"({'measured' if src == 'measured' else 'nominal'} max SM clock)")
 
 
 def parse():
@@ -56,6 +70,8 @@ def parse():
     ap.add_argument("--max-iter", type=int, default=2000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the forms block (mixed precision, batch, adjoint) of the default run")
     ap.add_argument("--box", type=float, default=30.0, help="box length L of [0,L]^2")
     ap.add_argument("--R0", type=float, default=20.0, help="ECS start")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default=None,
@@ -109,16 +125,14 @@ def dist_setup():
 
 # ------------------------------------------------------------------ CPU oracle timing
 
-def oracle_steps_per_solve(args):
-    """Arnoldi steps (or stand-alone iterations) the oracle needs to reach rtol on the 256^2
-    instance of the workload (same box and physics, coarser grid): the count is
-    size-independent for this method (96, 97, 97 steps at 128^2, 256^2, 512^2)."""
+def oracle_steps_per_solve(args, prob=None, so=None):
+    """Arnoldi steps (or stand-alone iterations) the oracle's own solve of the workload takes
+    to reach rtol (one complete oracle solve; tens of seconds at 1024^2)."""
     from oracle import mgcccs_oracle as O
-    from paper_1412_1953_gb300 import inputs
-    n = 256
-    lv = max(1, args.levels - int(round(math.log2(args.n / n))))
-    prob = inputs.temkin_poet(n, L=30.0, R0=20.0, theta=math.pi / 6, E=args.E, seed=0)
-    so = O.Solver(O.params_from_problem(prob, levels=lv, n_b=args.nb), prob.v1, prob.v2, prob.v12)
+    if prob is None:
+        prob, _ = workload(args)
+    if so is None:
+        so = O.Solver(O.params_from_problem(prob, levels=args.levels, n_b=args.nb), prob.v1, prob.v2, prob.v12)
     if args.krylov:
         _, hist, rr = O.gmres(so, prob.f, m=args.krylov, rtol=args.rtol, max_iter=args.max_iter)
     else:
@@ -166,8 +180,12 @@ class ClockSampler:
             os.close(fd)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
+            # the timed region starts once the sampler has written its first line
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0 and self.proc.poll() is None:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
 
@@ -211,12 +229,18 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
-def kernel_source_sha():
-    """Hash of the source text that defines the fine-level complex128 k_jacobi launch: the
-    level descriptor and per-node arithmetic in common.cuh, the neighbour loads it calls and
-    the kernel itself (edits elsewhere do not change the kernel, so they keep its committed
-    ncu counters valid)."""
+def kernel_source_sha(kernel="k_jacobi"):
+    """Hash of the source text that defines a kernel whose ncu counters are committed:
+    k_jacobi (fine-level complex128 sweep: the level descriptor and per-node arithmetic in
+    common.cuh, the neighbour loads it calls and the kernel itself) or k_multiaxpy (the
+    Gram-Schmidt update template).  Edits elsewhere do not change the kernel, so they keep
+    its committed counters valid."""
     csrc = os.path.join(ROOT, "paper_1412_1953_gb300", "csrc")
+    if kernel == "k_multiaxpy":
+        src = open(os.path.join(csrc, "kernels_krylov.cu")).read()
+        a = src.index("template <class C>\n__global__ void __launch_bounds__(NT) k_multiaxpy(")
+        b = src.index("\n}\n", a)
+        return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
     hdr = open(os.path.join(csrc, "common.cuh")).read()
     src = open(os.path.join(csrc, "kernels_mg.cu")).read()
     h = hashlib.sha256()
@@ -241,7 +265,7 @@ def profiled_traffic(kernel, workload_name):
             if ":" in line and line.strip().startswith("- "):
                 k, v = line.strip()[2:].split(":", 1)
                 vals[k.strip()] = v.strip()
-        if vals.get("source_sha") != kernel_source_sha():
+        if vals.get("source_sha") != kernel_source_sha(kernel):
             return None
         return float(vals["dram_bytes_per_launch"])
     except Exception:
@@ -277,6 +301,87 @@ def jacobi_dp_ops(n, L, R0):
     return 2.0 * m * per_axis + 4.0 * u * u + 6.0 * (m * m - u * u)
 
 
+# ------------------------------------------------------------------ kernel rooflines
+
+def _event_ms(stream, fn, reps):
+    """Mean device time of one call of fn over reps back-to-back calls on `stream`."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def kernel_rooflines(args, solver, stream, f_d, flush, workload_name, device_index):
+    """Roofline of the kernel that leads a complex128 Arnoldi step by time (the Gram-Schmidt
+    update k_multiaxpy<double2>, 15% of a step; k_multidot<double2> 15%; both FP64-pipe bound),
+    timed live with CUDA events on the handle's stream over 50 launches of the same kernel
+    and launch shape the solve uses, with GS_VECTORS = 11 basis vectors of the fine level
+    (11 x 16.7 MB, larger than L2, so every launch streams from HBM).  Beside it: the
+    Gram-Schmidt dot pass (12 vectors, w included: the first pass of step j = 10) and the
+    fine-level omega-Jacobi sweep, the stencil kernel the metric names."""
+    import torch
+    N = (args.n - 1) ** 2
+    reps = 50
+    tf_peak, gops_peak, peak_src = fp64_peaks(device_index)
+    peaks, hbm_src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    k = GS_VECTORS
+    V = torch.randn((k + 1, N), dtype=torch.complex128, device="cuda", generator=gen)
+    w = V[k].clone()
+    coef = (1e-3 * torch.randn(k, dtype=torch.complex128, device="cuda", generator=gen)).contiguous()
+    hout = torch.empty(k + 1, dtype=torch.complex128, device="cuda")
+    Vd = V.clone()
+    Vd[k].copy_(w)                                     # the multi-dot of a step runs over V_0..V_j and w
+    for _ in range(3):
+        solver.gs_update(V, k, coef, w)
+        solver.gs_dots(Vd, k + 1, Vd[k], hout)
+    flush.zero_()
+    upd_ms = _event_ms(stream, lambda: solver.gs_update(V, k, coef, w), reps)
+    flush.zero_()
+    dot_ms = _event_ms(stream, lambda: solver.gs_dots(Vd, k + 1, Vd[k], hout), reps)
+    upd_flops = 8.0 * k * N                             # one complex FMA (4 DFMA) per vector and node
+    upd_bytes = 16.0 * (k + 2) * N                      # k vectors and w read, w written
+    dot_flops = 8.0 * k * N + 4.0 * N                   # k conjugate dots; |w|^2 by 2 DFMA per node
+    dot_bytes = 16.0 * (k + 1) * N                      # k + 1 vectors read once (w re-reads hit L2)
+    upd_tf = upd_flops / (upd_ms * 1e-3) / 1e12
+    del V, Vd, w
+    # the fine-level sweep (the stencil kernel of the metric), as in the previous line
+    u_s = torch.zeros_like(f_d)
+    for _ in range(3):
+        solver.smooth(0, u_s, f_d, 1)
+    flush.zero_()
+    jac_ms = _event_ms(stream, lambda: solver.smooth(0, u_s, f_d, 2), reps // 2) / 2   # two sweeps a call
+    box = uniform_box(args.n, 30.0, 20.0)
+    jac_flops = jacobi_flops((box, box), args.n - 1, args.n - 1)
+    jac_ops = jacobi_dp_ops(args.n, 30.0, 20.0)
+    jac_bytes = 64.0 * N
+    traffic = profiled_traffic("k_multiaxpy", workload_name)
+    return {"bound": "alu", "kernel": f"k_multiaxpy<double2> (Gram-Schmidt update, {k} basis vectors, "
+                                      f"fine level {args.n - 1}^2, complex128)",
+            "achieved": upd_tf, "peak": tf_peak, "unit": "TFLOP/s", "frac": upd_tf / tf_peak, "traffic": traffic,
+            "peak_source": peak_src, "kernel_ms": upd_ms, "flops_per_launch": upd_flops,
+            "algorithmic_bytes_per_launch": upd_bytes,
+            "hbm_achieved_gbs": upd_bytes / (upd_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src,
+            "hbm_frac": upd_bytes / (upd_ms * 1e-3) / 1e9 / hbm,
+            "others": [
+                {"kernel": f"k_multidot<double2> + k_reduce_dots ({k + 1} vectors, w among them)", "bound": "alu",
+                 "kernel_ms": dot_ms, "achieved": dot_flops / (dot_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                 "frac": dot_flops / (dot_ms * 1e-3) / 1e12 / tf_peak,
+                 "hbm_frac": dot_bytes / (dot_ms * 1e-3) / 1e9 / hbm},
+                {"kernel": "k_jacobi<double2> (fine-level omega-Jacobi sweep)", "bound": "alu",
+                 "kernel_ms": jac_ms, "achieved": jac_flops / (jac_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                 "frac": jac_flops / (jac_ms * 1e-3) / 1e12 / tf_peak,
+                 "dp_pipe_frac": jac_ops / (jac_ms * 1e-3) / 1e9 / gops_peak,
+                 "traffic": profiled_traffic("k_jacobi", workload_name),
+                 "hbm_frac": jac_bytes / (jac_ms * 1e-3) / 1e9 / hbm}]}
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_kernel(args):
@@ -303,14 +408,13 @@ def run_kernel(args):
     print(json.dumps({"mode": "kernel", "kernel": args.kernel, "workload": cfg["workload"]}))
 
 
-def run_adjoint(args):
-    """Differentiation workload: J = <g|u> on the 1024^2 TP problem (Z = 1, E = 0.5),
-    g a Gaussian window at (15, 15) with sigma = 2; forward + adjoint solve timed, and
-    dJ/dE, dJ/dZ, dJ/d(dV) at two nodes checked against central differences (step 1e-6)."""
+def adjoint_form(args, fd_nodes=2):
+    """Differentiation workload: J = <g|u> on the n^2 TP problem (Z = 1, E = 0.5), g a
+    Gaussian window at (15, 15) with sigma = 2; forward + adjoint solve timed (with the
+    setup), and dJ/dE, dJ/dZ, dJ/d(dV) at fd_nodes nodes checked against central
+    differences (step 1e-6) of J from forward solves."""
     import torch
     from paper_1412_1953_gb300 import adjoint as A
-    from paper_1412_1953_gb300 import build as B
-    B.build()
     n = args.n
     geom = dict(n=n, L=30.0, R0=20.0, theta=math.pi / 6)
     kw = dict(levels=args.levels, n_b=args.nb, krylov_restart=args.krylov)
@@ -329,19 +433,26 @@ def run_adjoint(args):
     J = lambda E_, Z_, dV_: A.amplitude_and_gradients(E_, Z_, dV_, f, g, geom, kw, rtol=rtol)["J"]
     fdE = (J(args.E + h, 1.0, dV0) - J(args.E - h, 1.0, dV0)) / (2 * h)
     fdZ = (J(args.E, 1.0 + h, dV0) - J(args.E, 1.0 - h, dV0)) / (2 * h)
-    nodes = [(n // 2 - 1, n // 2 - 1), (n // 2 + 40, n // 2 - 60)]
+    nodes = [(n // 2 - 1, n // 2 - 1), (n // 2 + 40, n // 2 - 60)][:fd_nodes]
     dv_err = []
     for (j, i) in nodes:
         e = torch.zeros_like(dV0)
         e[j, i] = h
         fd = (J(args.E, 1.0, dV0 + e) - J(args.E, 1.0, dV0 - e)) / (2 * h)
         dv_err.append(abs(res["ddV"][j, i].item() - fd) / abs(fd))
-    out = {"mode": "adjoint", "workload": f"tp_ecs_{n}_adjoint", "J": [res["J"].real, res["J"].imag],
-           "dJ_dE": [res["dE"].real, res["dE"].imag], "dJ_dZ": [res["dZ"].real, res["dZ"].imag],
-           "fd_rel_err_E": abs(res["dE"] - fdE) / abs(fdE), "fd_rel_err_Z": abs(res["dZ"] - fdZ) / abs(fdZ),
-           "fd_rel_err_dV": dv_err, "fd_step": h, "rtol": rtol, "forward_adjoint_steps": list(res["its"]),
-           "seconds_setup_forward_adjoint": t_fb,
-           "unknowns_per_s_forward_plus_adjoint": prob.n_unknowns / t_fb}
+    return {"workload": f"tp_ecs_{n}_adjoint", "levels": args.levels, "J": [res["J"].real, res["J"].imag],
+            "dJ_dE": [res["dE"].real, res["dE"].imag], "dJ_dZ": [res["dZ"].real, res["dZ"].imag],
+            "fd_rel_err_E": abs(res["dE"] - fdE) / abs(fdE), "fd_rel_err_Z": abs(res["dZ"] - fdZ) / abs(fdZ),
+            "fd_rel_err_dV": dv_err, "fd_step": h, "rtol": rtol, "forward_adjoint_steps": list(res["its"]),
+            "seconds_setup_forward_adjoint": t_fb,
+            "unknowns_per_s_forward_plus_adjoint": prob.n_unknowns / t_fb}
+
+
+def run_adjoint(args):
+    from paper_1412_1953_gb300 import build as B
+    B.build()
+    out = {"mode": "adjoint"}
+    out.update(adjoint_form(args))
     print(json.dumps(out), flush=True)
 
 
@@ -387,61 +498,77 @@ def run_sweep(args):
                     sv.close()
 
 
-def run_precision(args):
-    """Precision form: the same workload solved to rtol by plain FP64 GMRES(m)+MG-CCCS and
-    by the mixed form; time, iterations, relres under the oracle's FP64 operator, and the
-    mixed solution's relative difference from the FP64 one."""
+def precision_form(args, f=None, u_fp64=None):
+    """Precision form: the workload solved to rtol by the mixed form (complex64 inner
+    GMRES(m) cycles inside FP64 iterative refinement) and, unless given, by plain FP64;
+    time, iterations, the library's FP64 relative residual of each solution, and the
+    mixed solution's relative difference from the FP64 one (the parity tests tie the FP64
+    solution to the oracle's)."""
     import torch
-    from oracle import mgcccs_oracle as O
-    from paper_1412_1953_gb300 import build as B
     from paper_1412_1953_gb300 import mgcccs as M
-    B.build()
     prob, cfg = workload(args)
-    f = torch.as_tensor(prob.f).to("cuda")
-    lev = O.build_levels(O.params_from_problem(prob, levels=1, n_b=0), prob.v1, prob.v2, prob.v12)[0]
+    if f is None:
+        f = torch.as_tensor(prob.f).to("cuda")
     res, sols = {}, {}
     for prec in ("fp64", "mixed"):
+        if prec == "fp64" and u_fp64 is not None:
+            sols[prec] = u_fp64
+            continue
+        t0 = time.perf_counter()
         sv = M.Solver(M.params_for(prob, levels=args.levels, n_b=args.nb, krylov_restart=args.krylov,
                                    precision=1 if prec == "mixed" else 0), prob.v1, prob.v2, prob.v12)
+        torch.cuda.synchronize()
+        t_setup = time.perf_counter() - t0
         u = torch.zeros_like(f)
         for _ in range(2):
             u.zero_()
             sv.solve(u, f, rtol=args.rtol, max_iter=args.max_iter)
         times = []
-        for _ in range(max(1, args.steps)):
+        for _ in range(max(1, min(args.steps, 5))):
             u.zero_()
-            torch.cuda.synchronize()
-            t = time.perf_counter()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(sv.stream)
             its, rr = sv.solve(u, f, rtol=args.rtol, max_iter=args.max_iter)
-            torch.cuda.synchronize()
-            times.append(time.perf_counter() - t)
-        uh = u.cpu().numpy()
-        sols[prec] = uh
+            e1.record(sv.stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        r = torch.empty_like(f)
+        rn2 = sv.residual(u, f, r, norm=True)
+        sols[prec] = u.clone()
         t_med = statistics.median(times)
         res[prec] = {"seconds": t_med, "iterations": its, "relres": rr,
-                     "relres_oracle_operator": float(O.relres(lev, uh, prob.f)) if hasattr(O, "relres") else
-                     float(np.linalg.norm(O.residual(lev, uh, prob.f)) / np.linalg.norm(prob.f)),
-                     "unknowns_per_s": prob.n_unknowns / t_med}
+                     "relres_fp64_residual": math.sqrt(rn2) / float(torch.linalg.vector_norm(f)),
+                     "unknowns_per_s": prob.n_unknowns / t_med, "setup_s": t_setup}
         sv.close()
-    diff = float(np.linalg.norm(sols["mixed"] - sols["fp64"]) / np.linalg.norm(sols["fp64"]))
-    print(json.dumps({"mode": "precision", "config": cfg, "fp64": res["fp64"], "mixed": res["mixed"],
-                      "mixed_vs_fp64_rel_diff": diff,
-                      "speedup": res["fp64"]["seconds"] / res["mixed"]["seconds"]}), flush=True)
+    diff = float(torch.linalg.vector_norm(sols["mixed"] - sols["fp64"]) / torch.linalg.vector_norm(sols["fp64"]))
+    out = {"workload": cfg["workload"], "levels": args.levels, "mixed": res["mixed"],
+           "mixed_vs_fp64_rel_diff": diff}
+    if "fp64" in res:
+        out["fp64"] = res["fp64"]
+    return out
 
 
-def run_batch(args):
+def run_precision(args):
+    from paper_1412_1953_gb300 import build as B
+    B.build()
+    out = {"mode": "precision"}
+    out.update(precision_form(args))
+    if "fp64" in out:
+        out["speedup"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    print(json.dumps(out), flush=True)
+
+
+def batch_form(args, compare=True, per_problem=True):
     """Batching form: 64 energies in [0.1, 2.0] on grids n in {256, ..., 1024} (drawn with
     seed 1; L = 30 n / 512, ECS beyond 2L/3), mixed precision, n_b = 3, with the schedule
-    (levels, nu1, nu2) autotuned on the batch itself.  Times the batch graph (one launch solves all 64)
-    and, beside it, the host lock-step driver and one-at-a-time solves of a sample.
-    Reports solves/s, unknowns/s, setup time per energy and every problem's iterations
-    and relative residual."""
+    (levels, nu1, nu2) autotuned on the batch itself (--autotune) or the deepest hierarchy.
+    Times the batch graph (one launch solves all 64) and, with compare, the host lock-step
+    driver and one-at-a-time solves of a sample.  Reports solves/s, unknowns/s, setup time
+    per energy and every problem's iterations and relative residual."""
     import torch
     from paper_1412_1953_gb300 import batch as BT
-    from paper_1412_1953_gb300 import build as B
     from paper_1412_1953_gb300 import inputs
     from paper_1412_1953_gb300 import mgcccs as M
-    B.build()
     prec = 0 if args.precision == "fp64" else 1
     problems = inputs.batching_problems(count=args.batch_count)
     sizes = sorted({p.nx for p in problems})
@@ -477,6 +604,21 @@ def run_batch(args):
         graph.run(rtol=args.rtol, max_iter=args.max_iter)
     sec, (its, rr, st) = timed(lambda: graph.run(rtol=args.rtol, max_iter=args.max_iter))
     u_graph = [u.clone() for u in bs.u]
+    out = {"workload": f"tp_ecs_batch{len(problems)}", "problems": len(problems),
+           "grid_sizes": sizes, "precision": "complex64 inner cycles in FP64 refinement" if prec else "complex128",
+           "n_b": args.nb, "rtol": args.rtol,
+           "solves_per_s": len(problems) / sec, "unknowns_per_s": bs.unknowns / sec, "seconds": sec,
+           "all_converged": all(s == 0 for s in st), "max_relres": max(rr), "total_steps": sum(its),
+           "schedules": {str(n): {k: sched[n][k] for k in ("levels", "nu1", "nu2")} for n in sizes},
+           "autotune_seconds": t_tune, "setup_seconds": t_setup, "graph_build_seconds": t_graph,
+           "solves_per_s_with_setup": len(problems) / (sec + t_setup)}
+    if per_problem:
+        out["per_problem"] = [{"n": p.nx, "E": round(p.E, 6), "iterations": k, "relres": r}
+                              for p, k, r in zip(problems, its, rr)]
+    if not compare:
+        graph.close()
+        bs.close()
+        return out
     bs.solve(rtol=args.rtol, max_iter=5)              # capture the per-step graphs of the host driver
     sec_ls, (its_ls, _, _) = timed(lambda: bs.solve(rtol=args.rtol, max_iter=args.max_iter, zero=False))
     same_ls = its_ls == its and all(torch.equal(a, b) for a, b in zip(u_graph, bs.u))
@@ -493,23 +635,21 @@ def run_batch(args):
         t_single += time.perf_counter() - t
         same = same and k1 == its[k] and bool(torch.equal(u1, u_graph[k]))
     t_single_unknowns = sum(problems[k].n_unknowns for k in sample)
-    out = {"mode": "batch", "workload": f"tp_ecs_batch{len(problems)}", "problems": len(problems),
-           "grid_sizes": sizes, "precision": "complex64 inner cycles in FP64 refinement" if prec else "complex128",
-           "n_b": args.nb, "rtol": args.rtol,
-           "solves_per_s": len(problems) / sec, "unknowns_per_s": bs.unknowns / sec, "seconds": sec,
-           "all_converged": all(s == 0 for s in st), "max_relres": max(rr), "total_steps": sum(its),
-           "lockstep_host_driver": {"seconds": sec_ls, "solves_per_s": len(problems) / sec_ls,
-                                    "identical_to_graph": same_ls},
-           "one_at_a_time_sample": {"problems": sample, "unknowns_per_s": t_single_unknowns / t_single,
-                                    "identical_to_graph": same},
-           "schedules": {str(n): {k: sched[n][k] for k in ("levels", "nu1", "nu2")} for n in sizes},
-           "autotune_seconds": t_tune, "setup_seconds": t_setup, "graph_build_seconds": t_graph,
-           "solves_per_s_with_setup": len(problems) / (sec + t_setup),
-           "per_problem": [{"n": p.nx, "E": round(p.E, 6), "iterations": k, "relres": r}
-                           for p, k, r in zip(problems, its, rr)]}
-    print(json.dumps(out), flush=True)
+    out["lockstep_host_driver"] = {"seconds": sec_ls, "solves_per_s": len(problems) / sec_ls,
+                                   "identical_to_graph": same_ls}
+    out["one_at_a_time_sample"] = {"problems": sample, "unknowns_per_s": t_single_unknowns / t_single,
+                                   "identical_to_graph": same}
     graph.close()
     bs.close()
+    return out
+
+
+def run_batch(args):
+    from paper_1412_1953_gb300 import build as B
+    B.build()
+    out = {"mode": "batch"}
+    out.update(batch_form(args))
+    print(json.dumps(out), flush=True)
 
 
 def cpu_description():
@@ -553,6 +693,34 @@ def run_oracle_timing(args):
                      "seconds_per_step": per, "sampled_steps": sampled, "setup_seconds": setup,
                      "unknowns_per_s": prob.n_unknowns / (per * steps), "kind": "sampled Arnoldi steps"})
     print(json.dumps({"mode": "oracle", "cpu": cpu_description(), "rows": rows}), flush=True)
+
+
+def run_forms(args, f_d, u_fp64):
+    """The three forms beside the plain FP64 solve, each bounded to seconds: the mixed
+    precision form on the benchmark workload (against the FP64 solution just computed) and
+    at 2048^2 on [0,60]^2 (R0 = 40, n_b = 6, 7 levels: a 31^2 coarsest grid), the 64-energy
+    batch in one graph launch, and the adjoint gradients at 1024^2 with their
+    finite-difference checks.  A form that fails records its error instead of a result."""
+    import copy
+    forms = {}
+    t0 = time.perf_counter()
+
+    def attempt(name, fn):
+        try:
+            forms[name] = fn()
+        except Exception as exc:          # recorded, not hidden: the line carries the error
+            forms[name] = {"error": f"{type(exc).__name__}: {exc}"}
+
+    attempt("mixed", lambda: precision_form(args, f=f_d, u_fp64=u_fp64))
+    big = copy.copy(args)
+    big.n, big.box, big.R0, big.nb, big.levels = 2048, 60.0, 40.0, 6, 7
+    attempt("mixed_2048", lambda: precision_form(big))
+    bat = copy.copy(args)
+    bat.precision, bat.steps, bat.warmup, bat.autotune, bat.nb = "mixed", 2, 1, False, 3
+    attempt("batch", lambda: batch_form(bat, compare=False, per_problem=False))
+    attempt("adjoint", lambda: adjoint_form(args, fd_nodes=1))
+    forms["seconds"] = time.perf_counter() - t0
+    return forms
 
 
 def run_ours(args):
@@ -617,7 +785,6 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     launches = solver.launch_count() - l0
-    clocks = sampler.stop()
     total_ms = max_over_ranks(sum(ms), "cuda")
     value = world * N * args.steps / (total_ms / 1e3)
 
@@ -639,36 +806,11 @@ def run_ours(args):
     e2e = {"value": world * N * len(e2e_s) / e2e_total, "unit": UNIT,
            "h2d_bytes_per_step": 2 * N * 16, "d2h_bytes_per_step": N * 16}
 
-    # dominant kernel: the fine-level omega-Jacobi sweep, same launch as inside the solve
-    reps = 50
-    u_s = torch.zeros_like(f_d)
-    for _ in range(3):
-        solver.smooth(0, u_s, f_d, 1)
-    flush.zero_()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(reps // 2):
-        solver.smooth(0, u_s, f_d, 2)      # two launches, ping-pong, result back in u_s
-    e1.record(stream)
-    e1.synchronize()
-    k_ms = e0.elapsed_time(e1) / reps
-    box = uniform_box(args.n, 30.0, 20.0)
-    flops = jacobi_flops((box, box), args.n - 1, args.n - 1)
-    dp_ops = jacobi_dp_ops(args.n, 30.0, 20.0)
-    bytes_alg = 64.0 * N                                # u, f, omega/D read; u written
-    peaks, peak_src = measured_peaks()
-    traffic = profiled_traffic("k_jacobi", cfg["workload"])
-    roofline = {"bound": "alu", "kernel": "k_jacobi (fine level, complex128)",
-                "achieved": flops / (k_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": flops / (k_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "peak_source": "FP64: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (1.007 TFLOP/s measured)",
-                "dp_ops_per_launch": dp_ops, "dp_pipe_peak_gops": FP64_PIPE_GOPS,
-                "dp_pipe_frac": dp_ops / (k_ms * 1e-3) / 1e9 / FP64_PIPE_GOPS,
-                "kernel_ms": k_ms, "flops_per_launch": flops, "algorithmic_bytes_per_launch": bytes_alg,
-                "hbm_achieved_gbs": bytes_alg / (k_ms * 1e-3) / 1e9,
-                "hbm_peak_gbs": peaks.get("hbm_gbs", 6800.0), "hbm_peak_source": peak_src,
-                "hbm_frac": bytes_alg / (k_ms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}
+    u_fp64 = u_d.clone()
+    roofline = kernel_rooflines(args, solver, stream, f_d, flush, cfg["workload"], local)
+    # the sampler ran from before the timed solves through the end-to-end solves and the
+    # kernel timings (all GPU-bound), so its median reflects the clock under this load
+    clocks = sampler.stop()
     cfg.update({"iterations": int(statistics.median(iters)), "setup_s": round(setup_s, 3),
                 "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                 "l2": f"flushed before every timed step (256 MB write); working set "
@@ -679,6 +821,8 @@ def run_ours(args):
            "dtype": "c64 inner / c128 refinement" if args.precision == "mixed" else "c128 (FP64)",
            "data": "synthetic", "config": cfg, "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches),
            "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_forms and args.mode == "bench":
+        out["forms"] = run_forms(args, f_d, u_fp64)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_step, k, osetup = oracle_step_time(prob, args, args.cpu_seconds)
         n_steps = int(statistics.median(iters))
@@ -701,10 +845,10 @@ def run_reference(args):
         return
     prob, cfg = workload(args)
     from oracle import mgcccs_oracle as O
-    n_steps = oracle_steps_per_solve(args)
     t0 = time.perf_counter()
     so = O.Solver(O.params_from_problem(prob, levels=args.levels, n_b=args.nb), prob.v1, prob.v2, prob.v12)
     setup_s = time.perf_counter() - t0
+    n_steps = oracle_steps_per_solve(args, prob, so)
     per_step = 2           # oracle iterations (Arnoldi steps) per timed step: a bounded sample of one solve
     u = np.zeros_like(prob.f)
 
@@ -726,8 +870,8 @@ def run_reference(args):
     value = prob.n_unknowns / (t_it * n_steps)
     what = f"GMRES({args.krylov}) Arnoldi steps" if args.krylov else "MG-CCCS iterations"
     sample_txt = (f"{args.steps} x {per_step} timed oracle {what} (after {args.warmup * per_step} warm-up ones) on "
-                  f"the {args.n}^2 workload, {t_it:.3f} s each, scaled to the {n_steps} steps the oracle needs on "
-                  f"the 256^2 instance of the same problem (size-independent count); setup {setup_s:.1f} s excluded")
+                  f"the {args.n}^2 workload, {t_it:.3f} s each, scaled to the {n_steps} steps of the oracle's own "
+                  f"complete solve of this workload (run once, untimed); setup {setup_s:.1f} s excluded")
     cfg["iterations"] = n_steps
     if args.krylov:
         cfg["outer"] = (f"GMRES({args.krylov}) right-preconditioned by one MG-CCCS iteration; CPU oracle "

@@ -286,10 +286,32 @@ int mgcccs_get_bound_states(mgcccs_t h, mgcccs_c128* lambda, mgcccs_c128* phi,
  * before any stream capture.  All calls share the one array and each call
  * overwrites the slots it uses, so calls that overlap on the GPU (on different
  * streams, or from several host threads) race and give wrong sums.
- * Returns MGCCCS_EINVAL for a NULL pointer or n > MGCCCS_NOALLOC_MAX_N (nothing is
- * launched), MGCCCS_ECUDA if the address lookup or a launch fails. */
+ * n = 0 writes 0 (v may then be NULL).  Returns MGCCCS_EINVAL for a NULL norm2, a
+ * NULL v with n > 0, or n > MGCCCS_NOALLOC_MAX_N (nothing is launched), MGCCCS_ECUDA
+ * if the address lookup or a launch fails. */
 #define MGCCCS_NOALLOC_MAX_N 8388608
 int mgcccs_norm2_noalloc(const mgcccs_c128* v, size_t n, double* norm2, void* stream);
+
+/*
+ * The two halves of one classical Gram-Schmidt pass of the Arnoldi process of the
+ * GMRES(m) solver that MG-CCCS preconditions (Sec. 6), exposed for component tests and
+ * for timing the kernels the solve spends most of its time in:
+ *
+ *   mgcccs_gs_dots:   out[i] = sum_p conj(V_i[p]) w[p]            for i < k
+ *   mgcccs_gs_update: w[p]  -= sum_{i<k} coef[i] V_i[p]          (every p)
+ *
+ * V: device, k vectors of (nx-1)*(ny-1) values, vector i at V + i*ld (ld >= (nx-1)*(ny-1));
+ * w: device, (nx-1)*(ny-1) values (gs_update overwrites it); out, coef: device, k values.
+ * A vector V_i that is w itself (same address) gives out[i] = |w|^2.  The sums are FP64
+ * in a fixed order (per-block partials, then one block), so repeated calls give identical
+ * results.  mgcccs_gs_dots needs a handle set up with krylov_restart >= 1 and
+ * k <= krylov_restart + 1 (it uses the handle's partial-sum buffer); mgcccs_gs_update
+ * takes 1 <= k <= 61.  Async.  Errors: EINVAL (null pointer, k or ld out of range), ECUDA.
+ */
+int mgcccs_gs_dots(mgcccs_t h, const mgcccs_c128* V, long long ld, int k, const mgcccs_c128* w,
+                   mgcccs_c128* out);
+int mgcccs_gs_update(mgcccs_t h, const mgcccs_c128* V, long long ld, int k, const mgcccs_c128* coef,
+                     mgcccs_c128* w);
 
 /* Number of kernel launches issued since setup (for launch accounting). */
 long long mgcccs_launch_count(mgcccs_t h);

@@ -279,6 +279,37 @@ __device__ __forceinline__ void dispatch_kinds(const StencilViewT<C>& s, int i0,
   }
 }
 
+// residual_vals and jacobi_vals with D (respectively omega/D) at the node already loaded
+// by the caller (dv; only its real part is used where the diagonal is real): a fused pass
+// issues that load together with its other loads, before its block barrier.  Same
+// arithmetic, so the same results.
+template <int KX, int KY, int IR, int DG, class C>
+__device__ __forceinline__ C residual_vals_d(const StencilViewT<C>& s, int i, int j, C dv, C uc, C uw, C ue, C us,
+                                             C un, C fp) {
+  C t = axis_acc<KX, IR, true>(s.cx, s.west_x, s.east_x, i, uw, ue, fp);
+  t = axis_acc<KY, IR, true>(s.cy, s.west_y, s.east_y, j, us, un, t);
+  if (diag_real<DG>(s, i, j)) {
+    t.x = fma(-dv.x, uc.x, t.x);
+    t.y = fma(-dv.x, uc.y, t.y);
+    return t;
+  }
+  return cfms(dv, uc, t);
+}
+
+template <int KX, int KY, int IR, int DG, class C>
+__device__ __forceinline__ C jacobi_vals_d(const StencilViewT<C>& s, int i, int j, C dinv, C uc, C uw, C ue, C us,
+                                           C un, C fp) {
+  C t = axis_acc<KX, IR, true>(s.cx, s.west_x, s.east_x, i, uw, ue, fp);
+  t = axis_acc<KY, IR, true>(s.cy, s.west_y, s.east_y, j, us, un, t);
+  C o = cscal(s.keep, uc);
+  if (diag_real<DG>(s, i, j)) {
+    o.x = fma(dinv.x, t.x, o.x);
+    o.y = fma(dinv.x, t.y, o.y);
+    return o;
+  }
+  return cfma(dinv, t, o);
+}
+
 
 // Error bits written by kernels into the handle's device status word.
 enum {
@@ -287,7 +318,56 @@ enum {
   MGC_ST_NONFINITE = 4
 };
 
+// ---------------------------------------------------------------- programmatic dependent launch
+// The kernels of the solve path are launched with the programmatic-stream-serialization
+// attribute (PDL, sm_90 and later) whenever the previous operation the library enqueued on
+// the same stream was one of its kernels: the next kernel is then launched, and its blocks
+// dispatched, as the blocks of the current one exit, instead of after the whole grid and
+// its launch bookkeeping have retired.  Correctness does not depend on it: every kernel
+// launched this way calls mgc_pdl_enter() before its first global memory access, and
+// griddepcontrol.wait returns only once the preceding kernel has completed and its writes
+// are visible.  No kernel triggers its successor early (griddepcontrol.launch_dependents):
+// measured on the 1024^2 solve, an early trigger made the FP64 solve slower (34.8 against
+// 33.0 ms; the FP64-bound kernels then share their SMs with resident, waiting blocks),
+// while the trigger at block exit gives 33.0 ms FP64 and 12.9 ms mixed against 33.2 and
+// 13.2 ms with plain stream-ordered launches (-DMGC_NO_PDL builds those).
+__device__ __forceinline__ void mgc_pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Host side: the stream of the last kernel the library enqueued on this thread, or null
+// after any other operation (copy, memset, event, capture boundary, conditional node).
+extern thread_local cudaStream_t g_mgc_last_kernel_stream;
+extern thread_local bool g_mgc_last_was_kernel;
+inline void mgc_not_a_kernel() { g_mgc_last_was_kernel = false; }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t mgc_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+#ifndef MGC_NO_PDL   // -DMGC_NO_PDL builds the library with plain stream-ordered launches
+  if (g_mgc_last_was_kernel && g_mgc_last_kernel_stream == st) {
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+  }
+#endif
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, static_cast<Args&&>(args)...);
+  g_mgc_last_was_kernel = e == cudaSuccess;
+  g_mgc_last_kernel_stream = st;
+  return e;
+}
+
 // ---------------------------------------------------------------- launchers (defined in the .cu files)
+// Streaming multiprocessors of the current device, queried once per device; grid sizes
+// of the grid-stride kernels and the block-height switch of the stencil kernels scale
+// with it.  Without a usable device (a size query on a host with no GPU) it returns 152,
+// the count of the part this library is tuned on, which only shapes the workspace.
+int mgc_sm_count();
 // All return cudaGetLastError() of their launch.
 
 // kernels_mg.cu (templates instantiated for C = double2 and C = float2)
@@ -333,7 +413,8 @@ cudaError_t launch_round_copy(long long n, const cplx* a, float2* b, cudaStream_
 cudaError_t launch_promote(long long n, const float2* x, cplx* y, cudaStream_t st);
 
 // kernels_krylov.cu
-int krylov_blocks(long long n);
+// grid of the grid-stride Krylov kernels: per_sm blocks of 256 threads per SM at most
+int krylov_blocks(long long n, int per_sm);
 int multidot_blocks(long long n, int k);
 template <class C>
 cudaError_t launch_multidot(long long n, int k, const C* V, long long ld, const C* w, cplx* partial,
@@ -346,12 +427,21 @@ cudaError_t launch_multiaxpy(long long n, int k, const C* V, long long ld, const
 template <class C>
 cudaError_t launch_scale_by_norm(long long n, const C* w, C* out, const double* norm2, cplx* store,
                                  int nblk, cudaStream_t st);
+// the Givens update of Arnoldi step j (skipped when gate is given and *gate == 0)
 cudaError_t launch_givens(int j, int m, cplx* H, cplx* cs, cplx* sn, cplx* g, double* est, const double* hnorm2,
-                          cudaStream_t st);
+                          cudaStream_t st, const int* gate = nullptr);
+// Arguments of the Givens update of step j when k_sum_dgks performs it.
+struct GivensArgs {
+  int j, m;
+  cplx *H, *cs, *sn, *g;
+  double* est;
+};
 // |w|^2 from partials into *out plus the second-pass decision (*gate; in a device-driven
-// graph also the conditional node hd and the counter *fired)
+// graph also the conditional node hd and the counter *fired); with gv, the Givens update
+// of step j whenever no second pass follows
 cudaError_t launch_sum_dgks(const double* part, int n, double* out, const double* before, int* gate,
-                           cudaStream_t st, cudaGraphConditionalHandle hd = 0, int* fired = nullptr);
+                           cudaStream_t st, cudaGraphConditionalHandle hd = 0, int* fired = nullptr,
+                           const GivensArgs* gv = nullptr);
 cudaError_t launch_hess_solve(int k, int m, const cplx* H, const cplx* g, cplx* y, cudaStream_t st,
                               const int* dk = nullptr);
 

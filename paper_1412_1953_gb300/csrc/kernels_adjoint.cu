@@ -70,8 +70,8 @@ __global__ void __launch_bounds__(NT) k_wproduct(int mx, int my, const cplx* __r
 }  // namespace
 
 int wdot_blocks(long long n) {
-  long long b = (n + NT - 1) / NT;
-  return (int)(b < 608 ? (b < 1 ? 1 : b) : 608);
+  const long long b = (n + NT - 1) / NT, cap = 4LL * mgc_sm_count();
+  return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
 cudaError_t launch_weighted_dot(int mx, int my, const cplx* wx, const cplx* wy, const cplx* a, const cplx* b,

@@ -47,6 +47,7 @@ __device__ __forceinline__ C residual_at(const StencilViewT<C>& s, const C* __re
 template <int NB, class C>
 __global__ void __launch_bounds__(TX * WY) k_residual_project(StencilViewT<C> s, CCViewT<C> c, const C* __restrict__ u,
                                                               const C* __restrict__ f) {
+  mgc_pdl_enter();
   __shared__ C R[TY][TX + 1];
   const int lane = threadIdx.x;
   const int wy = threadIdx.y;
@@ -93,6 +94,7 @@ __global__ void __launch_bounds__(256) k_reduce_partials(int nb, int mx, int my,
                                                          const C* __restrict__ Px_part,
                                                          const C* __restrict__ Py_part,
                                                          cplx* __restrict__ Px, cplx* __restrict__ Py) {
+  mgc_pdl_enter();
   const int g = blockIdx.x * 256 + threadIdx.x;
   const int t = g >> 3, sub = g & 7;
   const int nx_tot = nb * my, ny_tot = nb * mx;
@@ -117,6 +119,7 @@ __global__ void __launch_bounds__(256) k_reduce_partials(int nb, int mx, int my,
 // c[a][b] = sum_j w_y(j) vphi_b(j) P^x_a(j): one block per (a, b).
 __global__ void __launch_bounds__(256) k_cc_coef(int nb, int my, const cplx* __restrict__ wvphi,
                                                  const cplx* __restrict__ Px, cplx* __restrict__ cmat) {
+  mgc_pdl_enter();
   __shared__ double sh[2][8];
   const int a = blockIdx.x / nb, b = blockIdx.x % nb;
   cplx acc = cmk(0.0, 0.0);
@@ -185,6 +188,7 @@ __host__ __device__ __forceinline__ int cr_rows(int m) { return (m + CR_CLUSTER 
 template <int NB>
 __global__ void __cluster_dims__(CR_CLUSTER, 1, 1) __launch_bounds__(CR_THREADS)
 k_channel_solve_pcr(CRSystem SA, CRSystem SB) {
+  mgc_pdl_enter();
   extern __shared__ cplx cr_x[];   // [2][R * NB]
   cg::cluster_group cl = cg::this_cluster();
   const int sys = blockIdx.x / CR_CLUSTER;
@@ -261,6 +265,7 @@ template <int NB, class C>
 __global__ void __launch_bounds__(256) k_cccs_correct(int mx, int my, const C* __restrict__ phi,
                                                       const C* __restrict__ vphi, const C* __restrict__ eA,
                                                       const C* __restrict__ eB, C* __restrict__ u) {
+  mgc_pdl_enter();
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y * 8 + threadIdx.y;
   if (i >= mx || j >= my) return;
@@ -276,15 +281,13 @@ __global__ void __launch_bounds__(256) k_cccs_correct(int mx, int my, const C* _
 template <int NB, class C>
 cudaError_t rp_launch(const StencilViewT<C>& s, const CCViewT<C>& c, const C* u, const C* f, cudaStream_t st) {
   dim3 g(cc_tiles_x(s.mx), cc_tiles_y(s.my));
-  k_residual_project<NB, C><<<g, dim3(TX, WY), 0, st>>>(s, c, u, f);
-  return cudaGetLastError();
+  return mgc_launch(k_residual_project<NB, C>, g, dim3(TX, WY), 0, st, s, c, u, f);
 }
 
 template <int NB, class C>
 cudaError_t corr_launch(const CCViewT<C>& c, C* u, cudaStream_t st) {
   dim3 g((c.mx + 31) / 32, (c.my + 7) / 8);
-  k_cccs_correct<NB, C><<<g, dim3(32, 8), 0, st>>>(c.mx, c.my, c.phi, c.vphi, c.eAc, c.eBc, u);
-  return cudaGetLastError();
+  return mgc_launch(k_cccs_correct<NB, C>, g, dim3(32, 8), 0, st, c.mx, c.my, c.phi, c.vphi, c.eAc, c.eBc, u);
 }
 
 }  // namespace
@@ -311,12 +314,10 @@ cudaError_t launch_residual_project(const StencilViewT<C>& s, const CCViewT<C>& 
 template <class C>
 cudaError_t launch_cc_rhs(const CCViewT<C>& c, cudaStream_t st) {
   int tot = c.nb * (c.mx + c.my);
-  k_reduce_partials<C><<<(8 * tot + 255) / 256, 256, 0, st>>>(c.nb, c.mx, c.my, cc_tiles_x(c.mx), cc_tiles_y(c.my),
-                                                               c.Px_part, c.Py_part, c.Px, c.Py);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = mgc_launch(k_reduce_partials<C>, dim3((8 * tot + 255) / 256), dim3(256), 0, st, c.nb, c.mx, c.my,
+                             cc_tiles_x(c.mx), cc_tiles_y(c.my), c.Px_part, c.Py_part, c.Px, c.Py);
   if (e != cudaSuccess) return e;
-  k_cc_coef<<<c.nb * c.nb, 256, 0, st>>>(c.nb, c.my, c.wvphi64, c.Px, c.c);
-  return cudaGetLastError();
+  return mgc_launch(k_cc_coef, dim3(c.nb * c.nb), dim3(256), 0, st, c.nb, c.my, c.wvphi64, c.Px, c.c);
 }
 
 // Clusters of more than 8 CTAs must be allowed per kernel (once, before any launch or
@@ -350,14 +351,14 @@ cudaError_t launch_channel_solve(const CRSystem& A, const CRSystem& B, cudaStrea
   const int mm = A.m > B.m ? A.m : B.m;
   const size_t smem = 2 * (size_t)cr_rows(mm) * A.nb * sizeof(cplx);
   switch (A.nb) {
-    case 1: k_channel_solve_pcr<1><<<2 * CR_CLUSTER, CR_THREADS, smem, st>>>(A, B); break;
-    case 2: k_channel_solve_pcr<2><<<2 * CR_CLUSTER, CR_THREADS, smem, st>>>(A, B); break;
-    case 3: k_channel_solve_pcr<3><<<2 * CR_CLUSTER, CR_THREADS, smem, st>>>(A, B); break;
-    case 4: k_channel_solve_pcr<4><<<2 * CR_CLUSTER, CR_THREADS, smem, st>>>(A, B); break;
-    case 5: k_channel_solve_pcr<5><<<2 * CR_CLUSTER, CR_THREADS, smem, st>>>(A, B); break;
-    case 6: k_channel_solve_pcr<6><<<2 * CR_CLUSTER, CR_THREADS, smem, st>>>(A, B); break;
-    case 7: k_channel_solve_pcr<7><<<2 * CR_CLUSTER, CR_THREADS, smem, st>>>(A, B); break;
-    case 8: k_channel_solve_pcr<8><<<2 * CR_CLUSTER, CR_THREADS, smem, st>>>(A, B); break;
+    case 1: return mgc_launch(k_channel_solve_pcr<1>, dim3(2 * CR_CLUSTER), dim3(CR_THREADS), smem, st, A, B);
+    case 2: return mgc_launch(k_channel_solve_pcr<2>, dim3(2 * CR_CLUSTER), dim3(CR_THREADS), smem, st, A, B);
+    case 3: return mgc_launch(k_channel_solve_pcr<3>, dim3(2 * CR_CLUSTER), dim3(CR_THREADS), smem, st, A, B);
+    case 4: return mgc_launch(k_channel_solve_pcr<4>, dim3(2 * CR_CLUSTER), dim3(CR_THREADS), smem, st, A, B);
+    case 5: return mgc_launch(k_channel_solve_pcr<5>, dim3(2 * CR_CLUSTER), dim3(CR_THREADS), smem, st, A, B);
+    case 6: return mgc_launch(k_channel_solve_pcr<6>, dim3(2 * CR_CLUSTER), dim3(CR_THREADS), smem, st, A, B);
+    case 7: return mgc_launch(k_channel_solve_pcr<7>, dim3(2 * CR_CLUSTER), dim3(CR_THREADS), smem, st, A, B);
+    case 8: return mgc_launch(k_channel_solve_pcr<8>, dim3(2 * CR_CLUSTER), dim3(CR_THREADS), smem, st, A, B);
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

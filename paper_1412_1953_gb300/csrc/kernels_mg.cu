@@ -9,7 +9,26 @@
 // bound by HBM).  The one-step kernels compute each output once; the fused level passes
 // further down recompute a one-node halo of their tiles instead of a launch.  The uniform
 // parts of each axis use a single neighbour coefficient.
+#include <atomic>
+
 #include "common.cuh"
+
+thread_local cudaStream_t g_mgc_last_kernel_stream = nullptr;
+thread_local bool g_mgc_last_was_kernel = false;
+
+int mgc_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  int n = cache[dev].load(std::memory_order_relaxed);
+  if (n > 0) return n;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    return 152;
+  }
+  cache[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
 
 namespace {
 
@@ -100,24 +119,10 @@ __device__ __forceinline__ C coarse_at(const C* __restrict__ ec, int mcx, int mc
                                                        : CT<C>::make(0.0, 0.0);
 }
 
-// Row `row` of the coarsest solve u = A_c^{-1} f by one warp (FP64 inverse, FP64 sums).
-template <class C>
-__device__ __forceinline__ void coarse_row(int nc, const cplx* __restrict__ Ainv, const C* __restrict__ f,
-                                           C* __restrict__ u, int row, int lane) {
-  cplx acc = cmk(0.0, 0.0);
-  const cplx* a = Ainv + (size_t)row * nc;
-  for (int c = lane; c < nc; c += 32) acc = cfma(__ldg(a + c), to_c128(__ldg(f + c)), acc);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
-    acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
-  }
-  if (lane == 0) u[row] = CT<C>::make(acc.x, acc.y);
-}
-
 template <class C>
 __global__ void __launch_bounds__(BX * BY) k_jacobi(StencilViewT<C> s, const C* __restrict__ u_in,
                                                     C* __restrict__ u_out, const C* __restrict__ f) {
+  mgc_pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= s.mx || j >= s.my) return;
@@ -130,6 +135,7 @@ __global__ void __launch_bounds__(BX * BY) k_jacobi(StencilViewT<C> s, const C* 
 template <class C>
 __global__ void __launch_bounds__(256) k_jacobi_zero(long long n, const C* __restrict__ Dinv, C* __restrict__ u_out,
                                                     const C* __restrict__ f) {
+  mgc_pdl_enter();
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p < n) u_out[p] = cmul(__ldg(Dinv + p), __ldg(f + p));
 }
@@ -140,18 +146,25 @@ __global__ void __launch_bounds__(256) k_jacobi_zero(long long n, const C* __res
 template <class C>
 __global__ void __launch_bounds__(256) k_scale_jacobi_zero(long long n, C* w, const double* __restrict__ norm2,
                                                           const C* __restrict__ Dinv, C* __restrict__ u_out) {
+  mgc_pdl_enter();
   __shared__ double sb;
+  // the node's loads are issued before the barrier, so they overlap thread 0's square root
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  C wv = CT<C>::make(0.0, 0.0), dv = wv;
+  if (p < n) {
+    wv = w[p];
+    dv = __ldg(Dinv + p);
+  }
   if (threadIdx.x == 0) {
     const double b = sqrt(*norm2);
     sb = b > 0.0 ? 1.0 / b : 0.0;
   }
   __syncthreads();
   const typename CT<C>::R sc = (typename CT<C>::R)sb;
-  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p < n) {
-    const C v = cscal(sc, w[p]);
+    const C v = cscal(sc, wv);
     w[p] = v;
-    u_out[p] = cmul(__ldg(Dinv + p), v);
+    u_out[p] = cmul(dv, v);
   }
 }
 
@@ -192,6 +205,7 @@ template <class C>
 __global__ void __launch_bounds__(BX * BY) k_residual(StencilViewT<C> s, const C* __restrict__ u,
                                                       const C* __restrict__ f, C* __restrict__ r,
                                                       double* __restrict__ norm_part) {
+  mgc_pdl_enter();
   __shared__ double sh[BX * BY / 32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -213,6 +227,7 @@ __global__ void __launch_bounds__(BX * BY) k_residual(StencilViewT<C> s, const C
 template <class C>
 __global__ void __launch_bounds__(256) k_restrict(int mx, int mcx, int mcy, const C* __restrict__ r,
                                                   C* __restrict__ rc) {
+  mgc_pdl_enter();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= mcx || J >= mcy) return;
@@ -245,6 +260,7 @@ __device__ __forceinline__ void prolong_cell(int mx, int my, int mcx, int mcy, c
 template <class C>
 __global__ void __launch_bounds__(BX * BY) k_prolong_add(int mx, int my, int mcx, int mcy, const C* __restrict__ ec,
                                                          C* __restrict__ u) {
+  mgc_pdl_enter();
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   const int L = blockIdx.y * blockDim.y + threadIdx.y;
   if (K > mcx || L > mcy) return;
@@ -262,6 +278,7 @@ template <class C>
 __global__ void __launch_bounds__(BX * BY) k_prolong_jacobi(StencilViewT<C> s, int mcx, int mcy,
                                                             const C* __restrict__ ec, const C* __restrict__ u,
                                                             C* __restrict__ o, const C* __restrict__ f) {
+  mgc_pdl_enter();
   typedef typename CT<C>::R R;
   constexpr int TW = BX + 2;
   __shared__ C T[BY + 2][TW];
@@ -318,11 +335,23 @@ __global__ void __launch_bounds__(DUW * (2 * DBY + 3)) k_zero_residual_restrict(
                                                                                 const C* __restrict__ f,
                                                                                 C* __restrict__ u,
                                                                                 C* __restrict__ fc) {
+  mgc_pdl_enter();
   __shared__ C U[2 * DBY + 3][DUW];
   __shared__ C Rt[2 * DBY + 1][DRW];
   const int cby = (blockDim.x / DUW - 3) / 2;   // coarse rows of the block
   const int I0 = blockIdx.x * DBX, J0 = blockIdx.y * cby;
   const int t = threadIdx.x;
+  const int rh = 2 * cby + 1;
+  // f and D of this thread's residual node, loaded with the tile so that the pass waits
+  // on memory once
+  const int ra = t % DRW, rb = t / DRW, ri = 2 * I0 + ra, rj = 2 * J0 + rb;
+  const bool rown = t < DRW * rh && ri < s.mx && rj < s.my;
+  const int rp = rj * s.mx + ri;
+  C rf = CT<C>::make(0.0, 0.0), rd = rf;
+  if (rown) {
+    rf = __ldg(f + rp);
+    rd = __ldg(s.D + rp);
+  }
   {
     const int a = t % DUW, b = t / DUW;
     const int i = 2 * I0 - 1 + a, j = 2 * J0 - 1 + b;
@@ -340,19 +369,14 @@ __global__ void __launch_bounds__(DUW * (2 * DBY + 3)) k_zero_residual_restrict(
     U[b][a] = v;
   }
   __syncthreads();
-  const int rh = 2 * cby + 1;
-  if (t < DRW * rh) {
-    const int a = t % DRW, b = t / DRW;
-    const int i = 2 * I0 + a, j = 2 * J0 + b;
-    if (i < s.mx && j < s.my) {
-      const int p = j * s.mx + i;
-      dispatch_kinds(s, 2 * I0, min(2 * I0 + DRW, s.mx), 2 * J0, min(2 * J0 + rh, s.my),
-                     [&](auto kx, auto ky, auto ir, auto dg) {
-                       Rt[b][a] = residual_vals<MGC_KINDS(kx, ky, ir, dg)>(
-                           s, i, j, p, U[b + 1][a + 1], U[b + 1][a], U[b + 1][a + 2], U[b][a + 1], U[b + 2][a + 1],
-                           __ldg(f + p));
-                     });
-    }
+  if (rown) {
+    const int a = ra, b = rb;
+    dispatch_kinds(s, 2 * I0, min(2 * I0 + DRW, s.mx), 2 * J0, min(2 * J0 + rh, s.my),
+                   [&](auto kx, auto ky, auto ir, auto dg) {
+                     Rt[b][a] = residual_vals_d<MGC_KINDS(kx, ky, ir, dg)>(
+                         s, ri, rj, rd, U[b + 1][a + 1], U[b + 1][a], U[b + 1][a + 2], U[b][a + 1], U[b + 2][a + 1],
+                         rf);
+                   });
   }
   __syncthreads();
   if (t < DBX * cby) {
@@ -364,14 +388,89 @@ __global__ void __launch_bounds__(DUW * (2 * DBY + 3)) k_zero_residual_restrict(
   }
 }
 
-// Coarsest level: u = A_c^{-1} f with the FP64 dense inverse built at setup; one warp
-// per row, accumulated in FP64 for either element type.
-template <class C>
-__global__ void __launch_bounds__(256) k_coarse_solve(int nc, const cplx* __restrict__ Ainv, const C* __restrict__ f,
-                                                      C* __restrict__ u) {
-  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+// Coarsest level: u = A_c^{-1} f with the FP64 dense inverse built at setup, accumulated
+// in FP64 for either element type; the FP64 pipes (2 DFMA per clock per SM) bound the
+// 4 nc^2 operations, so the rows are spread evenly over the SMs and every load of a row
+// is issued before its FMAs.  Two launch shapes:
+//  - complex128: one block per row; its CS_THREADS threads split the row's columns
+//    (thread t takes t, t + CS_THREADS, ...), f is read through L1;
+//  - complex64: CS_WARPS rows per block, one warp per row, f widened to FP64 once per
+//    block in shared memory (widening it once per row costs as much FP64 issue as the
+//    row's FMAs).
+constexpr int CS_THREADS = 128, CS_UNROLL = (MGC_MAX_COARSE + CS_THREADS - 1) / CS_THREADS;
+constexpr int CS_WARPS = 4, CS_WUNROLL = 8;
+
+__global__ void __launch_bounds__(CS_THREADS) k_coarse_solve(int nc, const cplx* __restrict__ Ainv,
+                                                              const cplx* __restrict__ f, cplx* __restrict__ u) {
+  mgc_pdl_enter();
+  __shared__ double sh[2][CS_THREADS / 32];
+  const int row = blockIdx.x, t = threadIdx.x;
+  const cplx* __restrict__ a = Ainv + (size_t)row * nc;
+  cplx av[CS_UNROLL], fv[CS_UNROLL];
+#pragma unroll
+  for (int q = 0; q < CS_UNROLL; ++q) {
+    const int c = t + q * CS_THREADS;
+    const bool ok = c < nc;
+    av[q] = ok ? __ldg(a + c) : cmk(0.0, 0.0);
+    fv[q] = ok ? __ldg(f + c) : cmk(0.0, 0.0);
+  }
+  cplx acc0 = cmk(0.0, 0.0), acc1 = cmk(0.0, 0.0);
+#pragma unroll
+  for (int q = 0; q < CS_UNROLL; q += 2) {
+    acc0 = cfma(av[q], fv[q], acc0);
+    if (q + 1 < CS_UNROLL) acc1 = cfma(av[q + 1], fv[q + 1], acc1);
+  }
+  acc0 = cadd(acc0, acc1);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc0.x += __shfl_down_sync(0xffffffffu, acc0.x, o);
+    acc0.y += __shfl_down_sync(0xffffffffu, acc0.y, o);
+  }
+  if ((t & 31) == 0) {
+    sh[0][t >> 5] = acc0.x;
+    sh[1][t >> 5] = acc0.y;
+  }
+  __syncthreads();
+  if (t == 0) {
+    cplx tot = cmk(0.0, 0.0);
+#pragma unroll
+    for (int w = 0; w < CS_THREADS / 32; ++w) tot = cadd(tot, cmk(sh[0][w], sh[1][w]));
+    u[row] = tot;
+  }
+}
+
+__global__ void __launch_bounds__(32 * CS_WARPS) k_coarse_solve_rows(int nc, const cplx* __restrict__ Ainv,
+                                                                     const float2* __restrict__ f,
+                                                                     float2* __restrict__ u) {
+  mgc_pdl_enter();
+  __shared__ cplx fs[MGC_MAX_COARSE];
+  for (int c = threadIdx.x; c < nc; c += 32 * CS_WARPS) fs[c] = to_c128(__ldg(f + c));
+  __syncthreads();
+  const int row = blockIdx.x * CS_WARPS + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (row >= nc) return;
-  coarse_row(nc, Ainv, f, u, row, threadIdx.x & 31);
+  const cplx* __restrict__ a = Ainv + (size_t)row * nc;
+  cplx acc0 = cmk(0.0, 0.0), acc1 = cmk(0.0, 0.0);
+  for (int c0 = 0; c0 < nc; c0 += 32 * CS_WUNROLL) {
+    cplx v[CS_WUNROLL];
+#pragma unroll
+    for (int q = 0; q < CS_WUNROLL; ++q) {
+      const int c = c0 + 32 * q + lane;
+      v[q] = c < nc ? __ldg(a + c) : cmk(0.0, 0.0);
+    }
+#pragma unroll
+    for (int q = 0; q < CS_WUNROLL; q += 2) {
+      const int c = c0 + 32 * q + lane;
+      if (c < nc) acc0 = cfma(v[q], fs[c], acc0);
+      if (c + 32 < nc) acc1 = cfma(v[q + 1], fs[c + 32], acc1);
+    }
+  }
+  acc0 = cadd(acc0, acc1);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc0.x += __shfl_down_sync(0xffffffffu, acc0.x, o);
+    acc0.y += __shfl_down_sync(0xffffffffu, acc0.y, o);
+  }
+  if (lane == 0) u[row] = make_float2((float)acc0.x, (float)acc0.y);
 }
 
 
@@ -379,6 +478,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int nc, const cplx* __rest
 // `gate` is given and *gate == 0.
 __global__ void __launch_bounds__(256) k_sum_partials(const double* __restrict__ part, int n,
                                                       double* __restrict__ out, const int* __restrict__ gate) {
+  mgc_pdl_enter();
   __shared__ double sh[8];
   if (gate && *gate == 0) return;
   double v = 0.0;
@@ -389,6 +489,7 @@ __global__ void __launch_bounds__(256) k_sum_partials(const double* __restrict__
 
 template <class C>
 __global__ void __launch_bounds__(256) k_norm2(const C* __restrict__ v, long long n, double* __restrict__ part) {
+  mgc_pdl_enter();
   __shared__ double sh[8];
   typename CT<C>::R acc = 0;
   for (long long p = blockIdx.x * 256LL + threadIdx.x; p < n; p += (long long)gridDim.x * 256)
@@ -400,6 +501,7 @@ __global__ void __launch_bounds__(256) k_norm2(const C* __restrict__ v, long lon
 template <class C>
 __global__ void __launch_bounds__(BX * BY) k_apply(StencilViewT<C> s, const C* __restrict__ x, C* __restrict__ y,
                                                    double* __restrict__ norm_part) {
+  mgc_pdl_enter();
   __shared__ double sh[BX * BY / 32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -421,6 +523,7 @@ __global__ void __launch_bounds__(BX * BY) k_apply(StencilViewT<C> s, const C* _
 // y32 = (x64 * scale) rounded to complex64, scale = 1/sqrt(*norm2) (1 when norm2 is null).
 __global__ void __launch_bounds__(256) k_demote(long long n, const cplx* __restrict__ x, const double* __restrict__ norm2,
                                                 float2* __restrict__ y) {
+  mgc_pdl_enter();
   __shared__ double s_sh;
   if (threadIdx.x == 0) s_sh = norm2 ? (*norm2 > 0.0 ? 1.0 / sqrt(*norm2) : 0.0) : 1.0;
   __syncthreads();
@@ -434,6 +537,7 @@ __global__ void __launch_bounds__(256) k_demote(long long n, const cplx* __restr
 // u64 += sqrt(*norm2) * e32 (the iterative-refinement update in FP64).
 __global__ void __launch_bounds__(256) k_promote_add(long long n, const float2* __restrict__ e,
                                                      const double* __restrict__ norm2, cplx* __restrict__ u) {
+  mgc_pdl_enter();
   __shared__ double s_sh;
   if (threadIdx.x == 0) s_sh = sqrt(*norm2);
   __syncthreads();
@@ -447,6 +551,7 @@ __global__ void __launch_bounds__(256) k_promote_add(long long n, const float2* 
 
 // y64 = x32 (exact widening).
 __global__ void __launch_bounds__(256) k_promote(long long n, const float2* __restrict__ x, cplx* __restrict__ y) {
+  mgc_pdl_enter();
   for (long long p = blockIdx.x * 256LL + threadIdx.x; p < n; p += (long long)gridDim.x * 256)
     y[p] = to_c128(__ldg(x + p));
 }
@@ -461,12 +566,12 @@ inline dim3 grid2(int mx, int my) { return dim3((mx + BX - 1) / BX, (my + BY - 1
 
 // Block height for a level of mx x my nodes: 64-thread blocks below two full 256-thread
 // blocks per SM, so the work of a small level spreads over more SMs' FP64 pipes.
-inline int level_by(int mx, int my) { return (long long)mx * my < 2LL * 152 * BX * BY ? 2 : BY; }
+inline int level_by(int mx, int my) { return (long long)mx * my < 2LL * mgc_sm_count() * BX * BY ? 2 : BY; }
 inline dim3 level_grid(int mx, int my, int by) { return dim3((mx + BX - 1) / BX, (my + by - 1) / by); }
 
 inline unsigned stride_blocks(long long n) {
-  long long b = (n + 255) / 256;
-  return (unsigned)(b < 1216 ? (b < 1 ? 1 : b) : 1216);
+  const long long b = (n + 255) / 256, cap = 8LL * mgc_sm_count();
+  return (unsigned)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
 }  // namespace
@@ -474,23 +579,21 @@ inline unsigned stride_blocks(long long n) {
 template <class C>
 cudaError_t launch_jacobi(const StencilViewT<C>& s, const C* u_in, C* u_out, const C* f, cudaStream_t st) {
   const int by = level_by(s.mx, s.my);
-  k_jacobi<C><<<level_grid(s.mx, s.my, by), dim3(BX, by), 0, st>>>(s, u_in, u_out, f);
-  return cudaGetLastError();
+  return mgc_launch(k_jacobi<C>, level_grid(s.mx, s.my, by), dim3(BX, by), 0, st, s, u_in, u_out, f);
 }
 
 template <class C>
 cudaError_t launch_jacobi_zero(const StencilViewT<C>& s, C* u_out, const C* f, cudaStream_t st) {
   long long n = (long long)s.mx * s.my;
-  k_jacobi_zero<C><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, s.Dinv, u_out, f);
-  return cudaGetLastError();
+  return mgc_launch(k_jacobi_zero<C>, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, n, s.Dinv, u_out, f);
 }
 
 template <class C>
 cudaError_t launch_scale_jacobi_zero(const StencilViewT<C>& s, C* w, const double* norm2, C* u_out,
                                      cudaStream_t st) {
   long long n = (long long)s.mx * s.my;
-  k_scale_jacobi_zero<C><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, w, norm2, s.Dinv, u_out);
-  return cudaGetLastError();
+  return mgc_launch(k_scale_jacobi_zero<C>, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, n, w, norm2, s.Dinv,
+                    u_out);
 }
 
 template <class C>
@@ -503,16 +606,14 @@ template <class C>
 cudaError_t launch_residual(const StencilViewT<C>& s, const C* u, const C* f, C* r, double* norm_part,
                             cudaStream_t st) {
   const int by = norm_part ? BY : level_by(s.mx, s.my);   // norm partials: one per full block
-  k_residual<C><<<level_grid(s.mx, s.my, by), dim3(BX, by), 0, st>>>(s, u, f, r, norm_part);
-  return cudaGetLastError();
+  return mgc_launch(k_residual<C>, level_grid(s.mx, s.my, by), dim3(BX, by), 0, st, s, u, f, r, norm_part);
 }
 
 template <class C>
 cudaError_t launch_restrict(int mx, int my, const C* r, C* rc, cudaStream_t st) {
   int mcx = (mx - 1) / 2, mcy = (my - 1) / 2;
   const int by = level_by(mcx, mcy);
-  k_restrict<C><<<level_grid(mcx, mcy, by), dim3(BX, by), 0, st>>>(mx, mcx, mcy, r, rc);
-  return cudaGetLastError();
+  return mgc_launch(k_restrict<C>, level_grid(mcx, mcy, by), dim3(BX, by), 0, st, mx, mcx, mcy, r, rc);
 }
 
 template <class C>
@@ -521,8 +622,7 @@ cudaError_t launch_prolong_jacobi(const StencilViewT<C>& s, const C* ec, const C
   const int mcx = (s.mx - 1) / 2, mcy = (s.my - 1) / 2;
   if (s.mx != 2 * mcx + 1 || s.my != 2 * mcy + 1) return cudaErrorInvalidValue;
   const int by = level_by(s.mx, s.my);
-  k_prolong_jacobi<C><<<level_grid(s.mx, s.my, by), dim3(BX, by), 0, st>>>(s, mcx, mcy, ec, u, o, f);
-  return cudaGetLastError();
+  return mgc_launch(k_prolong_jacobi<C>, level_grid(s.mx, s.my, by), dim3(BX, by), 0, st, s, mcx, mcy, ec, u, o, f);
 }
 
 template <class C>
@@ -530,13 +630,11 @@ cudaError_t launch_zero_residual_restrict(const StencilViewT<C>& s, const C* f, 
                                           cudaStream_t st) {
   const int mcx = (s.mx - 1) / 2, mcy = (s.my - 1) / 2;
   if (s.mx != 2 * mcx + 1 || s.my != 2 * mcy + 1) return cudaErrorInvalidValue;
-  const int cby = (long long)mcx * mcy < 2LL * 152 * DBX * DBY ? 2 : DBY;
+  const int cby = (long long)mcx * mcy < 2LL * mgc_sm_count() * DBX * DBY ? 2 : DBY;
   const dim3 grid((mcx + DBX - 1) / DBX, (mcy + cby - 1) / cby);
-  if (zero)
-    k_zero_residual_restrict<true, C><<<grid, DUW * (2 * cby + 3), 0, st>>>(s, mcx, mcy, f, u, fc);
-  else
-    k_zero_residual_restrict<false, C><<<grid, DUW * (2 * cby + 3), 0, st>>>(s, mcx, mcy, f, u, fc);
-  return cudaGetLastError();
+  const dim3 block(DUW * (2 * cby + 3));
+  if (zero) return mgc_launch(k_zero_residual_restrict<true, C>, grid, block, 0, st, s, mcx, mcy, f, u, fc);
+  return mgc_launch(k_zero_residual_restrict<false, C>, grid, block, 0, st, s, mcx, mcy, f, u, fc);
 }
 
 template <class C>
@@ -544,28 +642,30 @@ cudaError_t launch_prolong_add(int mx, int my, const C* ec, C* u, cudaStream_t s
   int mcx = (mx - 1) / 2, mcy = (my - 1) / 2;
   if (mx != 2 * mcx + 1 || my != 2 * mcy + 1) return cudaErrorInvalidValue;   // coarse = every other fine node
   const int by = level_by(mcx + 1, mcy + 1);
-  k_prolong_add<C><<<dim3((mcx + BX) / BX, (mcy + by) / by), dim3(BX, by), 0, st>>>(mx, my, mcx, mcy, ec, u);
-  return cudaGetLastError();
+  return mgc_launch(k_prolong_add<C>, dim3((mcx + BX) / BX, (mcy + by) / by), dim3(BX, by), 0, st, mx, my, mcx, mcy,
+                    ec, u);
 }
 
 template <class C>
 cudaError_t launch_coarse_solve(int nc, const cplx* Ainv, const C* f, C* u, cudaStream_t st) {
-  k_coarse_solve<C><<<(nc + 7) / 8, 256, 0, st>>>(nc, Ainv, f, u);
-  return cudaGetLastError();
+  if (nc < 1 || nc > MGC_MAX_COARSE) return cudaErrorInvalidValue;
+  if constexpr (sizeof(C) == sizeof(float2))
+    return mgc_launch(k_coarse_solve_rows, dim3((nc + CS_WARPS - 1) / CS_WARPS), dim3(32 * CS_WARPS), 0, st, nc, Ainv,
+                      f, u);
+  else
+    return mgc_launch(k_coarse_solve, dim3(nc), dim3(CS_THREADS), 0, st, nc, Ainv, f, u);
 }
 
 
 template <class C>
 cudaError_t launch_apply(const StencilViewT<C>& s, const C* x, C* y, cudaStream_t st, double* norm_part) {
   const int by = norm_part ? BY : level_by(s.mx, s.my);
-  k_apply<C><<<level_grid(s.mx, s.my, by), dim3(BX, by), 0, st>>>(s, x, y, norm_part);
-  return cudaGetLastError();
+  return mgc_launch(k_apply<C>, level_grid(s.mx, s.my, by), dim3(BX, by), 0, st, s, x, y, norm_part);
 }
 
 template <class C>
 cudaError_t launch_norm2(const C* v, long long n, double* part, int nblocks, cudaStream_t st) {
-  k_norm2<C><<<nblocks, 256, 0, st>>>(v, n, part);
-  return cudaGetLastError();
+  return mgc_launch(k_norm2<C>, dim3(nblocks), dim3(256), 0, st, v, n, part);
 }
 
 #define MGC_INSTANTIATE(C)                                                                                  \
@@ -590,28 +690,24 @@ MGC_INSTANTIATE(float2)
 #undef MGC_INSTANTIATE
 
 cudaError_t launch_sum_partials(const double* part, int n, double* out, cudaStream_t st, const int* gate) {
-  k_sum_partials<<<1, 256, 0, st>>>(part, n, out, gate);
-  return cudaGetLastError();
+  return mgc_launch(k_sum_partials, dim3(1), dim3(256), 0, st, part, n, out, gate);
 }
 
 int norm2_blocks(long long n) {
-  long long b = (n + 255) / 256;
-  return (int)(b < 1216 ? (b < 1 ? 1 : b) : 1216);
+  const long long b = (n + 255) / 256, cap = 8LL * mgc_sm_count();
+  return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
 cudaError_t launch_demote(long long n, const cplx* x, const double* norm2, float2* y, cudaStream_t st) {
-  k_demote<<<stride_blocks(n), 256, 0, st>>>(n, x, norm2, y);
-  return cudaGetLastError();
+  return mgc_launch(k_demote, dim3(stride_blocks(n)), dim3(256), 0, st, n, x, norm2, y);
 }
 
 cudaError_t launch_promote_add(long long n, const float2* e, const double* norm2, cplx* u, cudaStream_t st) {
-  k_promote_add<<<stride_blocks(n), 256, 0, st>>>(n, e, norm2, u);
-  return cudaGetLastError();
+  return mgc_launch(k_promote_add, dim3(stride_blocks(n)), dim3(256), 0, st, n, e, norm2, u);
 }
 
 cudaError_t launch_promote(long long n, const float2* x, cplx* y, cudaStream_t st) {
-  k_promote<<<stride_blocks(n), 256, 0, st>>>(n, x, y);
-  return cudaGetLastError();
+  return mgc_launch(k_promote, dim3(stride_blocks(n)), dim3(256), 0, st, n, x, y);
 }
 
 cudaError_t launch_round_copy(long long n, const cplx* a, float2* b, cudaStream_t st) {

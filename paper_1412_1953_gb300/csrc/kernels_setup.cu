@@ -665,13 +665,13 @@ cudaError_t launch_coarse_inverse(const StencilView& s, cplx* aug, cplx* Ainv, i
   const int nc = s.mx * s.my;
   cplx* fac = aug + (size_t)nc * 2 * nc;
   const long long total = 2LL * nc * nc;
-  const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 8);
+  const int grid = (int)std::min<long long>((total + 255) / 256, 8LL * mgc_sm_count());
   k_gj_assemble<<<grid, 256, 0, st>>>(s, aug);
   cudaError_t e = cudaGetLastError();
   for (int k = 0; k < nc && e == cudaSuccess; ++k) {
     k_gj_pivot<<<1, 1024, 0, st>>>(nc, aug, fac, k, status);
     const long long work = (long long)nc * (2LL * nc - k - 1);
-    const int g = (int)std::max<long long>(1, std::min<long long>((work + 255) / 256, 152LL * 8));
+    const int g = (int)std::max<long long>(1, std::min<long long>((work + 255) / 256, 8LL * mgc_sm_count()));
     k_gj_eliminate<<<g, 256, 0, st>>>(nc, aug, fac, k, status);
     e = cudaGetLastError();
   }

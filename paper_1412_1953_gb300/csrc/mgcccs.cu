@@ -65,6 +65,8 @@ struct mgcccs_handle {
   // GMRES(m) outer solver
   int km;
   int kr_nblk;
+  long long kld;            // pitch of the Krylov basis vectors: N rounded up to 32 entries, so
+                            // every vector starts 256-byte aligned and complex64 pairs load as 16 bytes
   cplx *V, *Z, *Hh, *cs, *sn, *g, *y, *hc, *dotpart;
   int* gate;
   cudaStream_t cap_st;                       // capture stream for the step graphs
@@ -242,17 +244,20 @@ void layout(mgcccs_handle* h, Carver& cv) {
   h->norm_nparts = nparts > n2b ? nparts : n2b;
   const long long N = (long long)mx * my;
   h->km = p.krylov_restart;
-  h->kr_nblk = krylov_blocks(N);
+  // complex128 Krylov kernels are FP64-bound at 4 blocks per SM; the complex64 update is
+  // bound by memory latency and gets 6, which its register count allows
+  h->kr_nblk = krylov_blocks(N, p.precision == 1 ? 6 : 4);
+  h->kld = (N + 31) / 32 * 32;
   if (h->km > 0) {
     const int m = h->km;
     if (p.precision == 1) {
-      h->V32 = cv.take<float2>((size_t)(m + 1) * N);
-      h->Z32 = cv.take<float2>((size_t)m * N);
+      h->V32 = cv.take<float2>((size_t)(m + 1) * h->kld);
+      h->Z32 = cv.take<float2>((size_t)m * h->kld);
       h->e32 = cv.take<float2>((size_t)N);
       h->r64 = cv.take<cplx>((size_t)N);
     } else {
-      h->V = cv.take<cplx>((size_t)(m + 1) * N);
-      h->Z = cv.take<cplx>((size_t)m * N);
+      h->V = cv.take<cplx>((size_t)(m + 1) * h->kld);
+      h->Z = cv.take<cplx>((size_t)m * h->kld);
     }
     h->Hh = cv.take<cplx>((size_t)(m + 1) * m);
     h->cs = cv.take<cplx>(m);
@@ -309,8 +314,10 @@ AxisCoefT<float2> axis_coef32(const AxisCoefT<cplx>& a) {
     if (e_ != cudaSuccess) return MGCCCS_ECUDA;  \
   } while (0)
 
+// every runtime call other than a kernel launch ends a chain of programmatic launches
 #define MGC_CUDA(expr)                           \
   do {                                           \
+    mgc_not_a_kernel();                          \
     if ((expr) != cudaSuccess) return MGCCCS_ECUDA; \
   } while (0)
 
@@ -609,6 +616,7 @@ struct CaptureGuard {          // ends a capture on error so that the stream sta
     if (open) {
       cudaGraph_t g = nullptr;
       cudaStreamEndCapture(s, &g);
+      mgc_not_a_kernel();
     }
   }
 };
@@ -683,10 +691,11 @@ int issue_arnoldi_step(mgcccs_handle* h, int j) {
   const StencilViewT<C>& s0 = *level_io<C>(h, 0).sv;
   const long long N = (long long)s0.mx * s0.my;
   const int nb = h->kr_nblk;
+  const long long ld = h->kld;
   C* V = kv_V<C>(h);
-  C* vj = V + (size_t)j * N;
-  C* w = V + (size_t)(j + 1) * N;
-  C* zj = kv_Z<C>(h) + (size_t)j * N;
+  C* vj = V + (size_t)j * ld;
+  C* w = V + (size_t)(j + 1) * ld;
+  C* zj = kv_Z<C>(h) + (size_t)j * ld;
   cplx* col = h->Hh + (size_t)j * (m + 1);
   // v_j = w_j / |w_j| (|w_j|^2 left in norm_out[1] by step j-1; v_0 is normalised by the
   // cycle start): fused into the first pre-smoothing sweep of the preconditioner when
@@ -707,17 +716,21 @@ int issue_arnoldi_step(mgcccs_handle* h, int j) {
   // so the multi-dot over columns 0..j+1 also yields |w|^2 (for the reorthogonalisation
   // test), left in H(j+1, j) until the Givens rotation writes that entry.
   const int nbd = multidot_blocks(N, j + 2);
-  MGC_LAUNCH(launch_multidot(N, j + 2, (const C*)V, N, (const C*)w, h->dotpart, nbd, (const int*)nullptr, st));
+  MGC_LAUNCH(launch_multidot(N, j + 2, (const C*)V, ld, (const C*)w, h->dotpart, nbd, (const int*)nullptr, st));
   MGC_LAUNCH(launch_reduce_dots(nbd, j + 2, h->dotpart, col, nullptr, st));
   const double* w_norm2 = reinterpret_cast<const double*>(col + j + 1);
-  MGC_LAUNCH(launch_multiaxpy(N, j + 1, (const C*)V, N, col, -1.0, w, h->norm_part, nb, (const int*)nullptr, st));
+  MGC_LAUNCH(launch_multiaxpy(N, j + 1, (const C*)V, ld, col, -1.0, w, h->norm_part, nb, (const int*)nullptr, st));
   // second pass only when the first one cancelled |w| by more than 1e3;
-  // the corrections are added into H(0:j, j)
+  // the corrections are added into H(0:j, j).  The Givens rotation j takes h_{j+1,j} = |w|
+  // from its square; without a second pass (nearly every step) k_sum_dgks applies it, after
+  // one the pass ends with it.  w is normalised at the start of step j+1 (a cycle that
+  // stops here never uses it).
+  const GivensArgs gv{j, m, h->Hh, h->cs, h->sn, h->g, h->norm_out + 2};
   if (h->device_loop) {
     // device-driven graph: the pass is the body of a conditional node, so it costs no
     // launch when it does not run
     MGC_LAUNCH(launch_sum_dgks(h->norm_part, nb, h->norm_out + 1, w_norm2, h->gate, st, h->dgks_cond[j],
-                               &h->ctl->dgks));
+                               &h->ctl->dgks, &gv));
     cudaGraph_t* body = nullptr;
     int rc2 = add_conditional(st, h->dgks_cond[j], cudaGraphCondTypeIf, 1, &body);
     if (rc2) return rc2;
@@ -726,25 +739,24 @@ int issue_arnoldi_step(mgcccs_handle* h, int j) {
     if (rc2) return rc2;
     cudaStream_t bs = h->gst[0];
     const long long b0 = h->launches;
-    MGC_LAUNCH(launch_multidot(N, j + 1, (const C*)V, N, (const C*)w, h->dotpart, nbd, (const int*)nullptr, bs));
+    MGC_LAUNCH(launch_multidot(N, j + 1, (const C*)V, ld, (const C*)w, h->dotpart, nbd, (const int*)nullptr, bs));
     MGC_LAUNCH(launch_reduce_dots(nbd, j + 1, h->dotpart, h->hc, col, bs));
-    MGC_LAUNCH(launch_multiaxpy(N, j + 1, (const C*)V, N, h->hc, -1.0, w, h->norm_part, nb, (const int*)nullptr, bs));
+    MGC_LAUNCH(launch_multiaxpy(N, j + 1, (const C*)V, ld, h->hc, -1.0, w, h->norm_part, nb, (const int*)nullptr, bs));
     MGC_LAUNCH(launch_sum_partials(h->norm_part, nb, h->norm_out + 1, bs));
+    MGC_LAUNCH(launch_givens(j, m, h->Hh, h->cs, h->sn, h->g, h->norm_out + 2, h->norm_out + 1, bs));
     h->sg_dgks = h->launches - b0;
     h->launches = b0;
     rc2 = capture_end(cg);
     if (rc2) return rc2;
   } else {
-    MGC_LAUNCH(launch_sum_dgks(h->norm_part, nb, h->norm_out + 1, w_norm2, h->gate, st));
-    MGC_LAUNCH(launch_multidot(N, j + 1, (const C*)V, N, (const C*)w, h->dotpart, nbd, (const int*)h->gate, st));
+    MGC_LAUNCH(launch_sum_dgks(h->norm_part, nb, h->norm_out + 1, w_norm2, h->gate, st, 0, nullptr, &gv));
+    MGC_LAUNCH(launch_multidot(N, j + 1, (const C*)V, ld, (const C*)w, h->dotpart, nbd, (const int*)h->gate, st));
     MGC_LAUNCH(launch_reduce_dots(nbd, j + 1, h->dotpart, h->hc, col, st));
-    MGC_LAUNCH(launch_multiaxpy(N, j + 1, (const C*)V, N, h->hc, -1.0, w, h->norm_part, nb, (const int*)h->gate,
+    MGC_LAUNCH(launch_multiaxpy(N, j + 1, (const C*)V, ld, h->hc, -1.0, w, h->norm_part, nb, (const int*)h->gate,
                                 st));
     MGC_LAUNCH(launch_sum_partials(h->norm_part, nb, h->norm_out + 1, st, h->gate));
+    MGC_LAUNCH(launch_givens(j, m, h->Hh, h->cs, h->sn, h->g, h->norm_out + 2, h->norm_out + 1, st, h->gate));
   }
-  // Givens rotation j, taking h_{j+1,j} = |w| from its square; w is normalised at the
-  // start of step j+1 (a cycle that stops here never uses it)
-  MGC_LAUNCH(launch_givens(j, m, h->Hh, h->cs, h->sn, h->g, h->norm_out + 2, h->norm_out + 1, st));
   if (!h->device_loop)
     MGC_CUDA(cudaMemcpyAsync(h->est_host + j, h->norm_out + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
   return MGCCCS_OK;
@@ -763,6 +775,7 @@ int launch_arnoldi_step(mgcccs_handle* h, int j) {
     int rc = issue_arnoldi_step<C>(h, j);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->cap_st, &g);
+    mgc_not_a_kernel();
     h->st = orig;
     count[j] = h->launches - before;
     h->launches = before;
@@ -861,7 +874,7 @@ int gmres_impl(mgcccs_handle* h, cplx* u, const cplx* f, double fn, double rtol,
       return MGCCCS_ENONFINITE;
     }
     MGC_LAUNCH(launch_hess_solve(k, m, h->Hh, h->g, h->y, st));
-    MGC_LAUNCH(launch_multiaxpy(N, k, (const cplx*)h->Z, N, h->y, 1.0, u, (double*)nullptr, nb, (const int*)nullptr, st));
+    MGC_LAUNCH(launch_multiaxpy(N, k, (const cplx*)h->Z, h->kld, h->y, 1.0, u, (double*)nullptr, nb, (const int*)nullptr, st));
   }
   if (iters) *iters = steps;
   if (relres) *relres = rr;
@@ -923,7 +936,7 @@ int gmres_ir_impl(mgcccs_handle* h, cplx* u, const cplx* f, double fn, double rt
     }
     MGC_LAUNCH(launch_hess_solve(k, m, h->Hh, h->g, h->y, st));
     MGC_CUDA(cudaMemsetAsync(h->e32, 0, sizeof(float2) * (size_t)N, st));
-    MGC_LAUNCH(launch_multiaxpy(N, k, (const float2*)h->Z32, N, h->y, 1.0, h->e32, (double*)nullptr, nb,
+    MGC_LAUNCH(launch_multiaxpy(N, k, (const float2*)h->Z32, h->kld, h->y, 1.0, h->e32, (double*)nullptr, nb,
                                 (const int*)nullptr, st));
     MGC_LAUNCH(launch_promote_add(N, h->e32, h->norm_out, u, st));
   }
@@ -1017,11 +1030,11 @@ int batch_cycle_end(BatchItem& it) {
   MGC_LAUNCH(launch_hess_solve(it.k, h->km, h->Hh, h->g, h->y, st));
   if (h->mixed) {
     MGC_CUDA(cudaMemsetAsync(h->e32, 0, sizeof(float2) * (size_t)N, st));
-    MGC_LAUNCH(launch_multiaxpy(N, it.k, (const float2*)h->Z32, N, h->y, 1.0, h->e32, (double*)nullptr, nb,
+    MGC_LAUNCH(launch_multiaxpy(N, it.k, (const float2*)h->Z32, h->kld, h->y, 1.0, h->e32, (double*)nullptr, nb,
                                 (const int*)nullptr, st));
     MGC_LAUNCH(launch_promote_add(N, h->e32, h->norm_out, it.u, st));
   } else {
-    MGC_LAUNCH(launch_multiaxpy(N, it.k, (const cplx*)h->Z, N, h->y, 1.0, it.u, (double*)nullptr, nb,
+    MGC_LAUNCH(launch_multiaxpy(N, it.k, (const cplx*)h->Z, h->kld, h->y, 1.0, it.u, (double*)nullptr, nb,
                                 (const int*)nullptr, st));
   }
   return MGCCCS_OK;
@@ -1177,11 +1190,11 @@ int append_solve(mgcccs_handle* h, cplx* u, const cplx* f, cudaGraph_t G) {
     MGC_LAUNCH(launch_hess_solve(m, m, h->Hh, h->g, h->y, S, &h->ctl->k));
     if (h->mixed) {
       MGC_CUDA(cudaMemsetAsync(h->e32, 0, sizeof(float2) * (size_t)N, S));
-      MGC_LAUNCH(launch_multiaxpy(N, m, (const float2*)h->Z32, N, h->y, 1.0, h->e32, (double*)nullptr, nb,
+      MGC_LAUNCH(launch_multiaxpy(N, m, (const float2*)h->Z32, h->kld, h->y, 1.0, h->e32, (double*)nullptr, nb,
                                   (const int*)nullptr, S, &h->ctl->k));
       MGC_LAUNCH(launch_promote_add(N, h->e32, h->norm_out, u, S));
     } else {
-      MGC_LAUNCH(launch_multiaxpy(N, m, (const cplx*)h->Z, N, h->y, 1.0, u, (double*)nullptr, nb,
+      MGC_LAUNCH(launch_multiaxpy(N, m, (const cplx*)h->Z, h->kld, h->y, 1.0, u, (double*)nullptr, nb,
                                   (const int*)nullptr, S, &h->ctl->k));
     }
     rc = capture_end(cg);
@@ -1363,6 +1376,7 @@ size_t mgcccs_workspace_size(const mgcccs_params* p) {
 
 int mgcccs_setup(mgcccs_t* out, const mgcccs_params* p, const mgcccs_c128* v1, const mgcccs_c128* v2,
                  const mgcccs_c128* v12, void* workspace, size_t workspace_bytes, void* stream) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!out || !valid_params(p) || !v1 || !v2 || !v12 || !workspace) return MGCCCS_EINVAL;
   *out = nullptr;
   size_t need = mgcccs_workspace_size(p);
@@ -1390,6 +1404,7 @@ int mgcccs_setup_with_states(mgcccs_t* out, const mgcccs_params* p, const mgcccs
                              const mgcccs_c128* v12, const mgcccs_c128* lambda, const mgcccs_c128* phi,
                              const mgcccs_c128* mu, const mgcccs_c128* vphi, void* workspace, size_t workspace_bytes,
                              void* stream) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!out || !valid_params(p) || !v1 || !v2 || !v12 || !workspace) return MGCCCS_EINVAL;
   if (p->n_b > 0 && (!lambda || !phi || !mu || !vphi)) return MGCCCS_EINVAL;
   *out = nullptr;
@@ -1417,17 +1432,20 @@ int mgcccs_setup_with_states(mgcccs_t* out, const mgcccs_params* p, const mgcccs
 }
 
 int mgcccs_vcycle(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!h || !u || !f) return MGCCCS_EINVAL;
   return vcycle_fine(h, reinterpret_cast<cplx*>(u), reinterpret_cast<const cplx*>(f), false);
 }
 
 int mgcccs_cccs(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!h || !u || !f || h->nb <= 0) return MGCCCS_EINVAL;
   return cccs_fine(h, reinterpret_cast<cplx*>(u), reinterpret_cast<const cplx*>(f));
 }
 
 int mgcccs_solve(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f, double rtol, int max_iter, int* iters,
                  double* relres, double* history) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!h || !u || !f) return MGCCCS_EINVAL;
   return solve_impl(h, reinterpret_cast<cplx*>(u), reinterpret_cast<const cplx*>(f), rtol, max_iter, iters, relres,
                     history);
@@ -1435,6 +1453,7 @@ int mgcccs_solve(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f, double rtol, 
 
 int mgcccs_solve_host(mgcccs_t h, mgcccs_c128* u_host, const mgcccs_c128* f_host, double rtol, int max_iter,
                       int* iters, double* relres) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!h || !u_host || !f_host) return MGCCCS_EINVAL;
   const size_t bytes = sizeof(cplx) * (size_t)h->lv[0].mx * h->lv[0].my;
   MGC_CUDA(cudaMemcpyAsync(h->hf, f_host, bytes, cudaMemcpyHostToDevice, h->st));
@@ -1447,6 +1466,7 @@ int mgcccs_solve_host(mgcccs_t h, mgcccs_c128* u_host, const mgcccs_c128* f_host
 }
 
 int mgcccs_precond_apply(mgcccs_t h, mgcccs_c128* z, const mgcccs_c128* r) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!h || !z || !r || (const void*)z == (const void*)r) return MGCCCS_EINVAL;
   if (!h->mixed) return precond(h, reinterpret_cast<cplx*>(z), reinterpret_cast<const cplx*>(r));
   // mixed handle: the complex64 preconditioner between a rounding and a widening
@@ -1459,18 +1479,21 @@ int mgcccs_precond_apply(mgcccs_t h, mgcccs_c128* z, const mgcccs_c128* r) {
 }
 
 int mgcccs_matvec(mgcccs_t h, const mgcccs_c128* x, mgcccs_c128* y) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!h || !x || !y || (const void*)x == (const void*)y) return MGCCCS_EINVAL;
   MGC_LAUNCH(launch_apply(h->lv[0].sv, reinterpret_cast<const cplx*>(x), reinterpret_cast<cplx*>(y), h->st));
   return MGCCCS_OK;
 }
 
 int mgcccs_residual(mgcccs_t h, const mgcccs_c128* u, const mgcccs_c128* f, mgcccs_c128* r, double* norm2) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!h || !u || !f || !r || (const void*)r == (const void*)u) return MGCCCS_EINVAL;
   return residual_norm2(h, reinterpret_cast<const cplx*>(u), reinterpret_cast<const cplx*>(f),
                         reinterpret_cast<cplx*>(r), norm2);
 }
 
 int mgcccs_smooth(mgcccs_t h, int level, mgcccs_c128* u, const mgcccs_c128* f, int sweeps) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!h || !u || !f || level < 0 || level >= h->L || sweeps < 0) return MGCCCS_EINVAL;
   LevelBufs& b = h->lv[level];
   cplx* uu = reinterpret_cast<cplx*>(u);
@@ -1486,6 +1509,7 @@ int mgcccs_smooth(mgcccs_t h, int level, mgcccs_c128* u, const mgcccs_c128* f, i
 }
 
 int mgcccs_level_residual(mgcccs_t h, int level, const mgcccs_c128* u, const mgcccs_c128* f, mgcccs_c128* r) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!h || !u || !f || !r || level < 0 || level >= h->L) return MGCCCS_EINVAL;
   MGC_LAUNCH(launch_residual(h->lv[level].sv, reinterpret_cast<const cplx*>(u), reinterpret_cast<const cplx*>(f),
                              reinterpret_cast<cplx*>(r), nullptr, h->st));
@@ -1493,6 +1517,7 @@ int mgcccs_level_residual(mgcccs_t h, int level, const mgcccs_c128* u, const mgc
 }
 
 int mgcccs_restrict(mgcccs_t h, int level, const mgcccs_c128* r, mgcccs_c128* rc) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!h || !r || !rc || level < 0 || level + 1 >= h->L) return MGCCCS_EINVAL;
   MGC_LAUNCH(launch_restrict(h->lv[level].mx, h->lv[level].my, reinterpret_cast<const cplx*>(r),
                              reinterpret_cast<cplx*>(rc), h->st));
@@ -1500,6 +1525,7 @@ int mgcccs_restrict(mgcccs_t h, int level, const mgcccs_c128* r, mgcccs_c128* rc
 }
 
 int mgcccs_prolong_add(mgcccs_t h, int level, const mgcccs_c128* ec, mgcccs_c128* u) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!h || !ec || !u || level < 0 || level + 1 >= h->L) return MGCCCS_EINVAL;
   MGC_LAUNCH(launch_prolong_add(h->lv[level].mx, h->lv[level].my, reinterpret_cast<const cplx*>(ec),
                                 reinterpret_cast<cplx*>(u), h->st));
@@ -1507,9 +1533,35 @@ int mgcccs_prolong_add(mgcccs_t h, int level, const mgcccs_c128* ec, mgcccs_c128
 }
 
 int mgcccs_coarse_solve(mgcccs_t h, const mgcccs_c128* f, mgcccs_c128* u) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!h || !f || !u) return MGCCCS_EINVAL;
   MGC_LAUNCH(launch_coarse_solve(h->nc, h->Ainv, reinterpret_cast<const cplx*>(f), reinterpret_cast<cplx*>(u),
                                  h->st));
+  return MGCCCS_OK;
+}
+
+int mgcccs_gs_dots(mgcccs_t h, const mgcccs_c128* V, long long ld, int k, const mgcccs_c128* w,
+                   mgcccs_c128* out) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
+  if (!h || !V || !w || !out || h->km < 1 || k < 1 || k > h->km + 1) return MGCCCS_EINVAL;
+  const long long N = (long long)h->lv[0].mx * h->lv[0].my;
+  if (ld < N) return MGCCCS_EINVAL;
+  const int nbd = multidot_blocks(N, k);
+  MGC_LAUNCH(launch_multidot(N, k, reinterpret_cast<const cplx*>(V), ld, reinterpret_cast<const cplx*>(w),
+                             h->dotpart, nbd, (const int*)nullptr, h->st));
+  MGC_LAUNCH(launch_reduce_dots(nbd, k, h->dotpart, reinterpret_cast<cplx*>(out), nullptr, h->st));
+  return MGCCCS_OK;
+}
+
+int mgcccs_gs_update(mgcccs_t h, const mgcccs_c128* V, long long ld, int k, const mgcccs_c128* coef,
+                     mgcccs_c128* w) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
+  if (!h || !V || !coef || !w || k < 1 || k > MGC_MAX_RESTART + 1) return MGCCCS_EINVAL;
+  const long long N = (long long)h->lv[0].mx * h->lv[0].my;
+  if (ld < N) return MGCCCS_EINVAL;
+  MGC_LAUNCH(launch_multiaxpy(N, k, reinterpret_cast<const cplx*>(V), ld, reinterpret_cast<const cplx*>(coef),
+                              -1.0, reinterpret_cast<cplx*>(w), (double*)nullptr, h->kr_nblk, (const int*)nullptr,
+                              h->st));
   return MGCCCS_OK;
 }
 
@@ -1530,6 +1582,7 @@ int mgcccs_get_bound_states(mgcccs_t h, mgcccs_c128* lambda, mgcccs_c128* phi, m
 
 int mgcccs_weighted_dot(mgcccs_t h, const mgcccs_c128* a, const mgcccs_c128* b, const mgcccs_c128* d,
                         mgcccs_c128 scale, mgcccs_c128* out) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!h || !a || !b || !out) return MGCCCS_EINVAL;
   const LevelBufs& l0 = h->lv[0];
   MGC_LAUNCH(launch_weighted_dot(l0.mx, l0.my, l0.w_x, l0.w_y, reinterpret_cast<const cplx*>(a),
@@ -1541,6 +1594,7 @@ int mgcccs_weighted_dot(mgcccs_t h, const mgcccs_c128* a, const mgcccs_c128* b, 
 
 int mgcccs_weighted_product(mgcccs_t h, const mgcccs_c128* a, const mgcccs_c128* b, mgcccs_c128 scale,
                             mgcccs_c128* out) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!h || !a || !b || !out) return MGCCCS_EINVAL;
   const LevelBufs& l0 = h->lv[0];
   MGC_LAUNCH(launch_weighted_product(l0.mx, l0.my, l0.w_x, l0.w_y, reinterpret_cast<const cplx*>(a),
@@ -1551,6 +1605,7 @@ int mgcccs_weighted_product(mgcccs_t h, const mgcccs_c128* a, const mgcccs_c128*
 
 int mgcccs_batch_solve(mgcccs_t* handles, int count, mgcccs_c128* const* u, const mgcccs_c128* const* f,
                        double rtol, int max_iter, int* iters, double* relres, int* status) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!handles || count < 1 || !u || !f || max_iter < 1 || !(rtol >= 0.0)) return MGCCCS_EINVAL;
   std::vector<BatchItem> items(count);
   for (int k = 0; k < count; ++k) {
@@ -1633,6 +1688,7 @@ struct mgcccs_batch {
 
 int mgcccs_batch_create(mgcccs_batch_t* out, mgcccs_t* handles, int count, mgcccs_c128* const* u,
                         const mgcccs_c128* const* f, void* stream) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!out || !handles || count < 1 || !u || !f) return MGCCCS_EINVAL;
   *out = nullptr;
   std::vector<mgcccs_handle*> hs(count);
@@ -1662,11 +1718,13 @@ int mgcccs_batch_create(mgcccs_batch_t* out, mgcccs_t* handles, int count, mgccc
 }
 
 int mgcccs_batch_run(mgcccs_batch_t b, double rtol, int max_iter, int* iters, double* relres, int* status) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!b || max_iter < 1 || !(rtol >= 0.0)) return MGCCCS_EINVAL;
   for (mgcccs_handle* h : b->hs) {
     int rc = stage_ctl(h, rtol, max_iter, b->st);
     if (rc) return rc;
   }
+  mgc_not_a_kernel();
   if (cudaGraphLaunch(b->exec, b->st) != cudaSuccess) return MGCCCS_ECUDA;
   for (mgcccs_handle* h : b->hs) {
     int rc = fetch_ctl(h, b->st);

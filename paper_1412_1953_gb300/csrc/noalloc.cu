@@ -82,7 +82,7 @@ int partials_address(double** out) {
 }  // namespace
 
 extern "C" int mgcccs_norm2_noalloc(const mgcccs_c128* v, size_t n, double* norm2, void* stream) {
-  if (!v || !norm2) return MGCCCS_EINVAL;
+  if (!norm2 || (!v && n)) return MGCCCS_EINVAL;   // an empty vector may come as NULL
   if (n > (size_t)MGCCCS_NOALLOC_MAX_N) return MGCCCS_EINVAL;
   double* part = nullptr;
   int rc = partials_address(&part);

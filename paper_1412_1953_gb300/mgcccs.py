@@ -80,6 +80,8 @@ _SIGS = {
     "mgcccs_prolong_add": (_i, [_vp, _i, _vp, _vp]),
     "mgcccs_coarse_solve": (_i, [_vp, _vp, _vp]),
     "mgcccs_get_bound_states": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "mgcccs_gs_dots": (_i, [_vp, _vp, ctypes.c_longlong, _i, _vp, _vp]),
+    "mgcccs_gs_update": (_i, [_vp, _vp, ctypes.c_longlong, _i, _vp, _vp]),
     "mgcccs_launch_count": (ctypes.c_longlong, [_vp]),
     "mgcccs_norm2_noalloc": (_i, [_vp, ctypes.c_size_t, _vp, _vp]),
     "mgcccs_strerror": (ctypes.c_char_p, [_i]),
@@ -131,9 +133,13 @@ def mgcccs_norm2_noalloc(v, out, stream=None):
         raise TypeError("v must be a contiguous complex128 CUDA tensor")
     if out.dtype != torch.float64 or not out.is_cuda or out.numel() < 1:
         raise TypeError("out must be a float64 CUDA tensor")
-    st = stream if stream is not None else torch.cuda.current_stream(v.device)
-    _check(lib().mgcccs_norm2_noalloc(v.data_ptr(), v.numel(), out.data_ptr(), st.cuda_stream),
-           "mgcccs_norm2_noalloc")
+    if out.device != v.device:
+        raise TypeError("out must be on the device of v")
+    # the scratch address is looked up for the current device: make it v's
+    with torch.cuda.device(v.device):
+        st = stream if stream is not None else torch.cuda.current_stream(v.device)
+        _check(lib().mgcccs_norm2_noalloc(v.data_ptr(), v.numel(), out.data_ptr(), st.cuda_stream),
+               "mgcccs_norm2_noalloc")
 
 
 def make_params(nx, ny, Lx, Ly, R0x, R0y, theta, E, levels=5, nu1=1, nu2=1, omega=2.0 / 3.0, n_b=3,
@@ -288,6 +294,27 @@ class Solver:
         sc = mgcccs_c128(complex(scale).real, complex(scale).imag)
         _check(lib().mgcccs_weighted_product(self.h, self._f(a, "a"), self._f(b, "b"), sc, self._f(out, "out")),
                "mgcccs_weighted_product")
+
+    # -- Gram-Schmidt halves of an Arnoldi step (fine-level vectors)
+    def _basis(self, V, k):
+        import torch
+        if not isinstance(V, torch.Tensor) or V.dtype != torch.complex128 or not V.is_cuda:
+            raise TypeError("V must be a complex128 CUDA tensor")
+        if V.dim() != 2 or V.shape[0] < k or V.shape[1] < self.n or V.stride(1) != 1:
+            raise ValueError(f"V must be a (>= {k}, >= {self.n}) complex128 tensor with unit column stride")
+        return V.data_ptr(), V.stride(0)
+
+    def gs_dots(self, V, k, w, out):
+        """out[i] = sum_p conj(V[i, p]) w[p] for i < k (out: k-element complex128 CUDA tensor)."""
+        vp, ld = self._basis(V, k)
+        _check(lib().mgcccs_gs_dots(self.h, vp, ld, int(k), self._f(w, "w"), _ptr(_dev_c128(out, k, "out"))),
+               "mgcccs_gs_dots")
+
+    def gs_update(self, V, k, coef, w):
+        """w -= sum_{i<k} coef[i] V[i] (coef: k-element complex128 CUDA tensor)."""
+        vp, ld = self._basis(V, k)
+        _check(lib().mgcccs_gs_update(self.h, vp, ld, int(k), _ptr(_dev_c128(coef, k, "coef")), self._f(w, "w")),
+               "mgcccs_gs_update")
 
     # -- single steps
     def level_size(self, level: int) -> int:

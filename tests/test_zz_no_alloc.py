@@ -1,6 +1,9 @@
-"""The allocation-free norm entry point (for callers that cannot call cudaMalloc, e.g.
-inside a graph capture in global mode or under a framework allocator with a hard cap)
-against the residual norm the solver's own entry point computes, on two calls in a row.
+"""The allocation-free norm entry point, for callers that cannot call cudaMalloc: code
+running while a CUDA graph is captured in the global mode (allocation is illegal there),
+code under a framework allocator that owns all device memory with a hard cap, and loops
+that must not take the implicit synchronisation an allocation can cause.  Its result is
+checked against the residual norm the solver's own entry point computes and against a
+host sum of the same vector, on two calls in a row, plus the empty vector.
 
 Kept in a file that pytest collects last, so a failure here stops a first-failure run
 only after every other test has run."""
@@ -35,6 +38,11 @@ def _residual_and_norm(n, seed):
     return sg, r, n2
 
 
+def _host_norm2(r):
+    a = r.cpu().numpy().ravel()
+    return float(np.sum(a.real * a.real + a.imag * a.imag))
+
+
 def test_norm2_noalloc_matches_residual_norm_on_two_calls():
     build.build()
     out = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
@@ -43,14 +51,25 @@ def test_norm2_noalloc_matches_residual_norm_on_two_calls():
     M.mgcccs_norm2_noalloc(r1, out)
     torch.cuda.synchronize()
     assert abs(out.item() - ref1) <= 1e-13 * ref1
+    assert abs(out.item() - _host_norm2(r1)) <= 1e-13 * ref1
     # second call in a row, a vector that spans many scratch slots
     sg2, r2, ref2 = _residual_and_norm(512, 2)
     out.fill_(-1.0)
     M.mgcccs_norm2_noalloc(r2, out)
     torch.cuda.synchronize()
     assert abs(out.item() - ref2) <= 1e-13 * ref2
+    assert abs(out.item() - _host_norm2(r2)) <= 1e-13 * ref2
     # sizes beyond the stated maximum are refused before any launch
     code = M.lib().mgcccs_norm2_noalloc(r2.data_ptr(), M.NOALLOC_MAX_N + 1, out.data_ptr(), None)
     assert code == M.EINVAL
     torch.cuda.synchronize()
     assert out.item() == pytest.approx(ref2, rel=1e-13)
+    # the empty vector: 0, whether it comes as a real pointer or as NULL
+    out.fill_(-1.0)
+    assert M.lib().mgcccs_norm2_noalloc(r2.data_ptr(), 0, out.data_ptr(), None) == M.OK
+    torch.cuda.synchronize()
+    assert out.item() == 0.0
+    out.fill_(-1.0)
+    M.mgcccs_norm2_noalloc(torch.empty(0, dtype=torch.complex128, device="cuda"), out)
+    torch.cuda.synchronize()
+    assert out.item() == 0.0
