@@ -261,21 +261,41 @@ k_channel_solve_pcr(CRSystem SA, CRSystem SB) {
   }
 }
 
+// u += sum_m phi_m(x) e^A_m(y) + sum_l e^B_l(x) vphi_l(y) (Eq. (30)).  A thread takes one
+// column i and CC_ROWS consecutive rows: phi_m(i) and e^B_l(i) stay in registers across its
+// rows (per node only the warp-uniform e^A_m(j), vphi_l(j) are loaded), and the loads of
+// its CC_ROWS values of u are issued together.  Same sums in the same order per node.
+constexpr int CC_ROWS = 4;
+
 template <int NB, class C>
 __global__ void __launch_bounds__(256) k_cccs_correct(int mx, int my, const C* __restrict__ phi,
                                                       const C* __restrict__ vphi, const C* __restrict__ eA,
                                                       const C* __restrict__ eB, C* __restrict__ u) {
   mgc_pdl_enter();
   const int i = blockIdx.x * 32 + threadIdx.x;
-  const int j = blockIdx.y * 8 + threadIdx.y;
-  if (i >= mx || j >= my) return;
-  const int p = j * mx + i;
-  C v = u[p];
+  const int j0 = (blockIdx.y * 8 + threadIdx.y) * CC_ROWS;
+  if (i >= mx || j0 >= my) return;
+  C a[NB], b[NB];
 #pragma unroll
-  for (int m = 0; m < NB; ++m) v = cfma(__ldg(phi + m * mx + i), __ldg(eA + m * my + j), v);
+  for (int m = 0; m < NB; ++m) {
+    a[m] = __ldg(phi + m * mx + i);
+    b[m] = __ldg(eB + m * mx + i);
+  }
+  C v[CC_ROWS];
 #pragma unroll
-  for (int l = 0; l < NB; ++l) v = cfma(__ldg(eB + l * mx + i), __ldg(vphi + l * my + j), v);
-  u[p] = v;
+  for (int r = 0; r < CC_ROWS; ++r)
+    if (j0 + r < my) v[r] = u[(j0 + r) * mx + i];
+#pragma unroll
+  for (int r = 0; r < CC_ROWS; ++r) {
+    const int j = j0 + r;
+    if (j >= my) break;
+    C w = v[r];
+#pragma unroll
+    for (int m = 0; m < NB; ++m) w = cfma(a[m], __ldg(eA + m * my + j), w);
+#pragma unroll
+    for (int l = 0; l < NB; ++l) w = cfma(b[l], __ldg(vphi + l * my + j), w);
+    u[j * mx + i] = w;
+  }
 }
 
 template <int NB, class C>
@@ -286,7 +306,7 @@ cudaError_t rp_launch(const StencilViewT<C>& s, const CCViewT<C>& c, const C* u,
 
 template <int NB, class C>
 cudaError_t corr_launch(const CCViewT<C>& c, C* u, cudaStream_t st) {
-  dim3 g((c.mx + 31) / 32, (c.my + 7) / 8);
+  dim3 g((c.mx + 31) / 32, (c.my + 8 * CC_ROWS - 1) / (8 * CC_ROWS));
   return mgc_launch(k_cccs_correct<NB, C>, g, dim3(32, 8), 0, st, c.mx, c.my, c.phi, c.vphi, c.eAc, c.eBc, u);
 }
 

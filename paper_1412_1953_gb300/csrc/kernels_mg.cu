@@ -143,17 +143,31 @@ __global__ void __launch_bounds__(256) k_jacobi_zero(long long n, const C* __res
 // First sweep from a zero initial guess on the Krylov vector w, fused with its
 // normalisation: v = w / sqrt(*norm2) (zeros if the norm vanishes) is written back in
 // place and u = omega D^{-1} v; the same arithmetic as k_scale_by_norm then k_jacobi_zero.
+// Two consecutive nodes per thread, their loads issued before the barrier (so they
+// overlap thread 0's square root); for complex64 the pair is one 16-byte access per
+// array when all three arrays are 16-byte aligned (the Krylov vectors and level buffers
+// are), else two 8-byte ones.
 template <class C>
 __global__ void __launch_bounds__(256) k_scale_jacobi_zero(long long n, C* w, const double* __restrict__ norm2,
                                                           const C* __restrict__ Dinv, C* __restrict__ u_out) {
   mgc_pdl_enter();
   __shared__ double sb;
-  // the node's loads are issued before the barrier, so they overlap thread 0's square root
-  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  C wv = CT<C>::make(0.0, 0.0), dv = wv;
-  if (p < n) {
-    wv = w[p];
-    dv = __ldg(Dinv + p);
+  const long long p = 2 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
+  C wv[2], dv[2];
+  const bool vec = sizeof(C) == sizeof(float2) && p + 1 < n &&
+                   ((reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(Dinv) |
+                     reinterpret_cast<uintptr_t>(u_out)) & 15) == 0;
+  if (vec) {
+    const float4 a = *reinterpret_cast<const float4*>(w + p);
+    const float4 d = __ldg(reinterpret_cast<const float4*>(Dinv + p));
+    wv[0] = CT<C>::make(a.x, a.y); wv[1] = CT<C>::make(a.z, a.w);
+    dv[0] = CT<C>::make(d.x, d.y); dv[1] = CT<C>::make(d.z, d.w);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      wv[e] = p + e < n ? w[p + e] : CT<C>::make(0.0, 0.0);
+      dv[e] = p + e < n ? __ldg(Dinv + p + e) : CT<C>::make(0.0, 0.0);
+    }
   }
   if (threadIdx.x == 0) {
     const double b = sqrt(*norm2);
@@ -161,10 +175,22 @@ __global__ void __launch_bounds__(256) k_scale_jacobi_zero(long long n, C* w, co
   }
   __syncthreads();
   const typename CT<C>::R sc = (typename CT<C>::R)sb;
-  if (p < n) {
-    const C v = cscal(sc, wv);
-    w[p] = v;
-    u_out[p] = cmul(dv, v);
+  C v[2], o[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    v[e] = cscal(sc, wv[e]);
+    o[e] = cmul(dv[e], v[e]);
+  }
+  if (vec) {
+    *reinterpret_cast<float4*>(w + p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    *reinterpret_cast<float4*>(u_out + p) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+      if (p + e < n) {
+        w[p + e] = v[e];
+        u_out[p + e] = o[e];
+      }
   }
 }
 
@@ -389,36 +415,37 @@ __global__ void __launch_bounds__(DUW * (2 * DBY + 3)) k_zero_residual_restrict(
 }
 
 // Coarsest level: u = A_c^{-1} f with the FP64 dense inverse built at setup, accumulated
-// in FP64 for either element type; the FP64 pipes (2 DFMA per clock per SM) bound the
-// 4 nc^2 operations, so the rows are spread evenly over the SMs and every load of a row
-// is issued before its FMAs.  Two launch shapes:
-//  - complex128: one block per row; its CS_THREADS threads split the row's columns
-//    (thread t takes t, t + CS_THREADS, ...), f is read through L1;
-//  - complex64: CS_WARPS rows per block, one warp per row, f widened to FP64 once per
-//    block in shared memory (widening it once per row costs as much FP64 issue as the
-//    row's FMAs).
-constexpr int CS_THREADS = 128, CS_UNROLL = (MGC_MAX_COARSE + CS_THREADS - 1) / CS_THREADS;
-constexpr int CS_WARPS = 4, CS_WUNROLL = 8;
+// in FP64 for either element type; the FP64 pipe (2 DFMA per clock per SM) bounds the
+// 4 nc^2 operations.  One block of CS_THREADS threads per row, so the block scheduler
+// spreads the rows evenly over the SMs; thread t takes columns t, t + CS_THREADS, ... (f
+// read through L1, complex64 f widened as it is used), and the warps of the ~6 rows each
+// SM holds hide the load latency.  Two warps per row keep the shuffle reduction (10 FP64
+// adds a thread) small
+// beside the 4 x 16 FMAs of each thread; with four warps per row it cost a third of the
+// FMA work, and one warp per row of four per block left SMs idle.
+constexpr int CS_THREADS = 64, CS_UNROLL = (MGC_MAX_COARSE + CS_THREADS - 1) / CS_THREADS;
 
+template <class C>
 __global__ void __launch_bounds__(CS_THREADS) k_coarse_solve(int nc, const cplx* __restrict__ Ainv,
-                                                              const cplx* __restrict__ f, cplx* __restrict__ u) {
+                                                              const C* __restrict__ f, C* __restrict__ u) {
   mgc_pdl_enter();
   __shared__ double sh[2][CS_THREADS / 32];
   const int row = blockIdx.x, t = threadIdx.x;
   const cplx* __restrict__ a = Ainv + (size_t)row * nc;
-  cplx av[CS_UNROLL], fv[CS_UNROLL];
+  cplx av[CS_UNROLL];
+  C fv[CS_UNROLL];
 #pragma unroll
   for (int q = 0; q < CS_UNROLL; ++q) {
     const int c = t + q * CS_THREADS;
     const bool ok = c < nc;
     av[q] = ok ? __ldg(a + c) : cmk(0.0, 0.0);
-    fv[q] = ok ? __ldg(f + c) : cmk(0.0, 0.0);
+    fv[q] = ok ? __ldg(f + c) : CT<C>::make(0.0, 0.0);
   }
   cplx acc0 = cmk(0.0, 0.0), acc1 = cmk(0.0, 0.0);
 #pragma unroll
   for (int q = 0; q < CS_UNROLL; q += 2) {
-    acc0 = cfma(av[q], fv[q], acc0);
-    if (q + 1 < CS_UNROLL) acc1 = cfma(av[q + 1], fv[q + 1], acc1);
+    acc0 = cfma(av[q], to_c128(fv[q]), acc0);
+    acc1 = cfma(av[q + 1], to_c128(fv[q + 1]), acc1);
   }
   acc0 = cadd(acc0, acc1);
 #pragma unroll
@@ -435,42 +462,8 @@ __global__ void __launch_bounds__(CS_THREADS) k_coarse_solve(int nc, const cplx*
     cplx tot = cmk(0.0, 0.0);
 #pragma unroll
     for (int w = 0; w < CS_THREADS / 32; ++w) tot = cadd(tot, cmk(sh[0][w], sh[1][w]));
-    u[row] = tot;
+    u[row] = CT<C>::make(tot.x, tot.y);
   }
-}
-
-__global__ void __launch_bounds__(32 * CS_WARPS) k_coarse_solve_rows(int nc, const cplx* __restrict__ Ainv,
-                                                                     const float2* __restrict__ f,
-                                                                     float2* __restrict__ u) {
-  mgc_pdl_enter();
-  __shared__ cplx fs[MGC_MAX_COARSE];
-  for (int c = threadIdx.x; c < nc; c += 32 * CS_WARPS) fs[c] = to_c128(__ldg(f + c));
-  __syncthreads();
-  const int row = blockIdx.x * CS_WARPS + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (row >= nc) return;
-  const cplx* __restrict__ a = Ainv + (size_t)row * nc;
-  cplx acc0 = cmk(0.0, 0.0), acc1 = cmk(0.0, 0.0);
-  for (int c0 = 0; c0 < nc; c0 += 32 * CS_WUNROLL) {
-    cplx v[CS_WUNROLL];
-#pragma unroll
-    for (int q = 0; q < CS_WUNROLL; ++q) {
-      const int c = c0 + 32 * q + lane;
-      v[q] = c < nc ? __ldg(a + c) : cmk(0.0, 0.0);
-    }
-#pragma unroll
-    for (int q = 0; q < CS_WUNROLL; q += 2) {
-      const int c = c0 + 32 * q + lane;
-      if (c < nc) acc0 = cfma(v[q], fs[c], acc0);
-      if (c + 32 < nc) acc1 = cfma(v[q + 1], fs[c + 32], acc1);
-    }
-  }
-  acc0 = cadd(acc0, acc1);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    acc0.x += __shfl_down_sync(0xffffffffu, acc0.x, o);
-    acc0.y += __shfl_down_sync(0xffffffffu, acc0.y, o);
-  }
-  if (lane == 0) u[row] = make_float2((float)acc0.x, (float)acc0.y);
 }
 
 
@@ -592,7 +585,7 @@ template <class C>
 cudaError_t launch_scale_jacobi_zero(const StencilViewT<C>& s, C* w, const double* norm2, C* u_out,
                                      cudaStream_t st) {
   long long n = (long long)s.mx * s.my;
-  return mgc_launch(k_scale_jacobi_zero<C>, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, n, w, norm2, s.Dinv,
+  return mgc_launch(k_scale_jacobi_zero<C>, dim3((unsigned)((n + 511) / 512)), dim3(256), 0, st, n, w, norm2, s.Dinv,
                     u_out);
 }
 
@@ -649,11 +642,7 @@ cudaError_t launch_prolong_add(int mx, int my, const C* ec, C* u, cudaStream_t s
 template <class C>
 cudaError_t launch_coarse_solve(int nc, const cplx* Ainv, const C* f, C* u, cudaStream_t st) {
   if (nc < 1 || nc > MGC_MAX_COARSE) return cudaErrorInvalidValue;
-  if constexpr (sizeof(C) == sizeof(float2))
-    return mgc_launch(k_coarse_solve_rows, dim3((nc + CS_WARPS - 1) / CS_WARPS), dim3(32 * CS_WARPS), 0, st, nc, Ainv,
-                      f, u);
-  else
-    return mgc_launch(k_coarse_solve, dim3(nc), dim3(CS_THREADS), 0, st, nc, Ainv, f, u);
+  return mgc_launch(k_coarse_solve<C>, dim3(nc), dim3(CS_THREADS), 0, st, nc, Ainv, f, u);
 }
 
 
