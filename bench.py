@@ -609,7 +609,7 @@ def batch_form(args, compare=True, per_problem=True):
            "n_b": args.nb, "rtol": args.rtol,
            "solves_per_s": len(problems) / sec, "unknowns_per_s": bs.unknowns / sec, "seconds": sec,
            "all_converged": all(s == 0 for s in st), "max_relres": max(rr), "total_steps": sum(its),
-           "schedules": {str(n): {k: sched[n][k] for k in ("levels", "nu1", "nu2")} for n in sizes},
+           "schedules": {str(n): {k: sched[n].get(k, 0) for k in ("levels", "nu1", "nu2", "tile_rows")} for n in sizes},
            "autotune_seconds": t_tune, "setup_seconds": t_setup, "graph_build_seconds": t_graph,
            "solves_per_s_with_setup": len(problems) / (sec + t_setup)}
     if per_problem:

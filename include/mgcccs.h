@@ -184,6 +184,14 @@ int mgcccs_eig_fallbacks(mgcccs_t h);
 enum { MGCCCS_DRIVER_GRAPH = 0, MGCCCS_DRIVER_HOST = 1 };
 int mgcccs_set_solve_driver(mgcccs_t h, int driver);
 
+/* Block height (2, 4 or 8 rows; 0 = the default 2) of the smoothing, residual, transfer
+ * and operator passes on the levels of h that are too small to fill the GPU with 32 x 8
+ * blocks; a tuning knob for the batch autotuner (the results do not depend on it).
+ * Waits for h's stream, then drops h's cached solve graphs (they hold the old launch
+ * shapes); batch graphs built earlier keep the shapes they were built with.  EINVAL for
+ * another value. */
+int mgcccs_set_tile_rows(mgcccs_t h, int rows);
+
 /* Batched device-driven solves: one CUDA graph holding the device-driven solves of
  * `count` problems (one handle each, krylov_restart >= 1, any mix of grids, energies
  * and precisions) as independent branches, so that one launch runs them all

@@ -10,10 +10,11 @@ instead of running one by one.
 
 The autotuner picks the pre/post smoothing sweep counts (nu1, nu2) and the level count
 (from the deepest hierarchy to the shallowest whose coarsest grid has at most 32 cells)
-with the shortest measured setup + solve time
-of the batch itself, and caches the choice in a JSON file keyed by the batch's grids, the
-precision and the GPU name.  Tile shapes of the kernels are fixed (chosen for the FP64
-pipe and HBM), so the schedule is what varies.
+with the shortest measured setup + solve time of the batch itself, then the tile height
+of the stencil passes on the small levels (2, 4 or 8 rows per block: a batch of many
+small grids runs most of its launches on those levels) by solve time, and caches the
+choice in a JSON file keyed by the batch's grids, the precision and the GPU name.  The
+fine-level tiles stay fixed (32 x 8, chosen for the FP64 pipe and HBM).
 """
 from __future__ import annotations
 
@@ -27,6 +28,7 @@ from . import mgcccs as M
 
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "autotune.json")
 SWEEPS = ((1, 1), (2, 1), (1, 2), (2, 2))
+TILE_ROWS = (2, 4, 8)
 
 
 def level_candidates(n: int, coarsest_min: int = 8, coarsest_max: int = 32) -> list[int]:
@@ -44,7 +46,7 @@ def level_candidates(n: int, coarsest_min: int = 8, coarsest_max: int = 32) -> l
 
 def default_schedule(n: int) -> dict:
     lv = level_candidates(n)
-    return {"levels": lv[-1] if lv else 1, "nu1": 1, "nu2": 1}
+    return {"levels": lv[-1] if lv else 1, "nu1": 1, "nu2": 1, "tile_rows": 0}
 
 
 def _cache_key(problems, precision: int, gpu: str) -> str:
@@ -116,6 +118,32 @@ def autotune(problems, precision: int = 1, n_b: int = 3, krylov_restart: int = 2
             if ok and (best is None or cost < best[0]):
                 best = (cost, sched)
     schedules = best[1] if best else {n: default_schedule(n) for n in sizes}
+    # tile height of the small levels' passes, on the chosen schedule (setup does not
+    # depend on it, so the solve time alone decides)
+    bs = BatchSolver(problems, schedules, n_b=n_b, precision=precision, krylov_restart=krylov_restart)
+    best_rows = None
+    for rows in TILE_ROWS:
+        for sv in bs.solvers:
+            sv.set_tile_rows(rows)
+        g = bs.graph()
+        g.run(rtol=rtol, max_iter=5)
+        times = []
+        for _ in range(repeats):
+            for u in bs.u:
+                u.zero_()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            its, rr, st = g.run(rtol=rtol, max_iter=max_iter)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t)
+        g.close()
+        ok = all(x == M.OK for x in st) and max(rr) <= rtol
+        trials.append({"tile_rows": rows, "seconds": min(times), "steps": int(sum(its)), "converged": ok})
+        if ok and (best_rows is None or min(times) < best_rows[0]):
+            best_rows = (min(times), rows)
+    bs.close()
+    for n in schedules:
+        schedules[n] = dict(schedules[n], tile_rows=best_rows[1] if best_rows else 0)
     if cache_path:
         cache = _load(cache_path)
         cache[key] = {"schedules": {str(n): sch for n, sch in schedules.items()}, "trials": trials}
@@ -139,8 +167,10 @@ class BatchSolver:
             sch = (schedules or {}).get(prob.nx) or default_schedule(prob.nx)
             p = M.params_for(prob, levels=sch["levels"], nu1=sch["nu1"], nu2=sch["nu2"], n_b=n_b,
                              krylov_restart=krylov_restart, precision=precision)
-            self.solvers.append(M.Solver(p, prob.v1, prob.v2, prob.v12, stream=torch.cuda.Stream(),
-                                         reuse_states=True))
+            sv = M.Solver(p, prob.v1, prob.v2, prob.v12, stream=torch.cuda.Stream(), reuse_states=True)
+            if sch.get("tile_rows"):
+                sv.set_tile_rows(sch["tile_rows"])
+            self.solvers.append(sv)
         self.f = [torch.as_tensor(prob.f).to("cuda") for prob in self.problems]
         self.u = [torch.zeros_like(f) for f in self.f]
 

@@ -91,8 +91,33 @@ template <> struct CT<float2> {
     return make_float2((float)a, (float)b);
   }
 };
+// binary32 -> binary64 by integer operations (exact, IEEE 754 layouts: 8/23-bit and
+// 11/52-bit exponent/fraction fields, biases 127 and 1023).  On this part a conversion
+// instruction issues on the FP64 pipe, 1/64 of the FP32 rate and the unit the
+// mixed-precision path's FP64 kernels are bound by; the integer form issues on the ALU.
+__device__ __forceinline__ double f2d_exact(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned sign = b & 0x80000000u, e = (b >> 23) & 0xffu;
+  unsigned m = b & 0x7fffffu;
+  int ed;
+  if (e == 0u) {
+    if (m == 0u) return __hiloint2double((int)sign, 0);          // +-0
+    const int s = __clz((int)m) - 8;                              // subnormal: normalise
+    m = (m << s) & 0x7fffffu;
+    ed = 897 - s;
+  } else {
+    ed = e == 0xffu ? 0x7ff : (int)e + 896;                       // inf / nan keep their fraction
+  }
+  return __hiloint2double((int)(sign | ((unsigned)ed << 20) | (m >> 3)), (int)(m << 29));
+}
 __host__ __device__ __forceinline__ double2 to_c128(double2 a) { return a; }
-__host__ __device__ __forceinline__ double2 to_c128(float2 a) { return make_double2(a.x, a.y); }
+__host__ __device__ __forceinline__ double2 to_c128(float2 a) {
+#ifdef __CUDA_ARCH__
+  return make_double2(f2d_exact(a.x), f2d_exact(a.y));
+#else
+  return make_double2(a.x, a.y);
+#endif
+}
 
 // ---------------------------------------------------------------- level descriptors
 
@@ -121,6 +146,8 @@ struct StencilViewT {
   const C* east_y;         // [my]
   const C* D;              // [my*mx] full diagonal of H - E
   const C* Dinv;           // [my*mx] omega / D
+  int tile_rows;           // block height of the stencil passes on levels too small to fill the
+                           // GPU with 32 x 8 blocks (2, 4 or 8; 0 = 2); a tuning knob only
 };
 typedef StencilViewT<cplx> StencilView;
 typedef StencilViewT<float2> StencilView32;

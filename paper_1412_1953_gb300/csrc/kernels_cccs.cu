@@ -262,10 +262,14 @@ k_channel_solve_pcr(CRSystem SA, CRSystem SB) {
 }
 
 // u += sum_m phi_m(x) e^A_m(y) + sum_l e^B_l(x) vphi_l(y) (Eq. (30)).  A thread takes one
-// column i and CC_ROWS consecutive rows: phi_m(i) and e^B_l(i) stay in registers across its
-// rows (per node only the warp-uniform e^A_m(j), vphi_l(j) are loaded), and the loads of
-// its CC_ROWS values of u are issued together.  Same sums in the same order per node.
-constexpr int CC_ROWS = 4;
+// column i and cc_rows<C>() consecutive rows: phi_m(i) and e^B_l(i) stay in registers
+// across its rows (per node only the warp-uniform e^A_m(j), vphi_l(j) are loaded), and the
+// loads of its values of u are issued together, so a complex64 warp has 8 x 256 bytes of u
+// in flight (the complex64 pass is bound by how much of u is in flight).  Same sums in the
+// same order per node.  Rows per thread: 8 for complex64 (memory-bound), 4 for complex128
+// (FP64-bound, where the register cost of more rows would only lower occupancy).
+template <class C>
+__host__ __device__ constexpr int cc_rows() { return sizeof(C) == sizeof(float2) ? 8 : 4; }
 
 template <int NB, class C>
 __global__ void __launch_bounds__(256) k_cccs_correct(int mx, int my, const C* __restrict__ phi,
@@ -273,6 +277,7 @@ __global__ void __launch_bounds__(256) k_cccs_correct(int mx, int my, const C* _
                                                       const C* __restrict__ eB, C* __restrict__ u) {
   mgc_pdl_enter();
   const int i = blockIdx.x * 32 + threadIdx.x;
+  constexpr int CC_ROWS = cc_rows<C>();
   const int j0 = (blockIdx.y * 8 + threadIdx.y) * CC_ROWS;
   if (i >= mx || j0 >= my) return;
   C a[NB], b[NB];
@@ -306,7 +311,7 @@ cudaError_t rp_launch(const StencilViewT<C>& s, const CCViewT<C>& c, const C* u,
 
 template <int NB, class C>
 cudaError_t corr_launch(const CCViewT<C>& c, C* u, cudaStream_t st) {
-  dim3 g((c.mx + 31) / 32, (c.my + 8 * CC_ROWS - 1) / (8 * CC_ROWS));
+  dim3 g((c.mx + 31) / 32, (c.my + 8 * cc_rows<C>() - 1) / (8 * cc_rows<C>()));
   return mgc_launch(k_cccs_correct<NB, C>, g, dim3(32, 8), 0, st, c.mx, c.my, c.phi, c.vphi, c.eAc, c.eBc, u);
 }
 

@@ -1679,6 +1679,27 @@ int mgcccs_set_solve_driver(mgcccs_t h, int driver) {
   return MGCCCS_OK;
 }
 
+int mgcccs_set_tile_rows(mgcccs_t h, int rows) {
+  if (!h || (rows != 0 && rows != 2 && rows != 4 && rows != 8)) return MGCCCS_EINVAL;
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return MGCCCS_ECUDA;
+  for (int l = 0; l < h->L; ++l) {
+    h->lv[l].sv.tile_rows = rows;
+    h->lv[l].sv32.tile_rows = rows;
+  }
+  // the cached graphs hold the old launch shapes
+  for (int j = 0; j < MGC_MAX_RESTART; ++j) {
+    if (h->step_exec[j]) cudaGraphExecDestroy(h->step_exec[j]);
+    if (h->step_exec32[j]) cudaGraphExecDestroy(h->step_exec32[j]);
+    h->step_exec[j] = h->step_exec32[j] = nullptr;
+  }
+  for (int q = 0; q < 4; ++q) {
+    if (h->solve_exec[q]) cudaGraphExecDestroy(h->solve_exec[q]);
+    h->solve_exec[q] = nullptr;
+    h->solve_u[q] = h->solve_f[q] = nullptr;
+  }
+  return MGCCCS_OK;
+}
+
 struct mgcccs_batch {
   std::vector<mgcccs_handle*> hs;
   std::vector<cplx*> u;

@@ -62,6 +62,7 @@ _SIGS = {
     "mgcccs_solve_host": (_i, [_vp, _vp, _vp, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
     "mgcccs_precond_apply": (_i, [_vp, _vp, _vp]),
     "mgcccs_set_solve_driver": (_i, [_vp, _i]),
+    "mgcccs_set_tile_rows": (_i, [_vp, _i]),
     "mgcccs_axis_spectrum": (_i, [_vp, _i, _i, _vp]),
     "mgcccs_eig_fallbacks": (_i, [_vp]),
     "mgcccs_batch_create": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp),
@@ -363,6 +364,11 @@ class Solver:
 
     def eig_fallbacks(self) -> int:
         return int(lib().mgcccs_eig_fallbacks(self.h))
+
+    def set_tile_rows(self, rows: int):
+        """Block height of the passes on the levels too small to fill the GPU (2, 4, 8; 0 =
+        default); results do not depend on it."""
+        _check(lib().mgcccs_set_tile_rows(self.h, int(rows)), "mgcccs_set_tile_rows")
 
     def launch_count(self) -> int:
         return int(lib().mgcccs_launch_count(self.h))

@@ -17,7 +17,7 @@ def test_level_candidates_keep_the_coarsest_grid_between_8_and_32_cells():
         lv = cands[-1] + 1
         assert n % (1 << (lv - 1)) or n // (1 << (lv - 1)) < 8
     assert BT.level_candidates(384) == [5, 6]         # coarsest grids of 24 and 12 cells
-    assert BT.default_schedule(1024) == {"levels": 8, "nu1": 1, "nu2": 1}
+    assert BT.default_schedule(1024) == {"levels": 8, "nu1": 1, "nu2": 1, "tile_rows": 0}
 
 
 def test_batching_recipe_and_cache_key():

@@ -104,6 +104,7 @@ def test_autotune_picks_a_converging_schedule_per_grid(tmp_path):
     for n, s in sched.items():
         assert (s["nu1"], s["nu2"]) in BT.SWEEPS
         assert s["levels"] in BT.level_candidates(n)
+        assert s["tile_rows"] in BT.TILE_ROWS
     bs = BT.BatchSolver(problems, sched, n_b=3, precision=1)
     g = bs.graph()
     its, rr, st = g.run(rtol=1e-10, max_iter=2000)
@@ -111,3 +112,24 @@ def test_autotune_picks_a_converging_schedule_per_grid(tmp_path):
     g.close()
     bs.close()
     assert BT.autotune(problems, precision=1, cache_path=cache) == sched
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tile_rows_do_not_change_the_solve(precision):
+    """The small levels' tile height (the autotuner's tile knob) changes launch shapes only:
+    every tile kind evaluates the same per-node arithmetic, so the solves are bit-identical."""
+    prob = _problem(128, 0.6, seed=5)
+    sv = M.Solver(M.params_for(prob, levels=5, n_b=3, krylov_restart=20, precision=precision),
+                  prob.v1, prob.v2, prob.v12)
+    f = torch.as_tensor(prob.f).to("cuda")
+    out = {}
+    for rows in (0, 4, 8, 2):
+        sv.set_tile_rows(rows)
+        u = torch.zeros_like(f)
+        its, rr = sv.solve(u, f, rtol=1e-10, max_iter=600)
+        out[rows] = (its, u)
+    for rows in (4, 8, 2):
+        assert out[rows][0] == out[0][0]
+        assert torch.equal(out[rows][1], out[0][1])
+    with pytest.raises(M.MGCCCSError):
+        sv.set_tile_rows(3)
