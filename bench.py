@@ -573,8 +573,8 @@ def batch_form(args, compare=True, per_problem=True):
     problems = inputs.batching_problems(count=args.batch_count)
     sizes = sorted({p.nx for p in problems})
     t0 = time.perf_counter()
-    sched = (BT.autotune(problems, precision=prec, n_b=args.nb) if args.autotune
-             else {n: BT.default_schedule(n) for n in sizes})
+    sched = (BT.autotune(problems, precision=prec, n_b=args.nb, repeats=getattr(args, "tune_repeats", 2))
+             if args.autotune else {n: BT.default_schedule(n) for n in sizes})
     t_tune = time.perf_counter() - t0
     M._STATE_CACHE.clear()          # setup time below includes one bound-state solve per grid size
     torch.cuda.synchronize()
@@ -610,6 +610,7 @@ def batch_form(args, compare=True, per_problem=True):
            "solves_per_s": len(problems) / sec, "unknowns_per_s": bs.unknowns / sec, "seconds": sec,
            "all_converged": all(s == 0 for s in st), "max_relres": max(rr), "total_steps": sum(its),
            "schedules": {str(n): {k: sched[n].get(k, 0) for k in ("levels", "nu1", "nu2", "tile_rows")} for n in sizes},
+           "schedule": "autotuned on this batch" if args.autotune else "default (deepest hierarchy, V(1,1))",
            "autotune_seconds": t_tune, "setup_seconds": t_setup, "graph_build_seconds": t_graph,
            "solves_per_s_with_setup": len(problems) / (sec + t_setup)}
     if per_problem:
@@ -699,8 +700,9 @@ def run_forms(args, f_d, u_fp64):
     """The three forms beside the plain FP64 solve, each bounded to seconds: the mixed
     precision form on the benchmark workload (against the FP64 solution just computed) and
     at 2048^2 on [0,60]^2 (R0 = 40, n_b = 6, 7 levels: a 31^2 coarsest grid), the 64-energy
-    batch in one graph launch, and the adjoint gradients at 1024^2 with their
-    finite-difference checks.  A form that fails records its error instead of a result."""
+    batch in one graph launch on the schedule the autotuner picks for it, and the adjoint
+    gradients at 1024^2 with their finite-difference checks.  A form that fails records its
+    error instead of a result."""
     import copy
     forms = {}
     t0 = time.perf_counter()
@@ -716,7 +718,8 @@ def run_forms(args, f_d, u_fp64):
     big.n, big.box, big.R0, big.nb, big.levels = 2048, 60.0, 40.0, 6, 7
     attempt("mixed_2048", lambda: precision_form(big))
     bat = copy.copy(args)
-    bat.precision, bat.steps, bat.warmup, bat.autotune, bat.nb = "mixed", 2, 1, False, 3
+    bat.precision, bat.steps, bat.warmup, bat.autotune, bat.nb = "mixed", 2, 1, True, 3
+    bat.tune_repeats = 1
     attempt("batch", lambda: batch_form(bat, compare=False, per_problem=False))
     attempt("adjoint", lambda: adjoint_form(args, fd_nodes=1))
     forms["seconds"] = time.perf_counter() - t0

@@ -8,12 +8,13 @@ independent branch of one CUDA graph, launched once) and the host lock-step driv
 a replayed graph on the problem's stream).  Either way small grids overlap on the GPU
 instead of running one by one.
 
-The autotuner picks the pre/post smoothing sweep counts (nu1, nu2) and the level count
-(from the deepest hierarchy to the shallowest whose coarsest grid has at most 32 cells)
-with the shortest measured setup + solve time of the batch itself, then the tile height
-of the stencil passes on the small levels (2, 4 or 8 rows per block: a batch of many
-small grids runs most of its launches on those levels) by solve time, and caches the
-choice in a JSON file keyed by the batch's grids, the precision and the GPU name.  The
+The autotuner picks, by coordinate descent on the batch itself, the pre/post smoothing
+sweep counts (nu1, nu2) and the level count (from the deepest hierarchy towards the
+shallowest whose coarsest grid has at most 32 cells) with the shortest measured setup +
+solve time, then the tile height of the stencil passes on the small levels (2, 4 or 8
+rows per block: a batch of many small grids runs most of its launches on those levels)
+by solve time, and caches the choice in a JSON file keyed by the batch's grids, the
+precision and the GPU name.  The
 fine-level tiles stay fixed (32 x 8, chosen for the FP64 pipe and HBM).
 """
 from __future__ import annotations
@@ -62,72 +63,23 @@ def _load(path):
         return {}
 
 
-def autotune(problems, precision: int = 1, n_b: int = 3, krylov_restart: int = 20, rtol: float = 1e-10,
-             max_iter: int = 2000, cache_path: str | None = DEFAULT_CACHE, repeats: int = 2,
-             force: bool = False) -> dict:
-    """Schedules {n: {levels, nu1, nu2}} for a batch of problems: every candidate — a sweep
-    pair (nu1, nu2) and the level count (the deepest of level_candidates, or one, two ...
-    levels less), the same choice for every grid size — is run on the whole batch as one batch
-    graph, and the shortest measured setup + solve time wins (each energy needs its own
-    setup; the bound states, which every schedule shares, are left out; cached unless
-    force).  The batch is
-    its own probe because a batch shares the GPU between its problems: throughput decides,
-    and a schedule with cheaper but more Arnoldi steps that wins a solve on its own (where
-    launch latency decides) can lose in the batch."""
+def _run_batch(problems, sched, n_b, precision, krylov_restart, rtol, max_iter, repeats, tile_rows=None):
+    """Setup seconds, best solve seconds over `repeats`, Arnoldi steps and convergence of
+    one schedule on the whole batch (one batch graph launch per solve)."""
     import torch
-    gpu = torch.cuda.get_device_name()
-    key = _cache_key(problems, precision, gpu)
-    cache = _load(cache_path) if cache_path else {}
-    if key in cache and not force:
-        return {int(n): sch for n, sch in cache[key]["schedules"].items()}
-    sizes = sorted({p.nx for p in problems})
-    # bound states are shared by every candidate (same grids and potentials): solve them
-    # once, so that the setup time below is the part a schedule changes
-    BatchSolver(problems, None, n_b=n_b, precision=precision, krylov_restart=krylov_restart).close()
-    best = None
-    trials = []
-    for drop in range(max(len(level_candidates(n)) for n in sizes)):
-        for nu1, nu2 in SWEEPS:
-            sched = {}
-            for n in sizes:
-                lv = level_candidates(n)
-                levels = lv[max(len(lv) - 1 - drop, 0)] if lv else 1
-                sched[n] = {"levels": levels, "nu1": nu1, "nu2": nu2}
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            bs = BatchSolver(problems, sched, n_b=n_b, precision=precision, krylov_restart=krylov_restart)
-            torch.cuda.synchronize()
-            setup = time.perf_counter() - t
-            g = bs.graph()
-            g.run(rtol=rtol, max_iter=5)                  # instantiate the batch graph
-            times, its, rr, st = [], [], [math.inf], []
-            for _ in range(repeats):
-                for u in bs.u:
-                    u.zero_()
-                torch.cuda.synchronize()
-                t = time.perf_counter()
-                its, rr, st = g.run(rtol=rtol, max_iter=max_iter)
-                torch.cuda.synchronize()
-                times.append(time.perf_counter() - t)
-            g.close()
-            bs.close()
-            ok = all(x == M.OK for x in st) and max(rr) <= rtol
-            cost = setup + min(times)
-            trials.append({"drop_levels": drop, "nu1": nu1, "nu2": nu2, "seconds": min(times), "setup_seconds": setup,
-                           "steps": int(sum(its)), "converged": ok})
-            if ok and (best is None or cost < best[0]):
-                best = (cost, sched)
-    schedules = best[1] if best else {n: default_schedule(n) for n in sizes}
-    # tile height of the small levels' passes, on the chosen schedule (setup does not
-    # depend on it, so the solve time alone decides)
-    bs = BatchSolver(problems, schedules, n_b=n_b, precision=precision, krylov_restart=krylov_restart)
-    best_rows = None
-    for rows in TILE_ROWS:
-        for sv in bs.solvers:
-            sv.set_tile_rows(rows)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    bs = BatchSolver(problems, sched, n_b=n_b, precision=precision, krylov_restart=krylov_restart)
+    torch.cuda.synchronize()
+    setup = time.perf_counter() - t
+    out = []
+    for rows in (tile_rows or (None,)):
+        if rows is not None:
+            for sv in bs.solvers:
+                sv.set_tile_rows(rows)
         g = bs.graph()
-        g.run(rtol=rtol, max_iter=5)
-        times = []
+        g.run(rtol=rtol, max_iter=5)                      # instantiate the batch graph
+        times, its, rr, st = [], [], [math.inf], []
         for _ in range(repeats):
             for u in bs.u:
                 u.zero_()
@@ -138,10 +90,66 @@ def autotune(problems, precision: int = 1, n_b: int = 3, krylov_restart: int = 2
             times.append(time.perf_counter() - t)
         g.close()
         ok = all(x == M.OK for x in st) and max(rr) <= rtol
-        trials.append({"tile_rows": rows, "seconds": min(times), "steps": int(sum(its)), "converged": ok})
-        if ok and (best_rows is None or min(times) < best_rows[0]):
-            best_rows = (min(times), rows)
+        out.append((rows, min(times), int(sum(its)), ok))
     bs.close()
+    return setup, out
+
+
+def autotune(problems, precision: int = 1, n_b: int = 3, krylov_restart: int = 20, rtol: float = 1e-10,
+             max_iter: int = 2000, cache_path: str | None = DEFAULT_CACHE, repeats: int = 2,
+             force: bool = False) -> dict:
+    """Schedules {n: {levels, nu1, nu2, tile_rows}} for a batch of problems, by coordinate
+    descent on the batch itself, each knob the same for every grid size: (1) every sweep
+    pair (nu1, nu2) on the deepest hierarchy, (2) with the best pair, one, two ... levels
+    less while that lowers the cost, (3) on that schedule the tile height of the small
+    levels' passes.  Cost is the measured setup + solve time for (1) and (2) (each energy
+    needs its own setup; the bound states, which every schedule shares, are left out) and
+    the solve time alone for (3), which setup does not depend on.  Cached unless force.
+    The batch is its own probe because a batch shares the GPU between its problems:
+    throughput decides, and a schedule with cheaper but more Arnoldi steps that wins a
+    solve on its own (where launch latency decides) can lose in the batch."""
+    import torch
+    gpu = torch.cuda.get_device_name()
+    key = _cache_key(problems, precision, gpu)
+    cache = _load(cache_path) if cache_path else {}
+    if key in cache and not force:
+        return {int(n): sch for n, sch in cache[key]["schedules"].items()}
+    sizes = sorted({p.nx for p in problems})
+    # bound states are shared by every candidate (same grids and potentials): solve them
+    # once, so that the setup time below is the part a schedule changes
+    BatchSolver(problems, None, n_b=n_b, precision=precision, krylov_restart=krylov_restart).close()
+    run = dict(n_b=n_b, precision=precision, krylov_restart=krylov_restart, rtol=rtol, max_iter=max_iter,
+               repeats=repeats)
+    trials = []
+
+    def schedule(drop, nu1, nu2):
+        sched = {}
+        for n in sizes:
+            lv = level_candidates(n)
+            sched[n] = {"levels": lv[max(len(lv) - 1 - drop, 0)] if lv else 1, "nu1": nu1, "nu2": nu2}
+        return sched
+
+    def cost(drop, nu1, nu2):
+        setup, ((_, sec, steps, ok),) = _run_batch(problems, schedule(drop, nu1, nu2), **run)
+        trials.append({"drop_levels": drop, "nu1": nu1, "nu2": nu2, "seconds": sec, "setup_seconds": setup,
+                       "steps": steps, "converged": ok})
+        return setup + sec if ok else math.inf
+
+    best = min(((cost(0, nu1, nu2), 0, nu1, nu2) for nu1, nu2 in SWEEPS), key=lambda x: x[0])
+    max_drop = max(len(level_candidates(n)) for n in sizes) - 1
+    for drop in range(1, max_drop + 1):
+        c = cost(drop, best[2], best[3])
+        if c >= best[0]:
+            break
+        best = (c, drop, best[2], best[3])
+    schedules = schedule(best[1], best[2], best[3]) if math.isfinite(best[0]) else \
+        {n: default_schedule(n) for n in sizes}
+    _, per_rows = _run_batch(problems, schedules, tile_rows=TILE_ROWS, **run)
+    best_rows = None
+    for rows, sec, steps, ok in per_rows:
+        trials.append({"tile_rows": rows, "seconds": sec, "steps": steps, "converged": ok})
+        if ok and (best_rows is None or sec < best_rows[0]):
+            best_rows = (sec, rows)
     for n in schedules:
         schedules[n] = dict(schedules[n], tile_rows=best_rows[1] if best_rows else 0)
     if cache_path:
