@@ -66,7 +66,9 @@ typedef struct {
   int levels;            /* multigrid levels including the fine one (>= 1);
                             the coarsest, with (nx>>(levels-1))-1 by
                             (ny>>(levels-1))-1 interior nodes, is solved by a
-                            dense direct method and must have at most 1024 of them */
+                            direct method: its dense inverse up to 1024 nodes,
+                            else block cyclic reduction over its rows, which
+                            needs at most 64 nodes per row and 4096 rows */
   int nu1, nu2;          /* pre/post omega-Jacobi sweeps per level */
   double omega;          /* Jacobi weight (2/3 in Sec. 3.2) */
   int n_b;               /* bound states per axis used by the CCCS, 0..8;
@@ -92,7 +94,8 @@ size_t mgcccs_workspace_size(const mgcccs_params* p);
 /*
  * Build the solver: ECS node coordinates and 5-point coefficients on every
  * level (Eq. (11)), the diagonal and omega/diagonal arrays, the dense inverse
- * of the coarsest operator, the n_b bound states of H1 and H2 (Eq. (9)) with
+ * of the coarsest operator (or, for a coarsest grid of more than 1024 nodes, the
+ * factors of its block cyclic reduction), the n_b bound states of H1 and H2 (Eq. (9)) with
  * bilinear normalisation int phi^2 dz = 1 (Sec. 3.1, Remark 3) and two
  * shift-and-invert refinement steps (Sec. 5.1.2), the channel potentials
  * V^A, V^B (Sec. 4.2) and the factorised coupled-channel systems

@@ -9,7 +9,9 @@ typedef double2 cplx;
 
 #define MGC_MAX_LEVELS 16
 #define MGC_MAX_NB 8
-#define MGC_MAX_COARSE 1024
+#define MGC_MAX_COARSE 1024    // unknowns of a coarsest grid solved by its dense inverse
+#define MGC_BP_MAX_M 64        // larger coarsest grids: block cyclic reduction, rows of at most
+#define MGC_BP_MAX_ROWS 4096   //   64 nodes and at most 4096 rows
 #define MGC_MAX_RESTART 60
 
 // ---------------------------------------------------------------- complex arithmetic
@@ -567,6 +569,15 @@ cudaError_t launch_setup_diag(int mx, int my, int stride, int fine_mx, const cpl
                               cplx* D, cplx* Dinv, int* status, cudaStream_t st);
 size_t coarse_inverse_scratch(int nc);                       // complex entries of aug
 cudaError_t launch_coarse_inverse(const StencilView& s, cplx* aug, cplx* Ainv, int* status, cudaStream_t st);
+// kernels_coarse.cu: coarsest grids beyond MGC_MAX_COARSE unknowns, block parallel cyclic
+// reduction over the grid rows (mx <= MGC_BP_MAX_M, my <= MGC_BP_MAX_ROWS)
+bool bpcr_fits(int mx, int my);
+size_t bpcr_factor_entries(int mx, int my);                  // complex entries of the factors
+size_t bpcr_scratch_entries(int mx, int my);                 // complex entries of setup scratch
+cudaError_t launch_bpcr_setup(const StencilView& s, cplx* fac, cplx* scratch, int* status, cudaStream_t st);
+// u = A_c^{-1} f through the factors; buf holds 2 mx my complex entries
+template <class C>
+cudaError_t launch_bpcr_solve(int mx, int my, const cplx* fac, const C* f, C* u, cplx* buf, cudaStream_t st);
 // eig: all m eigenvalues when already computed (eig_aberth), else null (FP64 QR inside)
 cudaError_t launch_bound_states(int m, const cplx* west, const cplx* east, const cplx* diag, const cplx* v,
                                 const cplx* w, int nb, cplx* lam, cplx* phi, cplx* scratch, int* status,

@@ -36,8 +36,10 @@ struct mgcccs_handle {
   int L;
   LevelBufs lv[MGC_MAX_LEVELS];
   int nc;
-  cplx* Ainv;
+  cplx* Ainv;              // dense inverse of the coarsest operator (nc <= MGC_MAX_COARSE)
   cplx* aug;
+  int coarse_bp;           // 1: larger coarsest grid, solved by block cyclic reduction
+  cplx *bp_fac, *bp_scr, *bp_buf;
   int nb;
   cplx *lam, *mu, *phi, *vphi, *wphi, *wvphi, *VA, *VB;
   CRSystem crA, crB;       // channel A (along y, x bound states), channel B (along x)
@@ -115,7 +117,7 @@ bool valid_params(const mgcccs_params* p) {
   if (p->nx % s || p->ny % s) return false;
   const int cx = p->nx / s, cy = p->ny / s;
   if (cx < 2 || cy < 2) return false;
-  if ((long long)(cx - 1) * (cy - 1) > MGC_MAX_COARSE) return false;
+  if ((long long)(cx - 1) * (cy - 1) > MGC_MAX_COARSE && !bpcr_fits(cx - 1, cy - 1)) return false;
   if (p->n_b < 0 || p->n_b > MGC_MAX_NB || p->n_b > p->nx - 1 || p->n_b > p->ny - 1) return false;
   if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 > 64) return false;
   if (!(p->Lx > 0) || !(p->Ly > 0) || !std::isfinite(p->E) || !std::isfinite(p->omega)) return false;
@@ -166,8 +168,17 @@ void layout(mgcccs_handle* h, Carver& cv) {
   h->inner_rtol = p.inner_rtol > 0.0 ? p.inner_rtol : 1e-5;
   const LevelBufs& c = h->lv[L - 1];
   h->nc = c.mx * c.my;
-  h->Ainv = cv.take<cplx>((size_t)h->nc * h->nc);
-  h->aug = cv.take<cplx>(coarse_inverse_scratch(h->nc));
+  h->coarse_bp = h->nc > MGC_MAX_COARSE;
+  if (h->coarse_bp) {
+    h->Ainv = h->aug = nullptr;
+    h->bp_fac = cv.take<cplx>(bpcr_factor_entries(c.mx, c.my));
+    h->bp_scr = cv.take<cplx>(bpcr_scratch_entries(c.mx, c.my));
+    h->bp_buf = cv.take<cplx>((size_t)2 * h->nc);
+  } else {
+    h->Ainv = cv.take<cplx>((size_t)h->nc * h->nc);
+    h->aug = cv.take<cplx>(coarse_inverse_scratch(h->nc));
+    h->bp_fac = h->bp_scr = h->bp_buf = nullptr;
+  }
   {
     const int mm = h->lv[0].mx > h->lv[0].my ? h->lv[0].mx : h->lv[0].my;
     h->v1c = cv.take<cplx>(h->lv[0].mx);
@@ -384,7 +395,11 @@ int do_setup(mgcccs_handle* h, const cplx* v1, const cplx* v2, const cplx* v12, 
       s.rbox = complex_seen ? 0 : 1;
     }
   }
-  MGC_LAUNCH(launch_coarse_inverse(h->lv[h->L - 1].sv, h->aug, h->Ainv, h->status, st));
+  if (h->coarse_bp) {
+    MGC_LAUNCH(launch_bpcr_setup(h->lv[h->L - 1].sv, h->bp_fac, h->bp_scr, h->status, st));
+  } else {
+    MGC_LAUNCH(launch_coarse_inverse(h->lv[h->L - 1].sv, h->aug, h->Ainv, h->status, st));
+  }
   if (h->nb > 0) {
     const LevelBufs& b = h->lv[0];
     const int nb = h->nb;
@@ -487,6 +502,15 @@ const CCViewT<float2>& cc_view<float2>(mgcccs_handle* h) { return h->cc32; }
 // Whether level passes are fused (zero-start sweep + residual + restriction; prolongation +
 // first post-smoothing sweep): always for complex64, whose FP32 work is cheap; for
 // complex128 below 512^2 nodes, where launch latency outweighs the halo recomputation.
+// The coarsest-level solve u = A_c^{-1} f: the dense inverse, or block cyclic reduction
+// for coarsest grids beyond MGC_MAX_COARSE unknowns.
+template <class C>
+cudaError_t coarse_solve(mgcccs_handle* h, const C* f, C* u, cudaStream_t st) {
+  const LevelBufs& c = h->lv[h->L - 1];
+  if (h->coarse_bp) return launch_bpcr_solve<C>(c.mx, c.my, h->bp_fac, f, u, h->bp_buf, st);
+  return launch_coarse_solve(h->nc, h->Ainv, f, u, st);
+}
+
 template <class C>
 bool fuse_level(const LevelIO<C>& b) {
   return sizeof(C) == sizeof(float2) || (long long)b.mx * b.my < 512LL * 512;
@@ -497,7 +521,7 @@ int vcycle_rec(mgcccs_handle* h, int l, C* u, const C* f, bool zero_init, C** ou
   cudaStream_t st = h->st;
   LevelIO<C> b = level_io<C>(h, l);
   if (l == h->L - 1) {
-    MGC_LAUNCH(launch_coarse_solve(h->nc, h->Ainv, f, u, st));
+    MGC_LAUNCH(coarse_solve<C>(h, f, u, st));
     *out = u;
     return MGCCCS_OK;
   }
@@ -1535,8 +1559,7 @@ int mgcccs_prolong_add(mgcccs_t h, int level, const mgcccs_c128* ec, mgcccs_c128
 int mgcccs_coarse_solve(mgcccs_t h, const mgcccs_c128* f, mgcccs_c128* u) {
   mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!h || !f || !u) return MGCCCS_EINVAL;
-  MGC_LAUNCH(launch_coarse_solve(h->nc, h->Ainv, reinterpret_cast<const cplx*>(f), reinterpret_cast<cplx*>(u),
-                                 h->st));
+  MGC_LAUNCH(coarse_solve<cplx>(h, reinterpret_cast<const cplx*>(f), reinterpret_cast<cplx*>(u), h->st));
   return MGCCCS_OK;
 }
 

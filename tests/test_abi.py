@@ -27,7 +27,10 @@ def test_host_only_entry_points(libpath):
     assert n > 16 * 127 * 127 * 4
     bad = mgcccs.make_params(100, 100, 30.0, 30.0, 20.0, 20.0, 0.5, 0.5, levels=5)   # 100 not divisible by 16
     assert mgcccs.mgcccs_workspace_size(bad) == 0
-    too_coarse = mgcccs.make_params(128, 128, 30.0, 30.0, 20.0, 20.0, 0.5, 0.5, levels=2)  # 63^2 > 1024
+    # a coarsest grid beyond 1024 nodes takes block cyclic reduction: rows of at most 64 nodes
+    rows63 = mgcccs.make_params(128, 128, 30.0, 30.0, 20.0, 20.0, 0.5, 0.5, levels=2)      # 63 x 63
+    assert 16 * 13 * 63 ** 3 < mgcccs.mgcccs_workspace_size(rows63) < 16 * 63 ** 4   # factors, not an inverse
+    too_coarse = mgcccs.make_params(256, 128, 30.0, 30.0, 20.0, 20.0, 0.5, 0.5, levels=2)  # 127 x 63
     assert mgcccs.mgcccs_workspace_size(too_coarse) == 0
     assert mgcccs.mgcccs_strerror(mgcccs.ENOTCONV).startswith("max_iter")
     assert mgcccs.lib().mgcccs_setup(None, None, None, None, None, None, 0, None) == mgcccs.EINVAL

@@ -28,13 +28,16 @@ def _oracle_relres(prob, u):
     return float(np.linalg.norm(O.residual(lev, u, prob.f)) / np.linalg.norm(prob.f))
 
 
-def test_precision_form_2048_meets_tolerance_and_matches_fp64():
+@pytest.mark.parametrize("levels", [6, 9])
+def test_precision_form_2048_meets_tolerance_and_matches_fp64(levels):
+    """6 levels: the 63^2 coarsest grid of block cyclic reduction, the depth the benchmark's
+    forms time; 9 levels: a 7^2 coarsest grid (dense inverse)."""
     prob = inputs.temkin_poet(2048, L=60.0, R0=40.0, theta=math.pi / 6, E=0.5, seed=0)
     f = torch.as_tensor(prob.f).to("cuda")
     sols = {}
     for prec in (0, 1):
-        sv = M.Solver(M.params_for(prob, levels=9, n_b=6, krylov_restart=20, precision=prec), prob.v1, prob.v2,
-                      prob.v12)
+        sv = M.Solver(M.params_for(prob, levels=levels, n_b=6, krylov_restart=20, precision=prec), prob.v1,
+                      prob.v2, prob.v12)
         u = torch.zeros_like(f)
         its, rr = sv.solve(u, f, rtol=1e-10, max_iter=1000)
         assert rr <= 1e-10

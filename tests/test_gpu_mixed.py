@@ -28,10 +28,13 @@ def _pair(prob, levels, nb, **kw):
     return so, sg
 
 
-def test_complex64_preconditioner_matches_oracle_to_single_precision():
-    L = 30.0 * 64 / 128
-    prob = inputs.temkin_poet(64, L=L, R0=2 * L / 3, theta=math.pi / 6, E=0.5, seed=5)
-    so, sg = _pair(prob, 4, 3)
+@pytest.mark.parametrize("n,levels", [(64, 4), (128, 2)])
+def test_complex64_preconditioner_matches_oracle_to_single_precision(n, levels):
+    """(128, 2): a 63 x 63 coarsest grid, solved by block cyclic reduction in FP64 from the
+    complex64 restricted residual."""
+    L = 30.0 * n / 128
+    prob = inputs.temkin_poet(n, L=L, R0=2 * L / 3, theta=math.pi / 6, E=0.5, seed=5)
+    so, sg = _pair(prob, levels, 3)
     rng = np.random.default_rng(9)
     r = rng.standard_normal(prob.f.shape) + 1j * rng.standard_normal(prob.f.shape)
     z = torch.zeros(prob.f.shape, dtype=torch.complex128, device="cuda")

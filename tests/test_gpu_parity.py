@@ -347,25 +347,48 @@ def test_coarse_solve_961_unknowns_matches_dense_solve():
         assert rel(host(ud), ref) <= 1e-12
 
 
+@pytest.mark.parametrize("n,ny,levels", [(128, None, 2), (64, 40, 1), (40, 64, 1), (64, 34, 1)])
+def test_coarse_solve_block_reduction_matches_dense_solve(n, ny, levels):
+    """Coarsest grids beyond 1024 nodes are solved by block cyclic reduction over their rows
+    (setup-time block factors, one launch per reduction level).  Against numpy's dense solve
+    of the oracle's coarsest operator: 63 x 63 (the coarsest grid of 1024^2 on 5 levels),
+    39 rows of 63, 63 rows of 39 and 33 rows of 63 (row counts that are not one less than
+    a power of two)."""
+    prob = tp_small(n, ny=ny)
+    so, sg = pair(prob, levels, 0)
+    lev = so.levels[-1]
+    assert lev.shape[0] * lev.shape[1] > 1024
+    A = O.assemble_unweighted(lev).toarray()
+    for seed in (5, 6):
+        f = rand_c(lev.shape, seed)
+        ud = torch.empty_like(dev(f))
+        sg.coarse_solve(dev(f), ud)
+        ref = np.linalg.solve(A, f.ravel()).reshape(f.shape)
+        assert rel(host(ud), ref) <= 1e-12
+
+
+BENCH_LEVELS = 5
+
+
 @pytest.fixture(scope="module")
 def bench_pair():
-    """The benchmark workload: 1024^2 TP/ECS on [0,30]^2, E = 0.5, n_b = 3, V(1,1), 6 levels
-    (31^2 coarsest grid), GMRES(20); the oracle on the same problem."""
+    """The benchmark workload: 1024^2 TP/ECS on [0,30]^2, E = 0.5, n_b = 3, V(1,1), 5 levels
+    (63^2 coarsest grid, block cyclic reduction), GMRES(20); the oracle on the same problem."""
     prob = inputs.temkin_poet(1024)
-    so = O.Solver(O.params_from_problem(prob, levels=6, n_b=3), prob.v1, prob.v2, prob.v12)
-    sg = M.Solver(M.params_for(prob, levels=6, n_b=3, krylov_restart=20), prob.v1, prob.v2, prob.v12)
+    so = O.Solver(O.params_from_problem(prob, levels=BENCH_LEVELS, n_b=3), prob.v1, prob.v2, prob.v12)
+    sg = M.Solver(M.params_for(prob, levels=BENCH_LEVELS, n_b=3, krylov_restart=20), prob.v1, prob.v2, prob.v12)
     yield prob, so, sg
     sg.close()
 
 
 def test_benchmark_configuration_steps_match_oracle(bench_pair):
-    """At the benchmarked size and depth: the 961-unknown coarsest solve (<= 1e-12 against a
+    """At the benchmarked size and depth: the 3969-unknown coarsest solve (<= 1e-12 against a
     dense solve), one V-cycle from zero (<= 1e-12), the bound states, and one CCCS after it
     (<= 1e-9: the correction is built from the third, nearly continuum-embedded eigenvector,
     whose last digits depend on how it was refined)."""
     prob, so, sg = bench_pair
     lev = so.levels[-1]
-    assert lev.shape == (31, 31)
+    assert lev.shape == (63, 63)
     fc = rand_c(lev.shape, 17)
     uc = torch.empty_like(dev(fc))
     sg.coarse_solve(dev(fc), uc)
