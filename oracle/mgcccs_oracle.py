@@ -243,13 +243,23 @@ def build_levels(p: Params, v1, v2, v12) -> list[Level]:
     return levels
 
 
+def coarsest_solve(lev: Level, f: np.ndarray) -> np.ndarray:
+    """The exact coarsest-level solve of the V-cycle (Sec. 3.2): dense LU with partial
+    pivoting of the coarsest operator, factorised on first use and kept on the level (a
+    level's operator never changes), then a forward and a back substitution per call."""
+    lu = lev.__dict__.get("_dense_lu")
+    if lu is None:
+        lu = scipy.linalg.lu_factor(assemble_unweighted(lev).toarray())
+        lev.__dict__["_dense_lu"] = lu
+    return scipy.linalg.lu_solve(lu, f.ravel()).reshape(f.shape)
+
+
 def vcycle(levels: list[Level], p: Params, u: np.ndarray, f: np.ndarray, l: int = 0) -> np.ndarray:
     """One V(nu1, nu2)-cycle on level l: pre-smooth, residual, restrict, recurse,
     interpolate and add, post-smooth.  The coarsest level is solved exactly."""
     lev = levels[l]
     if l == len(levels) - 1:
-        A = assemble_unweighted(lev).toarray()
-        return np.linalg.solve(A, f.ravel()).reshape(f.shape)
+        return coarsest_solve(lev, f)
     u = jacobi(lev, u, f, p.omega, p.nu1)
     rc = restrict_fw(residual(lev, u, f))
     ec = vcycle(levels, p, np.zeros_like(rc), rc, l + 1)
