@@ -8,14 +8,13 @@ independent branch of one CUDA graph, launched once) and the host lock-step driv
 a replayed graph on the problem's stream).  Either way small grids overlap on the GPU
 instead of running one by one.
 
-The autotuner picks, by coordinate descent on the batch itself, the pre/post smoothing
-sweep counts (nu1, nu2) and the level count (from the deepest hierarchy towards the
-shallowest whose coarsest grid has at most 32 cells) with the shortest measured setup +
-solve time, then the tile height of the stencil passes on the small levels (2, 4 or 8
-rows per block: a batch of many small grids runs most of its launches on those levels)
-by solve time, and caches the choice in a JSON file keyed by the batch's grids, the
-precision and the GPU name.  The
-fine-level tiles stay fixed (32 x 8, chosen for the FP64 pipe and HBM).
+The autotuner picks, by coordinate descent on the batch itself, the level count (from the
+deepest hierarchy to the shallowest whose coarsest grid has at most 64 cells) and then the
+pre/post smoothing sweep counts (nu1, nu2) with the shortest measured setup + solve time,
+then the tile height of the stencil passes on the small levels (2, 4 or 8 rows per block:
+a batch of many small grids runs most of its launches on those levels) by solve time, and
+caches the choice in a JSON file keyed by the batch's grids, the precision and the GPU
+name.  The fine-level tiles stay fixed (32 x 8, chosen for the FP64 pipe and HBM).
 """
 from __future__ import annotations
 
@@ -32,9 +31,10 @@ SWEEPS = ((1, 1), (2, 1), (1, 2), (2, 2))
 TILE_ROWS = (2, 4, 8)
 
 
-def level_candidates(n: int, coarsest_min: int = 8, coarsest_max: int = 32) -> list[int]:
+def level_candidates(n: int, coarsest_min: int = 8, coarsest_max: int = 64) -> list[int]:
     """Level counts whose coarsest grid has n / 2^(levels-1) cells per side in
-    [coarsest_min, coarsest_max] (the dense coarsest solve holds at most 31^2 unknowns)."""
+    [coarsest_min, coarsest_max]: up to 31^2 unknowns the coarsest solve applies a dense
+    inverse, beyond that (rows of at most 63 nodes) block cyclic reduction."""
     out = []
     for lv in range(2, 16):
         step = 1 << (lv - 1)
@@ -99,9 +99,9 @@ def autotune(problems, precision: int = 1, n_b: int = 3, krylov_restart: int = 2
              max_iter: int = 2000, cache_path: str | None = DEFAULT_CACHE, repeats: int = 2,
              force: bool = False) -> dict:
     """Schedules {n: {levels, nu1, nu2, tile_rows}} for a batch of problems, by coordinate
-    descent on the batch itself, each knob the same for every grid size: (1) every sweep
-    pair (nu1, nu2) on the deepest hierarchy, (2) with the best pair, one, two ... levels
-    less while that lowers the cost, (3) on that schedule the tile height of the small
+    descent on the batch itself, each knob the same for every grid size: (1) V(1,1) on
+    every depth (the deepest hierarchy, one, two ... levels less), (2) on the best depth
+    every other sweep pair (nu1, nu2), (3) on that schedule the tile height of the small
     levels' passes.  Cost is the measured setup + solve time for (1) and (2) (each energy
     needs its own setup; the bound states, which every schedule shares, are left out) and
     the solve time alone for (3), which setup does not depend on.  Cached unless force.
@@ -135,13 +135,13 @@ def autotune(problems, precision: int = 1, n_b: int = 3, krylov_restart: int = 2
                        "steps": steps, "converged": ok})
         return setup + sec if ok else math.inf
 
-    best = min(((cost(0, nu1, nu2), 0, nu1, nu2) for nu1, nu2 in SWEEPS), key=lambda x: x[0])
     max_drop = max(len(level_candidates(n)) for n in sizes) - 1
-    for drop in range(1, max_drop + 1):
-        c = cost(drop, best[2], best[3])
-        if c >= best[0]:
-            break
-        best = (c, drop, best[2], best[3])
+    nu1, nu2 = SWEEPS[0]
+    best = min(((cost(drop, nu1, nu2), drop, nu1, nu2) for drop in range(max_drop + 1)), key=lambda x: x[0])
+    for nu1, nu2 in SWEEPS[1:]:
+        c = cost(best[1], nu1, nu2)
+        if c < best[0]:
+            best = (c, best[1], nu1, nu2)
     schedules = schedule(best[1], best[2], best[3]) if math.isfinite(best[0]) else \
         {n: default_schedule(n) for n in sizes}
     _, per_rows = _run_batch(problems, schedules, tile_rows=TILE_ROWS, **run)

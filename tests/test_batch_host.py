@@ -6,17 +6,18 @@ from paper_1412_1953_gb300 import batch as BT
 from paper_1412_1953_gb300 import inputs
 
 
-def test_level_candidates_keep_the_coarsest_grid_between_8_and_32_cells():
+def test_level_candidates_keep_the_coarsest_grid_between_8_and_64_cells():
     for n in (64, 128, 256, 384, 512, 768, 1024, 2048):
         cands = BT.level_candidates(n)
         assert cands == sorted(cands) and cands
         for lv in cands:
             step = 1 << (lv - 1)
-            assert n % step == 0 and 8 <= n // step <= 32
+            assert n % step == 0 and 8 <= n // step <= 64
         # no deeper hierarchy keeps the coarsest grid at 8 cells or more
         lv = cands[-1] + 1
         assert n % (1 << (lv - 1)) or n // (1 << (lv - 1)) < 8
-    assert BT.level_candidates(384) == [5, 6]         # coarsest grids of 24 and 12 cells
+    assert BT.level_candidates(384) == [4, 5, 6]      # coarsest grids of 48, 24 and 12 cells
+    assert BT.level_candidates(1024) == [5, 6, 7, 8]  # 64 (block cyclic reduction) ... 8 cells
     assert BT.default_schedule(1024) == {"levels": 8, "nu1": 1, "nu2": 1, "tile_rows": 0}
 
 
