@@ -317,6 +317,28 @@ def _event_ms(stream, fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
+def fp64_probe(stream, device_index, iters=4096):
+    """Attainable FP64 rate of this GPU, measured live: mgcccs_fp64_probe (independent FP64
+    FMA chains only, 4 blocks of 256 threads per SM) timed with CUDA events on `stream`,
+    median of 5 launches after 2 warm-up launches."""
+    import torch
+    from paper_1412_1953_gb300 import mgcccs as M
+    blocks = 4 * torch.cuda.get_device_properties(device_index).multi_processor_count
+    out = torch.empty(blocks, dtype=torch.float64, device="cuda")
+    times = []
+    for r in range(7):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ops = M.mgcccs_fp64_probe(blocks, iters, out, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        if r >= 2:
+            times.append(e0.elapsed_time(e1) * 1e-3)
+    sec = statistics.median(times)
+    return {"tflops": 2.0 * ops / sec / 1e12, "ms": sec * 1e3, "lane_ops": ops,
+            "what": f"{blocks} blocks x 256 threads x {iters} rounds x {M.PROBE_CHAINS} independent DFMA chains"}
+
+
 def kernel_rooflines(args, solver, stream, f_d, flush, workload_name, device_index):
     """Roofline of the kernel that leads a complex128 Arnoldi step by time (the Gram-Schmidt
     update k_multiaxpy<double2>, 15% of a step; k_multidot<double2> 15%; both FP64-pipe bound),
@@ -363,6 +385,7 @@ def kernel_rooflines(args, solver, stream, f_d, flush, workload_name, device_ind
     jac_ops = jacobi_dp_ops(args.n, 30.0, 20.0)
     jac_bytes = 64.0 * N
     traffic = profiled_traffic("k_multiaxpy", workload_name)
+    probe = fp64_probe(stream, device_index)
     return {"bound": "alu", "kernel": f"k_multiaxpy<double2> (Gram-Schmidt update, {k} basis vectors, "
                                       f"fine level {args.n - 1}^2, complex128)",
             "achieved": upd_tf, "peak": tf_peak, "unit": "TFLOP/s", "frac": upd_tf / tf_peak, "traffic": traffic,
@@ -370,6 +393,7 @@ def kernel_rooflines(args, solver, stream, f_d, flush, workload_name, device_ind
             "algorithmic_bytes_per_launch": upd_bytes,
             "hbm_achieved_gbs": upd_bytes / (upd_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src,
             "hbm_frac": upd_bytes / (upd_ms * 1e-3) / 1e9 / hbm,
+            "fp64_probe": probe, "frac_of_probe": upd_tf / probe["tflops"],
             "others": [
                 {"kernel": f"k_multidot<double2> + k_reduce_dots ({k + 1} vectors, w among them)", "bound": "alu",
                  "kernel_ms": dot_ms, "achieved": dot_flops / (dot_ms * 1e-3) / 1e12, "unit": "TFLOP/s",

@@ -303,6 +303,19 @@ int mgcccs_get_bound_states(mgcccs_t h, mgcccs_c128* lambda, mgcccs_c128* phi,
 #define MGCCCS_NOALLOC_MAX_N 8388608
 int mgcccs_norm2_noalloc(const mgcccs_c128* v, size_t n, double* norm2, void* stream);
 
+/* ---- FP64 throughput probe (a measurement utility; the paper has no counterpart) ----
+ * The complex128 kernels are bound by the FP64 pipe.  mgcccs_fp64_probe launches
+ * `blocks` blocks of 256 threads on `stream` (cudaStream_t as void*; NULL = legacy
+ * default stream), each thread running MGCCCS_PROBE_CHAINS independent recurrences
+ * a <- fma(a, m, b) for `iters` rounds, and writes one sum per block to the device
+ * array out[0..blocks).  FP64 lane operations executed:
+ * blocks * 256 * iters * MGCCCS_PROBE_CHAINS (2 flops each); the caller times the
+ * launch (asynchronous) with events on `stream`.  Returns MGCCCS_EINVAL for
+ * blocks < 1, iters < 1 or a NULL out (nothing is launched), MGCCCS_ECUDA if the
+ * launch fails. */
+#define MGCCCS_PROBE_CHAINS 8
+int mgcccs_fp64_probe(int blocks, int iters, double m, double b, double* out, void* stream);
+
 /*
  * The two halves of one classical Gram-Schmidt pass of the Arnoldi process of the
  * GMRES(m) solver that MG-CCCS preconditions (Sec. 6), exposed for component tests and

@@ -85,6 +85,7 @@ _SIGS = {
     "mgcccs_gs_update": (_i, [_vp, _vp, ctypes.c_longlong, _i, _vp, _vp]),
     "mgcccs_launch_count": (ctypes.c_longlong, [_vp]),
     "mgcccs_norm2_noalloc": (_i, [_vp, ctypes.c_size_t, _vp, _vp]),
+    "mgcccs_fp64_probe": (_i, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _vp, _vp]),
     "mgcccs_strerror": (ctypes.c_char_p, [_i]),
     "mgcccs_destroy": (None, [_vp]),
 }
@@ -141,6 +142,23 @@ def mgcccs_norm2_noalloc(v, out, stream=None):
         st = stream if stream is not None else torch.cuda.current_stream(v.device)
         _check(lib().mgcccs_norm2_noalloc(v.data_ptr(), v.numel(), out.data_ptr(), st.cuda_stream),
                "mgcccs_norm2_noalloc")
+
+
+PROBE_CHAINS = 8
+
+
+def mgcccs_fp64_probe(blocks, iters, out, m=0.9999999, b=1e-9, stream=None):
+    """Launch the FP64 throughput probe (see include/mgcccs.h) into the float64 CUDA tensor
+    `out` (>= blocks elements) on `stream` (default: the current stream of out's device).
+    Returns the FP64 lane operations it executes."""
+    import torch
+    if out.dtype != torch.float64 or not out.is_cuda or out.numel() < blocks:
+        raise TypeError("out must be a float64 CUDA tensor of at least `blocks` elements")
+    with torch.cuda.device(out.device):
+        st = stream if stream is not None else torch.cuda.current_stream(out.device)
+        _check(lib().mgcccs_fp64_probe(int(blocks), int(iters), float(m), float(b), out.data_ptr(), st.cuda_stream),
+               "mgcccs_fp64_probe")
+    return int(blocks) * 256 * int(iters) * PROBE_CHAINS
 
 
 def make_params(nx, ny, Lx, Ly, R0x, R0y, theta, E, levels=5, nu1=1, nu2=1, omega=2.0 / 3.0, n_b=3,
