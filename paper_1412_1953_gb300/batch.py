@@ -18,6 +18,7 @@ name.  The fine-level tiles stay fixed (32 x 8, chosen for the FP64 pipe and HBM
 """
 from __future__ import annotations
 
+import concurrent.futures
 import json
 import math
 import os
@@ -29,6 +30,7 @@ from . import mgcccs as M
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "autotune.json")
 SWEEPS = ((1, 1), (2, 1), (1, 2), (2, 2))
 TILE_ROWS = (2, 4, 8)
+SETUP_THREADS = 4          # host threads that set problems of a batch up concurrently
 
 
 def level_candidates(n: int, coarsest_min: int = 8, coarsest_max: int = 64) -> list[int]:
@@ -167,18 +169,39 @@ class BatchSolver:
     """Setup handles (one stream each) for a list of Problems; solve() runs them together."""
 
     def __init__(self, problems, schedules: dict | None = None, n_b: int = 3, precision: int = 1,
-                 krylov_restart: int = 20):
+                 krylov_restart: int = 20, setup_threads: int = SETUP_THREADS):
         import torch
         self.problems = list(problems)
-        self.solvers = []
-        for prob in self.problems:
-            sch = (schedules or {}).get(prob.nx) or default_schedule(prob.nx)
-            p = M.params_for(prob, levels=sch["levels"], nu1=sch["nu1"], nu2=sch["nu2"], n_b=n_b,
-                             krylov_restart=krylov_restart, precision=precision)
-            sv = M.Solver(p, prob.v1, prob.v2, prob.v12, stream=torch.cuda.Stream(), reuse_states=True)
-            if sch.get("tile_rows"):
-                sv.set_tile_rows(sch["tile_rows"])
-            self.solvers.append(sv)
+        dev = torch.cuda.current_device()
+
+        def make(prob):
+            with torch.cuda.device(dev):
+                sch = (schedules or {}).get(prob.nx) or default_schedule(prob.nx)
+                p = M.params_for(prob, levels=sch["levels"], nu1=sch["nu1"], nu2=sch["nu2"], n_b=n_b,
+                                 krylov_restart=krylov_restart, precision=precision)
+                sv = M.Solver(p, prob.v1, prob.v2, prob.v12, stream=torch.cuda.Stream(), reuse_states=True)
+                if sch.get("tile_rows"):
+                    sv.set_tile_rows(sch["tile_rows"])
+                return sv
+
+        # the first problem of each grid computes the grid's bound states (then shared); the
+        # other setups run from several host threads, each on its own stream, so that their
+        # kernels (a setup alone fills few SMs) overlap on the GPU
+        first = {}
+        for k, prob in enumerate(self.problems):
+            first.setdefault((prob.nx, prob.ny, prob.Lx, prob.Ly, prob.R0x, prob.R0y, prob.theta,
+                              prob.v1.tobytes(), prob.v2.tobytes()), k)
+        self.solvers = [None] * len(self.problems)
+        for k in first.values():
+            self.solvers[k] = make(self.problems[k])
+        rest = [k for k in range(len(self.problems)) if self.solvers[k] is None]
+        if setup_threads > 1 and len(rest) > 1:
+            with concurrent.futures.ThreadPoolExecutor(max_workers=setup_threads) as ex:
+                for k, sv in zip(rest, ex.map(lambda k: make(self.problems[k]), rest)):
+                    self.solvers[k] = sv
+        else:
+            for k in rest:
+                self.solvers[k] = make(self.problems[k])
         self.f = [torch.as_tensor(prob.f).to("cuda") for prob in self.problems]
         self.u = [torch.zeros_like(f) for f in self.f]
 

@@ -20,6 +20,7 @@
 // coarsest grid of a 1024^2 problem on 5 levels, against 63 M for the dense inverse of
 // the same grid.  Everything stays FP64 in both precisions.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -266,10 +267,22 @@ cudaError_t launch_bpcr_setup(const StencilView& s, cplx* fac, cplx* scratch, in
   cplx* DfT = fac + (size_t)2 * Lp * B;
   const size_t inv_smem = sizeof(cplx) * ((size_t)m * m + m);
   const size_t mm_smem = sizeof(cplx) * (size_t)m * m;
-  cudaError_t e = cudaFuncSetAttribute(k_bp_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_bp_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mm_smem);
-  if (e != cudaSuccess) return e;
+  {
+    // the limits for the largest block size, set once: handles set up from several host
+    // threads must not lower the limit under another thread's launch
+    static std::mutex mu;
+    static bool granted = false;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!granted) {
+      const int M = MGC_BP_MAX_M;
+      cudaError_t e = cudaFuncSetAttribute(k_bp_invert, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(cplx) * (M * M + M)));
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_bp_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(cplx) * M * M));
+      if (e != cudaSuccess) return e;
+      granted = true;
+    }
+  }
   const int grid = (int)std::min<long long>(((long long)B + 255) / 256, 8LL * mgc_sm_count());
   k_bp_assemble<<<grid, 256, 0, st>>>(s, Dm, Lm[0], Um[0]);
   const dim3 gg(nr, BP_GEMM_SPLIT);

@@ -133,3 +133,29 @@ def test_tile_rows_do_not_change_the_solve(precision):
         assert torch.equal(out[rows][1], out[0][1])
     with pytest.raises(M.MGCCCSError):
         sv.set_tile_rows(3)
+
+
+def test_concurrent_setups_with_block_reduction_match_sequential_setups():
+    """Problems of a batch are set up from several host threads at once.  Here the coarsest
+    grids take block cyclic reduction with two block sizes (63 rows of 63 at 256^2 on 3
+    levels, 47 of 47 at 384^2 on 4 levels), whose setup kernels share launch limits: the
+    concurrent setups give the same solves, bit for bit, as setups made one at a time."""
+    from paper_1412_1953_gb300 import batch as BT
+    problems = [_problem(n, E, seed=k) for k, (n, E) in enumerate([(256, 0.4), (384, 1.1), (256, 1.7),
+                                                                     (384, 0.2), (256, 0.9), (384, 1.4)])]
+    sched = {256: {"levels": 3, "nu1": 1, "nu2": 1}, 384: {"levels": 4, "nu1": 1, "nu2": 1}}
+    out = {}
+    for threads in (1, 4):
+        bs = BT.BatchSolver(problems, sched, n_b=3, precision=1, setup_threads=threads)
+        g = bs.graph()
+        for u in bs.u:
+            u.zero_()
+        its, rr, st = g.run(rtol=1e-10, max_iter=2000)
+        torch.cuda.synchronize()
+        assert st == [M.OK] * len(problems) and max(rr) <= 1e-10
+        out[threads] = (its, [u.clone() for u in bs.u])
+        g.close()
+        bs.close()
+    assert out[1][0] == out[4][0]
+    for a, b in zip(out[1][1], out[4][1]):
+        assert torch.equal(a, b)
