@@ -1,6 +1,7 @@
 // Internal types and device helpers of the MG-CCCS library (not part of the C ABI).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "mgcccs.h"
@@ -390,6 +391,19 @@ inline cudaError_t mgc_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
   g_mgc_last_kernel_stream = st;
   return e;
 }
+
+// ---------------------------------------------------------------- tracing
+// Host-side NVTX range for the lifetime of the object: every C-ABI entry point and every
+// V-cycle level opens one, so a timeline tool shows which call and level enqueued each
+// kernel (inside a captured graph the ranges mark the capture, not the replays).  Without
+// a tool attached the calls return at once.
+struct MgcRange {
+  explicit MgcRange(const char* name) { nvtxRangePushA(name); }
+  ~MgcRange() { nvtxRangePop(); }
+  MgcRange(const MgcRange&) = delete;
+  MgcRange& operator=(const MgcRange&) = delete;
+};
+const char* mgc_level_range_name(int level);   // "mgcccs level <l>"
 
 // ---------------------------------------------------------------- launchers (defined in the .cu files)
 // Streaming multiprocessors of the current device, queried once per device; grid sizes

@@ -16,6 +16,15 @@
 thread_local cudaStream_t g_mgc_last_kernel_stream = nullptr;
 thread_local bool g_mgc_last_was_kernel = false;
 
+const char* mgc_level_range_name(int level) {
+  static const char* names[MGC_MAX_LEVELS] = {
+      "mgcccs level 0",  "mgcccs level 1",  "mgcccs level 2",  "mgcccs level 3",
+      "mgcccs level 4",  "mgcccs level 5",  "mgcccs level 6",  "mgcccs level 7",
+      "mgcccs level 8",  "mgcccs level 9",  "mgcccs level 10", "mgcccs level 11",
+      "mgcccs level 12", "mgcccs level 13", "mgcccs level 14", "mgcccs level 15"};
+  return level >= 0 && level < MGC_MAX_LEVELS ? names[level] : "mgcccs level";
+}
+
 int mgc_sm_count() {
   static std::atomic<int> cache[64];
   int dev = 0;

@@ -518,6 +518,7 @@ bool fuse_level(const LevelIO<C>& b) {
 
 template <class C>
 int vcycle_rec(mgcccs_handle* h, int l, C* u, const C* f, bool zero_init, C** out) {
+  MgcRange nvtx_range(mgc_level_range_name(l));
   cudaStream_t st = h->st;
   LevelIO<C> b = level_io<C>(h, l);
   if (l == h->L - 1) {
@@ -1400,6 +1401,7 @@ size_t mgcccs_workspace_size(const mgcccs_params* p) {
 
 int mgcccs_setup(mgcccs_t* out, const mgcccs_params* p, const mgcccs_c128* v1, const mgcccs_c128* v2,
                  const mgcccs_c128* v12, void* workspace, size_t workspace_bytes, void* stream) {
+  MgcRange nvtx_range("mgcccs_setup");
   mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!out || !valid_params(p) || !v1 || !v2 || !v12 || !workspace) return MGCCCS_EINVAL;
   *out = nullptr;
@@ -1428,6 +1430,7 @@ int mgcccs_setup_with_states(mgcccs_t* out, const mgcccs_params* p, const mgcccs
                              const mgcccs_c128* v12, const mgcccs_c128* lambda, const mgcccs_c128* phi,
                              const mgcccs_c128* mu, const mgcccs_c128* vphi, void* workspace, size_t workspace_bytes,
                              void* stream) {
+  MgcRange nvtx_range("mgcccs_setup_with_states");
   mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!out || !valid_params(p) || !v1 || !v2 || !v12 || !workspace) return MGCCCS_EINVAL;
   if (p->n_b > 0 && (!lambda || !phi || !mu || !vphi)) return MGCCCS_EINVAL;
@@ -1456,12 +1459,14 @@ int mgcccs_setup_with_states(mgcccs_t* out, const mgcccs_params* p, const mgcccs
 }
 
 int mgcccs_vcycle(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f) {
+  MgcRange nvtx_range("mgcccs_vcycle");
   mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!h || !u || !f) return MGCCCS_EINVAL;
   return vcycle_fine(h, reinterpret_cast<cplx*>(u), reinterpret_cast<const cplx*>(f), false);
 }
 
 int mgcccs_cccs(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f) {
+  MgcRange nvtx_range("mgcccs_cccs");
   mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!h || !u || !f || h->nb <= 0) return MGCCCS_EINVAL;
   return cccs_fine(h, reinterpret_cast<cplx*>(u), reinterpret_cast<const cplx*>(f));
@@ -1469,6 +1474,7 @@ int mgcccs_cccs(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f) {
 
 int mgcccs_solve(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f, double rtol, int max_iter, int* iters,
                  double* relres, double* history) {
+  MgcRange nvtx_range("mgcccs_solve");
   mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!h || !u || !f) return MGCCCS_EINVAL;
   return solve_impl(h, reinterpret_cast<cplx*>(u), reinterpret_cast<const cplx*>(f), rtol, max_iter, iters, relres,
@@ -1477,6 +1483,7 @@ int mgcccs_solve(mgcccs_t h, mgcccs_c128* u, const mgcccs_c128* f, double rtol, 
 
 int mgcccs_solve_host(mgcccs_t h, mgcccs_c128* u_host, const mgcccs_c128* f_host, double rtol, int max_iter,
                       int* iters, double* relres) {
+  MgcRange nvtx_range("mgcccs_solve_host");
   mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!h || !u_host || !f_host) return MGCCCS_EINVAL;
   const size_t bytes = sizeof(cplx) * (size_t)h->lv[0].mx * h->lv[0].my;
@@ -1490,6 +1497,7 @@ int mgcccs_solve_host(mgcccs_t h, mgcccs_c128* u_host, const mgcccs_c128* f_host
 }
 
 int mgcccs_precond_apply(mgcccs_t h, mgcccs_c128* z, const mgcccs_c128* r) {
+  MgcRange nvtx_range("mgcccs_precond_apply");
   mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!h || !z || !r || (const void*)z == (const void*)r) return MGCCCS_EINVAL;
   if (!h->mixed) return precond(h, reinterpret_cast<cplx*>(z), reinterpret_cast<const cplx*>(r));
@@ -1628,6 +1636,7 @@ int mgcccs_weighted_product(mgcccs_t h, const mgcccs_c128* a, const mgcccs_c128*
 
 int mgcccs_batch_solve(mgcccs_t* handles, int count, mgcccs_c128* const* u, const mgcccs_c128* const* f,
                        double rtol, int max_iter, int* iters, double* relres, int* status) {
+  MgcRange nvtx_range("mgcccs_batch_solve");
   mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!handles || count < 1 || !u || !f || max_iter < 1 || !(rtol >= 0.0)) return MGCCCS_EINVAL;
   std::vector<BatchItem> items(count);
@@ -1732,6 +1741,7 @@ struct mgcccs_batch {
 
 int mgcccs_batch_create(mgcccs_batch_t* out, mgcccs_t* handles, int count, mgcccs_c128* const* u,
                         const mgcccs_c128* const* f, void* stream) {
+  MgcRange nvtx_range("mgcccs_batch_create");
   mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!out || !handles || count < 1 || !u || !f) return MGCCCS_EINVAL;
   *out = nullptr;
@@ -1762,6 +1772,7 @@ int mgcccs_batch_create(mgcccs_batch_t* out, mgcccs_t* handles, int count, mgccc
 }
 
 int mgcccs_batch_run(mgcccs_batch_t b, double rtol, int max_iter, int* iters, double* relres, int* status) {
+  MgcRange nvtx_range("mgcccs_batch_run");
   mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
   if (!b || max_iter < 1 || !(rtol >= 0.0)) return MGCCCS_EINVAL;
   for (mgcccs_handle* h : b->hs) {
