@@ -8,13 +8,14 @@ independent branch of one CUDA graph, launched once) and the host lock-step driv
 a replayed graph on the problem's stream).  Either way small grids overlap on the GPU
 instead of running one by one.
 
-The autotuner picks, by coordinate descent on the batch itself, the level count (from the
-deepest hierarchy to the shallowest whose coarsest grid has at most 64 cells) and then the
-pre/post smoothing sweep counts (nu1, nu2) with the shortest measured setup + solve time,
-then the tile height of the stencil passes on the small levels (2, 4 or 8 rows per block:
-a batch of many small grids runs most of its launches on those levels) by solve time, and
-caches the choice in a JSON file keyed by the batch's grids, the precision and the GPU
-name.  The fine-level tiles stay fixed (32 x 8, chosen for the FP64 pipe and HBM).
+The autotuner picks, by a coarse grid search and then coordinate descent on the batch
+itself, the level count (from the deepest hierarchy to the shallowest whose coarsest grid
+has at most 64 cells) and the pre/post smoothing sweep counts (nu1, nu2) with the shortest
+measured setup + solve time, then the tile height of the stencil passes on the small
+levels (2, 4 or 8 rows per block: a batch of many small grids runs most of its launches on
+those levels) by solve time, and caches the choice in a JSON file keyed by the batch's
+grids, the precision and the GPU name.  The fine-level tiles stay fixed (32 x 8, chosen for
+the FP64 pipe and HBM).
 """
 from __future__ import annotations
 
@@ -101,12 +102,13 @@ def autotune(problems, precision: int = 1, n_b: int = 3, krylov_restart: int = 2
              max_iter: int = 2000, cache_path: str | None = DEFAULT_CACHE, repeats: int = 2,
              force: bool = False) -> dict:
     """Schedules {n: {levels, nu1, nu2, tile_rows}} for a batch of problems, by coordinate
-    descent on the batch itself, each knob the same for every grid size: (1) V(1,1) on
-    every depth (the deepest hierarchy, one, two ... levels less), (2) on the best depth
-    every other sweep pair (nu1, nu2), (3) on that schedule the tile height of the small
-    levels' passes.  Cost is the measured setup + solve time for (1) (each energy needs its
-    own setup; the bound states, which every schedule shares, are left out) and the solve
-    time alone for (2) and (3), which setup does not depend on.  Cached unless force.
+    descent on the batch itself, each knob the same for every grid size: (1) V(1,1) and
+    V(2,2) on every depth (the deepest hierarchy, one, two ... levels less: more sweeps can
+    make up for a shallower hierarchy and the reverse), (2) on the best depth the other
+    sweep pairs (nu1, nu2), (3) on that schedule the tile height of the small levels'
+    passes.  Cost is the measured setup + solve time for (1) (each energy needs its own
+    setup; the bound states, which every schedule shares, are left out) and the solve time
+    alone for (2) and (3), which setup does not depend on.  Cached unless force.
     The batch is its own probe because a batch shares the GPU between its problems:
     throughput decides, and a schedule with cheaper but more Arnoldi steps that wins a
     solve on its own (where launch latency decides) can lose in the batch."""
@@ -138,13 +140,16 @@ def autotune(problems, precision: int = 1, n_b: int = 3, krylov_restart: int = 2
         return (setup + sec if with_setup else sec) if ok else math.inf
 
     max_drop = max(len(level_candidates(n)) for n in sizes) - 1
-    nu1, nu2 = SWEEPS[0]
-    best = min(((cost(drop, nu1, nu2), drop, nu1, nu2) for drop in range(max_drop + 1)), key=lambda x: x[0])
+    corner = (SWEEPS[0], SWEEPS[-1])          # V(1,1) and V(2,2)
+    best = min(((cost(drop, nu1, nu2), drop, nu1, nu2) for drop in range(max_drop + 1) for nu1, nu2 in corner),
+               key=lambda x: x[0])
     # on one depth the setup does not depend on the sweeps: compare solve times only (the
     # setup's own timing noise, several host threads, would otherwise decide close calls)
-    best_solve = [t for t in trials if t["drop_levels"] == best[1]][0]["seconds"]
+    best_solve = [t for t in trials if (t["drop_levels"], t["nu1"], t["nu2"]) == best[1:]][0]["seconds"]
     best = (best_solve, best[1], best[2], best[3])
-    for nu1, nu2 in SWEEPS[1:]:
+    for nu1, nu2 in SWEEPS:
+        if (nu1, nu2) in corner:
+            continue
         c = cost(best[1], nu1, nu2, with_setup=False)
         if c < best[0]:
             best = (c, best[1], nu1, nu2)

@@ -19,10 +19,14 @@
 // (2 ceil(log2 nr) + 1) nr m^2 complex multiply-adds, 13 M FP64 FMAs for the 63 x 63
 // coarsest grid of a 1024^2 problem on 5 levels, against 63 M for the dense inverse of
 // the same grid.  Everything stays FP64 in both precisions.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -61,29 +65,77 @@ __global__ void k_bp_assemble(StencilView s, cplx* __restrict__ Dm, cplx* __rest
   }
 }
 
-// dst_j = src_j^{-1} (or its transpose when trans) for each block j = blockIdx.x:
-// Gauss-Jordan in place in shared memory with partial pivoting (largest |re| + |im| in
-// the column, lowest row on ties); row interchanges are undone as column interchanges
-// in reverse order at the end.  A zero pivot sets MGC_ST_PIVOT and leaves dst unwritten.
-__global__ void __launch_bounds__(BP_THREADS) k_bp_invert(int m, const cplx* __restrict__ src,
-                                                          cplx* __restrict__ dst, int trans,
-                                                          int* __restrict__ status) {
-  extern __shared__ cplx sm[];
-  cplx* A = sm;                       // m * m
-  cplx* fcol = sm + m * m;            // m
-  __shared__ int perm[64];
+// The first reduction level needs no products: L_j = west_y[j] I and U_j = east_y[j] I are
+// scalar multiples of the identity, so with Di_j = D_j^{-1}
+//   alpha_j = wy_j Di_{j-1},  gamma_j = ey_j Di_{j+1},
+//   D_j' = D_j - wy_j ey_{j-1} Di_{j-1} - ey_j wy_{j+1} Di_{j+1},
+//   L_j' = -wy_j wy_{j-1} Di_{j-1} (j >= 2),  U_j' = -ey_j ey_{j+1} Di_{j+1} (j <= nr - 3),
+// one elementwise pass (alpha^T, gamma^T stored transposed; L', U' skipped on the last level).
+__global__ void k_bp_setup0(int nr, int m, const cplx* __restrict__ wy, const cplx* __restrict__ ey,
+                            const cplx* __restrict__ Di, cplx* __restrict__ AT, cplx* __restrict__ GT,
+                            cplx* __restrict__ Dm, cplx* __restrict__ Ln, cplx* __restrict__ Un, int last) {
+  const long long mm = (long long)m * m, tot = mm * nr;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < tot;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(q / mm), e = (int)(q % mm), r = e / m, c = e % m;
+    const long long tq = (long long)j * mm + (long long)c * m + r;
+    const cplx z = cmk(0.0, 0.0);
+    const cplx a = j >= 1 ? cmul(wy[j], Di[q - mm]) : z;
+    const cplx g = j + 1 < nr ? cmul(ey[j], Di[q + mm]) : z;
+    AT[tq] = a;
+    GT[tq] = g;
+    cplx d = Dm[q];
+    if (j >= 1) d = cfms(a, ey[j - 1], d);
+    if (j + 1 < nr) d = cfms(g, wy[j + 1], d);
+    Dm[q] = d;
+    if (!last) {
+      Ln[q] = j >= 2 ? cneg(cmul(a, wy[j - 1])) : z;
+      Un[q] = j + 2 < nr ? cneg(cmul(g, ey[j + 1])) : z;
+    }
+  }
+}
+
+// dst_j = src_j^{-1} (or its transpose when trans) for each block j: Gauss-Jordan with
+// partial pivoting (largest |re| + |im| in the column, lowest row on ties), a zero pivot
+// setting MGC_ST_PIVOT and leaving dst unwritten, with each block's elimination split over
+// a cluster of two CTAs: CTA r keeps columns
+// [32 r, 32 r + 32) in its shared memory, so two SMs share the O(m^3) FP64 work of a block.
+// Per pivot k: the owner of column k finds the pivot row and publishes it (cluster barrier);
+// both swap their rows k and p; the owner publishes 1/pivot and column k (barrier); both
+// scale row k and update their columns (barrier).  The row interchanges are undone at the
+// write-out: output column c is column sigma(c) of the reduced matrix, sigma the composition
+// of the interchanges in pivot order, read from whichever CTA holds it.
+constexpr int BP_HALF = 32;                      // columns per CTA (MGC_BP_MAX_M / 2)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(BP_THREADS)
+    k_bp_invert2(int m, const cplx* __restrict__ src, cplx* __restrict__ dst, int trans, int* __restrict__ status) {
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ cplx A[MGC_BP_MAX_M][BP_HALF];
+  __shared__ cplx fcol[MGC_BP_MAX_M];
+  __shared__ cplx s_d;
+  __shared__ int perm[MGC_BP_MAX_M];
   __shared__ int s_piv, s_fail;
-  const int t = threadIdx.x, mm = m * m;
-  const cplx* __restrict__ a = src + (size_t)blockIdx.x * mm;
-  for (int q = t; q < mm; q += blockDim.x) A[q] = a[q];
+  const int rank = (int)cl.block_rank(), t = threadIdx.x;
+  const int blk = blockIdx.x / 2;
+  const int c0 = rank * BP_HALF, nc = max(0, min(BP_HALF, m - c0));
+  const int mm = m * m;
+  const cplx* __restrict__ a = src + (size_t)blk * mm;
+  for (int q = t; q < m * BP_HALF; q += blockDim.x) {
+    const int r = q / BP_HALF, c = q - r * BP_HALF;
+    A[r][c] = c < nc ? a[r * m + c0 + c] : cmk(0.0, 0.0);
+  }
   if (t == 0) s_fail = 0;
-  __syncthreads();
+  cl.sync();
+  int* piv_peer = cl.map_shared_rank(&s_piv, rank ^ 1);
+  int* fail_peer = cl.map_shared_rank(&s_fail, rank ^ 1);
+  cplx* fcol_peer = cl.map_shared_rank(fcol, rank ^ 1);
+  cplx* d_peer = cl.map_shared_rank(&s_d, rank ^ 1);
   for (int k = 0; k < m; ++k) {
-    if (t < 32) {
+    const int own = k / BP_HALF, kc = k - own * BP_HALF;
+    if (rank == own && t < 32) {
       double best = -1.0;
       int bi = m;
       for (int r = k + t; r < m; r += 32) {
-        const double v = cabs1(A[r * m + k]);
+        const double v = cabs1(A[r][kc]);
         if (v > best) { best = v; bi = r; }
       }
 #pragma unroll
@@ -93,55 +145,71 @@ __global__ void __launch_bounds__(BP_THREADS) k_bp_invert(int m, const cplx* __r
         if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
       }
       if (t == 0) {
+        const int f = (!(best > 0.0) || bi >= m) ? 1 : 0;
         s_piv = bi;
-        if (!(best > 0.0) || bi >= m) s_fail = 1;
+        *piv_peer = bi;
+        s_fail = f;
+        *fail_peer = f;
       }
     }
-    __syncthreads();
+    cl.sync();
     if (s_fail) break;
     const int p = s_piv;
     if (p != k) {
-      for (int c = t; c < m; c += blockDim.x) {
-        const cplx x = A[k * m + c];
-        A[k * m + c] = A[p * m + c];
-        A[p * m + c] = x;
+      for (int c = t; c < BP_HALF; c += blockDim.x) {
+        const cplx x = A[k][c];
+        A[k][c] = A[p][c];
+        A[p][c] = x;
       }
     }
     if (t == 0) perm[k] = p;
     __syncthreads();
-    const cplx d = cdiv(cmk(1.0, 0.0), A[k * m + k]);
-    __syncthreads();                   // every thread has read the pivot
-    for (int c = t; c < m; c += blockDim.x) A[k * m + c] = c == k ? d : cmul(A[k * m + c], d);
-    for (int r = t; r < m; r += blockDim.x) fcol[r] = A[r * m + k];
-    __syncthreads();
-    for (int q = t; q < mm; q += blockDim.x) {
-      const int r = q / m, c = q - r * m;
-      if (r == k) continue;
-      const cplx old = c == k ? cmk(0.0, 0.0) : A[q];
-      A[q] = cfms(fcol[r], A[k * m + c], old);
-    }
-    __syncthreads();
-  }
-  if (s_fail) {
-    if (t == 0) atomicOr(status, MGC_ST_PIVOT);
-    return;
-  }
-  for (int k = m - 1; k >= 0; --k) {
-    const int p = perm[k];
-    if (p != k) {
+    if (rank == own) {
+      const cplx d = cdiv(cmk(1.0, 0.0), A[k][kc]);
+      if (t == 0) {
+        s_d = d;
+        *d_peer = d;
+      }
       for (int r = t; r < m; r += blockDim.x) {
-        const cplx x = A[r * m + k];
-        A[r * m + k] = A[r * m + p];
-        A[r * m + p] = x;
+        const cplx v = A[r][kc];
+        fcol[r] = v;
+        fcol_peer[r] = v;
       }
     }
+    cl.sync();
+    const cplx d = s_d;
+    for (int c = t; c < BP_HALF; c += blockDim.x)
+      A[k][c] = (rank == own && c == kc) ? d : cmul(A[k][c], d);
     __syncthreads();
+    for (int q = t; q < m * BP_HALF; q += blockDim.x) {
+      const int r = q / BP_HALF, c = q - r * BP_HALF;
+      if (r == k) continue;
+      const cplx old = (rank == own && c == kc) ? cmk(0.0, 0.0) : A[r][c];
+      A[r][c] = cfms(fcol[r], A[k][c], old);
+    }
+    cl.sync();
   }
-  cplx* __restrict__ o = dst + (size_t)blockIdx.x * mm;
-  for (int q = t; q < mm; q += blockDim.x) {
-    const int r = q / m, c = q - r * m;
-    o[trans ? c * m + r : q] = A[q];
+  if (s_fail) {
+    if (rank == 0 && t == 0) atomicOr(status, MGC_ST_PIVOT);
+    cl.sync();
+    return;
   }
+  // write-out: column c of the inverse is column sigma(c) of A, held by CTA sigma(c) / 32
+  cplx* __restrict__ o = dst + (size_t)blk * mm;
+  for (int q = t; q < m * nc; q += blockDim.x) {
+    const int r = q / nc, cl_ = q - r * nc, c = c0 + cl_;
+    int idx = c;
+    for (int k = 0; k < m; ++k) {
+      const int pk = perm[k];
+      if (idx == k) idx = pk;
+      else if (idx == pk) idx = k;
+    }
+    const int src_rank = idx / BP_HALF;
+    const cplx* col = src_rank == rank ? &A[0][0] : cl.map_shared_rank(&A[0][0], src_rank);
+    const cplx v = col[r * BP_HALF + (idx - src_rank * BP_HALF)];
+    o[trans ? c * m + r : r * m + c] = v;
+  }
+  cl.sync();                        // the partner's shared memory stays live until both have read
 }
 
 // One batched product of the reduction's setup:
@@ -265,20 +333,17 @@ cudaError_t launch_bpcr_setup(const StencilView& s, cplx* fac, cplx* scratch, in
   cplx* Um[2] = {scratch + 4 * B, scratch + 5 * B};
   const int Lp = bp_levels(nr);
   cplx* DfT = fac + (size_t)2 * Lp * B;
-  const size_t inv_smem = sizeof(cplx) * ((size_t)m * m + m);
   const size_t mm_smem = sizeof(cplx) * (size_t)m * m;
   {
-    // the limits for the largest block size, set once: handles set up from several host
-    // threads must not lower the limit under another thread's launch
+    // the limit for the largest block size, set once: handles set up from several host
+    // threads must not lower it under another thread's launch
     static std::mutex mu;
     static bool granted = false;
     std::lock_guard<std::mutex> lock(mu);
     if (!granted) {
       const int M = MGC_BP_MAX_M;
-      cudaError_t e = cudaFuncSetAttribute(k_bp_invert, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)(sizeof(cplx) * (M * M + M)));
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_bp_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(cplx) * M * M));
+      cudaError_t e =
+          cudaFuncSetAttribute(k_bp_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(cplx) * M * M));
       if (e != cudaSuccess) return e;
       granted = true;
     }
@@ -296,7 +361,14 @@ cudaError_t launch_bpcr_setup(const StencilView& s, cplx* fac, cplx* scratch, in
     // the last level keeps alpha^T, gamma^T in the free L/U buffers until D^{-1} is known
     cplx* AT = last ? Lm[cur ^ 1] : fac + (size_t)(2 * l) * B;
     cplx* GT = last ? Um[cur ^ 1] : fac + (size_t)(2 * l + 1) * B;
-    k_bp_invert<<<nr, BP_THREADS, inv_smem, st>>>(m, Dm, Di, 0, status);
+    k_bp_invert2<<<2 * nr, BP_THREADS, 0, st>>>(m, Dm, Di, 0, status);
+    if (l == 0) {
+      // scalar off-diagonal blocks: alpha, gamma, D', L', U' elementwise
+      k_bp_setup0<<<grid, 256, 0, st>>>(nr, m, s.west_y, s.east_y, Di, AT, GT, Dm, Lm[cur ^ 1], Um[cur ^ 1],
+                                        last ? 1 : 0);
+      if (!last) cur ^= 1;
+      continue;
+    }
     gemm(AT, 1, 0.0, 1.0, Lm[cur], 0, 0, Di, -s2, 0);           // alpha_j = L_j D_{j-s}^{-1}
     gemm(GT, 1, 0.0, 1.0, Um[cur], 0, 0, Di, s2, 0);            // gamma_j = U_j D_{j+s}^{-1}
     gemm(Dm, 0, 1.0, -1.0, AT, 0, 1, Um[cur], -s2, 0);          // D_j -= alpha_j U_{j-s}
@@ -307,7 +379,7 @@ cudaError_t launch_bpcr_setup(const StencilView& s, cplx* fac, cplx* scratch, in
       cur ^= 1;
     }
   }
-  k_bp_invert<<<nr, BP_THREADS, inv_smem, st>>>(m, Dm, DfT, 1, status);
+  k_bp_invert2<<<2 * nr, BP_THREADS, 0, st>>>(m, Dm, DfT, 1, status);
   if (Lp > 0) {
     // fold D^{-1} into the last level: (D^{-1} alpha)^T and (D^{-1} gamma)^T
     gemm(fac + (size_t)(2 * (Lp - 1)) * B, 1, 0.0, 1.0, DfT, 0, 1, Lm[cur ^ 1], 0, 1);
