@@ -201,16 +201,27 @@ class BatchSolver:
             first.setdefault((prob.nx, prob.ny, prob.Lx, prob.Ly, prob.R0x, prob.R0y, prob.theta,
                               prob.v1.tobytes(), prob.v2.tobytes()), k)
         self.solvers = [None] * len(self.problems)
-        for k in first.values():
+
+        def put(k):
             self.solvers[k] = make(self.problems[k])
-        rest = [k for k in range(len(self.problems)) if self.solvers[k] is None]
-        if setup_threads > 1 and len(rest) > 1:
-            with concurrent.futures.ThreadPoolExecutor(max_workers=setup_threads) as ex:
-                for k, sv in zip(rest, ex.map(lambda k: make(self.problems[k]), rest)):
-                    self.solvers[k] = sv
-        else:
-            for k in rest:
-                self.solvers[k] = make(self.problems[k])
+
+        try:
+            for k in first.values():
+                put(k)
+            rest = [k for k in range(len(self.problems)) if self.solvers[k] is None]
+            if setup_threads > 1 and len(rest) > 1:
+                with concurrent.futures.ThreadPoolExecutor(max_workers=setup_threads) as ex:
+                    for fut in [ex.submit(put, k) for k in rest]:
+                        fut.result()
+            else:
+                for k in rest:
+                    put(k)
+        except BaseException:
+            # a failed setup leaves no half-built batch: release the handles made so far
+            for sv in self.solvers:
+                if sv is not None:
+                    sv.close()
+            raise
         self.f = [torch.as_tensor(prob.f).to("cuda") for prob in self.problems]
         self.u = [torch.zeros_like(f) for f in self.f]
 
