@@ -829,6 +829,11 @@ def run_ours(args):
     u_pin = torch.empty(prob.f.shape, dtype=torch.complex128, pin_memory=True)
     f_pin.copy_(torch.as_tensor(prob.f))
     f_h, u_h = f_pin.numpy(), u_pin.numpy()
+    # warm-up: the first host-buffer solve captures the solve graph for the handle's own
+    # staging buffers (the timed device solves above used the caller's tensors)
+    for _ in range(max(1, min(args.warmup, 2))):
+        u_h[...] = 0
+        solver.solve_host(u_h, f_h, rtol=args.rtol, max_iter=args.max_iter)
     e2e_s = []
     for k in range(max(1, min(args.steps, 3))):
         u_h[...] = 0
