@@ -354,9 +354,10 @@ enum {
 // the same stream was one of its kernels: the next kernel is then launched, and its blocks
 // dispatched, as the blocks of the current one exit, instead of after the whole grid and
 // its launch bookkeeping have retired.  Correctness does not depend on it: every kernel
-// launched this way calls mgc_pdl_enter() before its first global memory access, and
-// griddepcontrol.wait returns only once the preceding kernel has completed and its writes
-// are visible.  No kernel triggers its successor early (griddepcontrol.launch_dependents):
+// launched this way calls mgc_pdl_enter() before it touches anything an earlier kernel of
+// the solve writes (the block-reduction levels first load their setup-time factors, which
+// no solve kernel writes), and griddepcontrol.wait returns only once the preceding kernel
+// has completed and its writes are visible.  No kernel triggers its successor early (griddepcontrol.launch_dependents):
 // measured on the 1024^2 solve, an early trigger made the FP64 solve slower (34.8 against
 // 33.0 ms; the FP64-bound kernels then share their SMs with resident, waiting blocks),
 // while the trigger at block exit gives 33.0 ms FP64 and 12.9 ms mixed against 33.2 and
