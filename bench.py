@@ -494,7 +494,7 @@ def run_sweep(args):
     from paper_1412_1953_gb300 import inputs
     from paper_1412_1953_gb300 import mgcccs as M
     B.build()
-    for n, lv in [(512, 7), (1024, 8)]:
+    for n, lv in [(512, 4), (1024, 5)]:         # 63^2 coarsest grids (block cyclic reduction)
         for E in (0.3, 0.5, 1.5):
             prob = inputs.temkin_poet(n, E=E, seed=0)
             f = torch.as_tensor(prob.f).to("cuda")
