@@ -8,6 +8,7 @@ import os
 import numpy as np
 import pytest
 import scipy.sparse
+import scipy.sparse.linalg
 
 from oracle import mgcccs_oracle as O
 from paper_1412_1953_gb300 import inputs
@@ -631,3 +632,23 @@ def test_inner_uniform_coefficients_have_the_closed_form(n, L, R0, gamma):
     np.testing.assert_allclose(ax.east[inner], c, rtol=1e-12)
     kink = len(inner)
     assert abs(ax.east[kink] - c) > 1e-3 * abs(c)
+
+
+def test_coarsest_solve_is_the_exact_solve_on_every_call():
+    """The V-cycle's coarsest solve (Sec. 3.2: exact) factorises the level once and reuses the
+    factors: on two right-hand sides in a row, and on two levels of different size, it
+    solves the assembled operator to a residual of rounding size, and equals a sparse LU
+    solve of the same operator."""
+    lev_a, _ = tp_level(16)
+    lev_b, _ = tp_level(32, E=1.1)
+    rng = np.random.default_rng(4)
+    for lev in (lev_a, lev_b, lev_a):
+        A = O.assemble_unweighted(lev).tocsc()
+        for _ in range(2):
+            f = rng.standard_normal(lev.shape) + 1j * rng.standard_normal(lev.shape)
+            x = O.coarsest_solve(lev, f)
+            back = np.linalg.norm(A @ x.ravel() - f.ravel()) / (
+                scipy.sparse.linalg.norm(A) * np.linalg.norm(x) + np.linalg.norm(f))
+            assert back <= 1e-15
+            ref = scipy.sparse.linalg.splu(A).solve(f.ravel()).reshape(f.shape)
+            assert np.abs(x - ref).max() <= 1e-11 * np.abs(ref).max()
