@@ -341,7 +341,7 @@ def fp64_probe(stream, device_index, iters=4096):
 
 def kernel_rooflines(args, solver, stream, f_d, flush, workload_name, device_index):
     """Roofline of the kernel that leads a complex128 Arnoldi step by time (the Gram-Schmidt
-    update k_multiaxpy<double2>, 15% of a step; k_multidot<double2> 15%; both FP64-pipe bound),
+    update k_multiaxpy<double2>, 14% of a step; k_multidot<double2> 13.5%; both FP64-pipe bound),
     timed live with CUDA events on the handle's stream over 50 launches of the same kernel
     and launch shape the solve uses, with GS_VECTORS = 11 basis vectors of the fine level
     (11 x 16.7 MB, larger than L2, so every launch streams from HBM).  Beside it: the
