@@ -712,8 +712,9 @@ def run_oracle_timing(args):
     el = time.perf_counter() - t
     rows.append({"workload": "tp_ecs_128", "steps": len(hist), "relres": float(rr), "seconds": el,
                  "setup_seconds": setup, "unknowns_per_s": prob.n_unknowns / el, "kind": "full solve"})
-    for n, L, R0, lv, nb, steps in ((512, 30.0, 20.0, 7, 3, 97), (1024, 30.0, 20.0, 8, 3, 99),
-                                     (2048, 60.0, 40.0, 9, 6, 163)):
+    # 63^2 coarsest grids, as the benchmark and the sweep (GPU step counts of those solves)
+    for n, L, R0, lv, nb, steps in ((512, 30.0, 20.0, 4, 3, 47), (1024, 30.0, 20.0, 5, 3, 48),
+                                     (2048, 60.0, 40.0, 6, 6, 76)):
         prob = inputs.temkin_poet(n, L=L, R0=R0, theta=math.pi / 6, E=0.5, seed=0)
         sub = argparse.Namespace(levels=lv, nb=nb, krylov=20)
         per, sampled, setup = oracle_step_time(prob, sub, seconds=args.cpu_seconds)
