@@ -98,8 +98,9 @@ __global__ void k_bp_setup0(int nr, int m, const cplx* __restrict__ wy, const cp
 // dst_j = src_j^{-1} (or its transpose when trans) for each block j: Gauss-Jordan with
 // partial pivoting (largest |re| + |im| in the column, lowest row on ties), a zero pivot
 // setting MGC_ST_PIVOT and leaving dst unwritten, with each block's elimination split over
-// a cluster of two CTAs: CTA r keeps columns
-// [32 r, 32 r + 32) in its shared memory, so two SMs share the O(m^3) FP64 work of a block.
+// a cluster of two CTAs: CTA r keeps columns [32 r, 32 r + 32) in its shared memory, so
+// two SMs share the O(m^3) FP64 work of a block (one CTA per block took 502 against 408 us
+// a launch of 63 blocks of 63 x 63, most of either being the per-pivot barriers).
 // Per pivot k: the owner of column k finds the pivot row and publishes it (cluster barrier);
 // both swap their rows k and p; the owner publishes 1/pivot and column k (barrier); both
 // scale row k and update their columns (barrier).  The row interchanges are undone at the
