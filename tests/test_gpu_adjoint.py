@@ -109,3 +109,29 @@ def test_autograd_function_matches_adjoint_gradients():
     assert abs(gZ.item() - (3 * ref["dZ"].real - 2 * ref["dZ"].imag)) <= 1e-9 * abs(ref["dZ"])
     want = 3 * ref["ddV"].real - 2 * ref["ddV"].imag
     assert torch.abs(gdV - want).max().item() <= 1e-9 * torch.abs(ref["ddV"]).max().item()
+
+
+def test_adjoint_gradients_through_block_reduction_match_oracle():
+    """The same gradients on 128^2 cells with 2 levels: the 63 x 63 coarsest grid is solved
+    by block cyclic reduction in every V-cycle of the forward and the adjoint solve."""
+    from paper_1412_1953_gb300 import adjoint as A
+    n, Lb = 128, 30.0
+    geom = dict(n=n, L=Lb, R0=2 * Lb / 3, theta=math.pi / 6)
+    kw = dict(levels=2, n_b=3, krylov_restart=20)
+    E, Z = 0.5, 1.0
+    prob = inputs.temkin_poet(n, L=Lb, R0=geom["R0"], theta=geom["theta"], E=E, seed=4)
+    g = inputs.gaussian_window(n, Lb, Lb / 2, Lb / 2, 2.0)
+    f, gd = torch.as_tensor(prob.f).to("cuda"), torch.as_tensor(g).to("cuda")
+    dV = np.zeros(prob.f.shape)
+    res = A.amplitude_and_gradients(E, Z, torch.as_tensor(dV).to("cuda"), f, gd, geom, kw, rtol=1e-13)
+    p = inputs.temkin_poet(n, L=Lb, R0=geom["R0"], theta=geom["theta"], E=E, Z=Z, noise_amplitude=0.0)
+    lev = O.build_levels(O.params_from_problem(p, levels=1, n_b=0), p.v1, p.v2, p.v12 + dV)[0]
+    u = O.direct_solve(lev, prob.f)
+    mu = O.direct_solve(lev, g)
+    dAdZ = inputs.tp_charge_derivative(n, Lb, geom["R0"], geom["theta"])
+    J = O.amplitude(lev, g, u)
+    dE, dZ, ddV = O.adjoint_gradients(lev, u, mu, dAdZ)
+    assert abs(res["J"] - J) <= 1e-9 * abs(J)
+    assert abs(res["dE"] - dE) <= 1e-8 * abs(dE)
+    assert abs(res["dZ"] - dZ) <= 1e-8 * abs(dZ)
+    assert np.abs(res["ddV"].cpu().numpy() - ddV).max() <= 1e-8 * np.abs(ddV).max()
