@@ -33,6 +33,8 @@ namespace {
 constexpr int BP_THREADS = 256;
 constexpr int BP_KQ = 8;            // warps of a solve block: parts of the k range
 constexpr int BP_KC = 8;            // k per warp (BP_KQ * BP_KC >= MGC_BP_MAX_M)
+static_assert(BP_KQ * BP_KC >= MGC_BP_MAX_M, "the warps of a solve block must cover every k");
+static_assert(32 * BP_KQ >= 3 * MGC_BP_MAX_M, "a solve block stages its three rows of b with one thread each");
 constexpr int BP_GEMM_SPLIT = 4;    // blocks per batched product (row slices)
 
 int bp_levels(int nr) {
