@@ -339,6 +339,57 @@ def fp64_probe(stream, device_index, iters=4096):
             "what": f"{blocks} blocks x 256 threads x {iters} rounds x {M.PROBE_CHAINS} independent DFMA chains"}
 
 
+def mixed_gs_roofline(args, rounds=10, sets=3):
+    """HBM roofline of the mixed form's leading complex64 kernels on the benchmark grid, the
+    half of the metric it is reported against FP64 plain: the Gram-Schmidt update (GS_VECTORS
+    basis vectors, the mean over a GMRES(20) cycle) and the multi-dot with its reduction
+    (GS_VECTORS + 1 vectors, w among them) on the basis pitch the solve uses.  One basis of
+    complex64 vectors (92 MB at 1023^2) fits in L2, so `sets` bases are used in turn and
+    back-to-back launches over them (more than L2 in all) are timed with CUDA events on the
+    handle's stream: every launch streams its vectors from HBM.  Algorithmic bytes: 8 B per
+    entry of every vector read, plus w written by the update."""
+    import torch
+    from paper_1412_1953_gb300 import mgcccs as M
+    prob, _ = workload(args)
+    sv = M.Solver(M.params_for(prob, levels=6, n_b=0, krylov_restart=20, precision=1), prob.v1, prob.v2, prob.v12)
+    st = sv.stream
+    N, k = sv.n, GS_VECTORS
+    ld = (N + 31) // 32 * 32
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    Vs = [torch.randn((k + 1, ld), dtype=torch.complex64, device="cuda", generator=gen) for _ in range(sets)]
+    ws = [V[k, :N].clone() for V in Vs]
+    coef = (1e-3 * torch.randn(k, dtype=torch.complex128, device="cuda", generator=gen)).contiguous()
+    out = torch.empty(k + 1, dtype=torch.complex128, device="cuda")
+    peaks, src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+
+    def per_launch_ms(call):
+        for q in range(sets):
+            call(q)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(rounds):
+            for q in range(sets):
+                call(q)
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / (rounds * sets)
+
+    upd_ms = per_launch_ms(lambda q: sv.gs_update_c64(Vs[q], k, coef, ws[q]))
+    dot_ms = per_launch_ms(lambda q: sv.gs_dots_c64(Vs[q], k + 1, Vs[q][k, :N], out))
+    sv.close()
+    upd_b, dot_b = 8.0 * N * (k + 2), 8.0 * N * (k + 1)
+    return {"bound": "hbm", "kernel": f"k_multiaxpy_c64 (complex64 Gram-Schmidt update, {k} basis vectors, "
+                                      f"fine level {args.n - 1}^2, {sets} bases in turn)",
+            "achieved": upd_b / (upd_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": upd_b / (upd_ms * 1e-3) / 1e9 / hbm, "peak_source": src, "kernel_ms": upd_ms,
+            "algorithmic_bytes_per_launch": upd_b,
+            "others": [{"kernel": f"k_multidot<float2> + k_reduce_dots ({k + 1} vectors, w among them)",
+                        "bound": "hbm", "kernel_ms": dot_ms, "achieved": dot_b / (dot_ms * 1e-3) / 1e9,
+                        "unit": "GB/s", "frac": dot_b / (dot_ms * 1e-3) / 1e9 / hbm}]}
+
+
 def kernel_rooflines(args, solver, stream, f_d, flush, workload_name, device_index):
     """Roofline of the kernel that leads a complex128 Arnoldi step by time (the Gram-Schmidt
     update k_multiaxpy<double2>, 14% of a step; k_multidot<double2> 13.5%; both FP64-pipe bound),
@@ -747,6 +798,11 @@ def run_forms(args, f_d, u_fp64):
     mix = copy.copy(args)
     mix.mixed_levels = 6
     attempt("mixed", lambda: precision_form(mix, f=f_d, u_fp64=u_fp64))
+    if isinstance(forms.get("mixed"), dict) and "error" not in forms["mixed"]:
+        try:
+            forms["mixed"]["roofline"] = mixed_gs_roofline(args)
+        except Exception as exc:
+            forms["mixed"]["roofline"] = {"error": f"{type(exc).__name__}: {exc}"}
     big = copy.copy(args)
     big.n, big.box, big.R0, big.nb, big.levels = 2048, 60.0, 40.0, 6, 6
     attempt("mixed_2048", lambda: precision_form(big))

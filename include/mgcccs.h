@@ -40,6 +40,7 @@ extern "C" {
 #endif
 
 typedef struct { double re, im; } mgcccs_c128;
+typedef struct { float re, im; } mgcccs_c64;     /* the mixed form's Krylov vectors (torch.complex64) */
 typedef struct mgcccs_handle* mgcccs_t;
 typedef struct mgcccs_batch* mgcccs_batch_t;
 
@@ -336,6 +337,15 @@ int mgcccs_gs_dots(mgcccs_t h, const mgcccs_c128* V, long long ld, int k, const 
                    mgcccs_c128* out);
 int mgcccs_gs_update(mgcccs_t h, const mgcccs_c128* V, long long ld, int k, const mgcccs_c128* coef,
                      mgcccs_c128* w);
+/* The same two halves on complex64 vectors, the kernels the mixed form (precision 1) runs
+ * in its complex64 GMRES cycles: V and w complex64 (mgcccs_c64), out and coef complex128;
+ * products accumulate in FP32 within a warp and in FP64 beyond.  With a 16-byte aligned V
+ * and w and an even ld, gs_update reads and writes entry pairs as 16-byte accesses.  Same
+ * contract and errors as above; mgcccs_gs_dots_c64 needs krylov_restart >= 1. */
+int mgcccs_gs_dots_c64(mgcccs_t h, const mgcccs_c64* V, long long ld, int k, const mgcccs_c64* w,
+                       mgcccs_c128* out);
+int mgcccs_gs_update_c64(mgcccs_t h, const mgcccs_c64* V, long long ld, int k, const mgcccs_c128* coef,
+                         mgcccs_c64* w);
 
 /* Number of kernel launches issued since setup (for launch accounting). */
 long long mgcccs_launch_count(mgcccs_t h);

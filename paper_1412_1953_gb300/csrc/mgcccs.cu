@@ -1596,6 +1596,32 @@ int mgcccs_gs_update(mgcccs_t h, const mgcccs_c128* V, long long ld, int k, cons
   return MGCCCS_OK;
 }
 
+int mgcccs_gs_dots_c64(mgcccs_t h, const mgcccs_c64* V, long long ld, int k, const mgcccs_c64* w,
+                       mgcccs_c128* out) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
+  if (!h || !V || !w || !out || h->km < 1 || k < 1 || k > h->km + 1) return MGCCCS_EINVAL;
+  const long long N = (long long)h->lv[0].mx * h->lv[0].my;
+  if (ld < N) return MGCCCS_EINVAL;
+  const int nbd = multidot_blocks(N, k);
+  MGC_LAUNCH(launch_multidot(N, k, reinterpret_cast<const float2*>(V), ld, reinterpret_cast<const float2*>(w),
+                             h->dotpart, nbd, (const int*)nullptr, h->st));
+  MGC_LAUNCH(launch_reduce_dots(nbd, k, h->dotpart, reinterpret_cast<cplx*>(out), nullptr, h->st));
+  return MGCCCS_OK;
+}
+
+int mgcccs_gs_update_c64(mgcccs_t h, const mgcccs_c64* V, long long ld, int k, const mgcccs_c128* coef,
+                         mgcccs_c64* w) {
+  mgc_not_a_kernel();   // the caller's stream: start a new chain of programmatic launches
+  if (!h || !V || !coef || !w || k < 1 || k > MGC_MAX_RESTART + 1) return MGCCCS_EINVAL;
+  const long long N = (long long)h->lv[0].mx * h->lv[0].my;
+  if (ld < N) return MGCCCS_EINVAL;
+  // the launch shape the mixed solve uses for its complex64 update
+  MGC_LAUNCH(launch_multiaxpy(N, k, reinterpret_cast<const float2*>(V), ld, reinterpret_cast<const cplx*>(coef),
+                              -1.0, reinterpret_cast<float2*>(w), (double*)nullptr, krylov_blocks(N, 6),
+                              (const int*)nullptr, h->st));
+  return MGCCCS_OK;
+}
+
 int mgcccs_get_bound_states(mgcccs_t h, mgcccs_c128* lambda, mgcccs_c128* phi, mgcccs_c128* mu,
                             mgcccs_c128* vphi) {
   if (!h || h->nb <= 0) return MGCCCS_EINVAL;

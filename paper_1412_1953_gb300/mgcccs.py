@@ -83,6 +83,8 @@ _SIGS = {
     "mgcccs_get_bound_states": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "mgcccs_gs_dots": (_i, [_vp, _vp, ctypes.c_longlong, _i, _vp, _vp]),
     "mgcccs_gs_update": (_i, [_vp, _vp, ctypes.c_longlong, _i, _vp, _vp]),
+    "mgcccs_gs_dots_c64": (_i, [_vp, _vp, ctypes.c_longlong, _i, _vp, _vp]),
+    "mgcccs_gs_update_c64": (_i, [_vp, _vp, ctypes.c_longlong, _i, _vp, _vp]),
     "mgcccs_launch_count": (ctypes.c_longlong, [_vp]),
     "mgcccs_norm2_noalloc": (_i, [_vp, ctypes.c_size_t, _vp, _vp]),
     "mgcccs_fp64_probe": (_i, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _vp, _vp]),
@@ -315,13 +317,22 @@ class Solver:
                "mgcccs_weighted_product")
 
     # -- Gram-Schmidt halves of an Arnoldi step (fine-level vectors)
-    def _basis(self, V, k):
+    def _basis(self, V, k, dtype=None):
         import torch
-        if not isinstance(V, torch.Tensor) or V.dtype != torch.complex128 or not V.is_cuda:
-            raise TypeError("V must be a complex128 CUDA tensor")
+        dtype = dtype or torch.complex128
+        if not isinstance(V, torch.Tensor) or V.dtype != dtype or not V.is_cuda:
+            raise TypeError(f"V must be a {dtype} CUDA tensor")
         if V.dim() != 2 or V.shape[0] < k or V.shape[1] < self.n or V.stride(1) != 1:
-            raise ValueError(f"V must be a (>= {k}, >= {self.n}) complex128 tensor with unit column stride")
+            raise ValueError(f"V must be a (>= {k}, >= {self.n}) {dtype} tensor with unit column stride")
         return V.data_ptr(), V.stride(0)
+
+    def _c64(self, t, name):
+        import torch
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.complex64 or not t.is_cuda:
+            raise TypeError(f"{name} must be a complex64 CUDA tensor")
+        if not t.is_contiguous() or t.numel() != self.n:
+            raise ValueError(f"{name} must be contiguous with {self.n} elements")
+        return t.data_ptr()
 
     def gs_dots(self, V, k, w, out):
         """out[i] = sum_p conj(V[i, p]) w[p] for i < k (out: k-element complex128 CUDA tensor)."""
@@ -334,6 +345,20 @@ class Solver:
         vp, ld = self._basis(V, k)
         _check(lib().mgcccs_gs_update(self.h, vp, ld, int(k), _ptr(_dev_c128(coef, k, "coef")), self._f(w, "w")),
                "mgcccs_gs_update")
+
+    def gs_dots_c64(self, V, k, w, out):
+        """The complex64 multi-dot of the mixed form: V, w complex64, out k-element complex128."""
+        import torch
+        vp, ld = self._basis(V, k, torch.complex64)
+        _check(lib().mgcccs_gs_dots_c64(self.h, vp, ld, int(k), self._c64(w, "w"), _ptr(_dev_c128(out, k, "out"))),
+               "mgcccs_gs_dots_c64")
+
+    def gs_update_c64(self, V, k, coef, w):
+        """The complex64 update of the mixed form: V, w complex64, coef k-element complex128."""
+        import torch
+        vp, ld = self._basis(V, k, torch.complex64)
+        _check(lib().mgcccs_gs_update_c64(self.h, vp, ld, int(k), _ptr(_dev_c128(coef, k, "coef")),
+                                          self._c64(w, "w")), "mgcccs_gs_update_c64")
 
     # -- single steps
     def level_size(self, level: int) -> int:

@@ -301,6 +301,36 @@ def test_gram_schmidt_halves_match_definition(k):
     assert torch.equal(out, out2)
 
 
+@pytest.mark.parametrize("ld_pad", [0, 1, 64])
+def test_complex64_gram_schmidt_halves_match_definition(ld_pad):
+    """mgcccs_gs_dots_c64 and mgcccs_gs_update_c64 (the kernels of the mixed form's
+    complex64 GMRES cycles) against their definitions evaluated in FP64 from the same
+    complex64 values: the products accumulate in FP32 within a warp, so the bound is
+    single-precision rounding of the sums.  Even and odd leading dimensions take the
+    paired and the per-entry update."""
+    prob = tp_small(128, seed=9)
+    _, sg = pair(prob, 3, 0, krylov_restart=20)
+    N = 127 * 127
+    ld = N + ld_pad
+    k = 11
+    V = rand_c((k + 1, ld), 60).astype(np.complex64)
+    w = rand_c(N, 61).astype(np.complex64)
+    V[k, :N] = w
+    Vd, wd = dev(V), dev(w)
+    out = torch.empty(k + 1, dtype=torch.complex128, device="cuda")
+    sg.gs_dots_c64(Vd, k + 1, Vd[k, :N], out)
+    V64, w64 = V[:, :N].astype(np.complex128), w.astype(np.complex128)
+    ref = V64.conj() @ w64
+    got = host(out)
+    scale = np.sqrt((np.abs(V64) ** 2).sum(axis=1) * (np.abs(w64) ** 2).sum())
+    assert np.all(np.abs(got - ref) <= 1e-5 * scale)
+    coef = rand_c(k, 62)
+    sg.gs_update_c64(Vd, k, dev(coef), wd)
+    want = w64 - coef @ V64[:k]
+    got_w = host(wd).astype(np.complex128)
+    assert np.abs(got_w - want).max() <= 1e-5 * np.abs(want).max()
+
+
 def test_gmres_partial_cycle_matches_oracle():
     """Ten Arnoldi steps of right-preconditioned GMRES(20) (one partial cycle): the GPU
     iterate (CGS2 Arnoldi, Givens least squares) equals the oracle's (MGS, dense
